@@ -1,0 +1,215 @@
+"""CPU oracle for population annealing of the 2D q-state Potts model.
+
+TEST INFRASTRUCTURE, not part of the product.  Only the test suite,
+``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import this package.  It wraps ``pa_oracle.c`` (plain,
+single-threaded C; see that file for the paper passages each function
+follows) with ctypes and numpy.  It never imports the CUDA package and the
+CUDA package never imports it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pa_oracle.c")
+_LIB = os.path.join(_HERE, "libpa_oracle.so")
+
+NEAREST_INT = 0
+ROUND = 1
+INIT_RANDOM = 0
+INIT_GROUND = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile pa_oracle.c into libpa_oracle.so (gcc, -O2, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+             "-Wall", "-o", tmp, _SRC, "-lm"],
+            check=True,
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("beta", ctypes.c_double), ("lnQ", ctypes.c_double), ("lnZ", ctypes.c_double),
+        ("meanE", ctypes.c_double), ("meanE2", ctypes.c_double), ("C", ctypes.c_double),
+        ("meanM", ctypes.c_double), ("S_f", ctypes.c_double),
+        ("R", ctypes.c_int64), ("n_families", ctypes.c_int64), ("sumE", ctypes.c_int64),
+        ("sumE2", ctypes.c_int64), ("sumMt", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        P = ctypes.c_void_p
+        i32, i64, u32, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+        L.orc_philox4x32_10.argtypes = [P, P, P]
+        L.orc_energy.argtypes = [ctypes.c_int, P]
+        L.orc_energy.restype = i64
+        L.orc_max_count.argtypes = [ctypes.c_int, ctypes.c_int, P]
+        L.orc_max_count.restype = i64
+        L.orc_thresholds.argtypes = [f64, P]
+        L.orc_metropolis_decide.argtypes = [ctypes.c_int, ctypes.c_int, P, u32, u32, P]
+        L.orc_metropolis_decide.restype = ctypes.c_int
+        L.orc_sweep_replica.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, u32, u32, u64]
+        L.orc_init_random.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, P]
+        L.orc_init_ground.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, P]
+        L.orc_copy_numbers.argtypes = [i64, P, f64, i64, ctypes.c_int, u32, u64, P, P, P]
+        L.orc_copy_numbers.restype = i64
+        L.orc_parents.argtypes = [i64, P, P]
+        L.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, ctypes.c_int, ctypes.c_int, P,
+                              ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+        L.orc_run.restype = i64
+        L.orc_obs_size.restype = ctypes.c_int
+        L.orc_density_of_states.argtypes = [ctypes.c_int, ctypes.c_int, P]
+        L.orc_density_of_states.restype = ctypes.c_int
+        L.orc_site_matrix.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, f64, P]
+        L.orc_site_matrix.restype = ctypes.c_int
+        L.orc_reweight.argtypes = [i64, P, P, f64, P, P, P, P]
+        assert L.orc_obs_size() == ctypes.sizeof(Obs)
+        del i32
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def energy(spins: np.ndarray) -> int:
+    s = np.ascontiguousarray(spins, dtype=np.uint8)
+    return int(lib().orc_energy(s.shape[-1], _p(s)))
+
+
+def max_count(q: int, spins: np.ndarray) -> int:
+    s = np.ascontiguousarray(spins, dtype=np.uint8)
+    return int(lib().orc_max_count(q, s.shape[-1], _p(s)))
+
+
+def thresholds(beta: float) -> np.ndarray:
+    t = np.zeros(9, dtype=np.uint32)
+    lib().orc_thresholds(float(beta), _p(t))
+    return t
+
+
+def metropolis_decide(q, cur, nb, u0, u1, thr) -> int:
+    n = np.ascontiguousarray(nb, dtype=np.int32)
+    t = np.ascontiguousarray(thr, dtype=np.uint32)
+    return int(lib().orc_metropolis_decide(q, cur, _p(n), int(u0), int(u1), _p(t)))
+
+
+def sweep_replica(q: int, spins: np.ndarray, beta: float, theta: int, step: int, slot: int, seed: int) -> np.ndarray:
+    """theta sweeps of one L x L replica; returns a new array."""
+    s = np.array(spins, dtype=np.uint8, copy=True, order="C")
+    thr = thresholds(beta)
+    lib().orc_sweep_replica(q, s.shape[-1], _p(s), _p(thr), theta, step, slot, seed)
+    return s
+
+
+def init_random(q: int, L: int, slot_begin: int, count: int, seed: int) -> np.ndarray:
+    out = np.zeros((count, L, L), dtype=np.uint8)
+    lib().orc_init_random(q, L, slot_begin, count, seed, _p(out))
+    return out
+
+
+def init_ground(q: int, L: int, slot_begin: int, count: int, seed: int) -> np.ndarray:
+    out = np.zeros((count, L, L), dtype=np.uint8)
+    lib().orc_init_ground(q, L, slot_begin, count, seed, _p(out))
+    return out
+
+
+def copy_numbers(E: np.ndarray, dbeta: float, R_target: int, mode: int, step: int, seed: int):
+    """Returns (r, lnQ, R_new, rho)."""
+    e = np.ascontiguousarray(E, dtype=np.int32)
+    r = np.zeros(e.size, dtype=np.int32)
+    rho = np.zeros(e.size, dtype=np.float64)
+    lnq = ctypes.c_double()
+    Rn = lib().orc_copy_numbers(e.size, _p(e), float(dbeta), R_target, mode, step, seed, _p(r),
+                                ctypes.byref(lnq), _p(rho))
+    return r, lnq.value, int(Rn), rho
+
+
+def parents(r: np.ndarray) -> np.ndarray:
+    rr = np.ascontiguousarray(r, dtype=np.int32)
+    out = np.zeros(int(rr.sum()), dtype=np.int32)
+    lib().orc_parents(rr.size, _p(rr), _p(out))
+    return out
+
+
+def run(q, L, R, seed, theta, betas, mode=NEAREST_INT, init_mode=INIT_RANDOM, R_cap=None,
+        want_hist=False, want_state=True):
+    """Full PA run over betas[0..K].  Returns a dict of numpy arrays."""
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    K = betas.size - 1
+    N = L * L
+    if R_cap is None:
+        R_cap = R + R // 4 + 64
+    obs = (Obs * (K + 1))()
+    hist = np.zeros((K + 1, 2 * N + 1), dtype=np.int32) if want_hist else None
+    spins = np.zeros((R_cap, L, L), dtype=np.uint8) if want_state else None
+    E = np.zeros(R_cap, dtype=np.int32) if want_state else None
+    anc = np.zeros(R_cap, dtype=np.int32) if want_state else None
+    Rf = lib().orc_run(q, L, R, R_cap, seed, theta, K, _p(betas), mode, init_mode,
+                       ctypes.cast(obs, ctypes.c_void_p),
+                       _p(hist) if hist is not None else None,
+                       _p(spins) if spins is not None else None,
+                       _p(E) if E is not None else None,
+                       _p(anc) if anc is not None else None)
+    out = {name: np.array([getattr(o, name) for o in obs]) for name, _ in Obs._fields_}
+    out["R_final"] = int(Rf)
+    if want_hist:
+        out["hist"] = hist
+    if want_state and Rf > 0:
+        out["spins"] = spins[:Rf]
+        out["E"] = E[:Rf]
+        out["anc"] = anc[:Rf]
+    return out
+
+
+def density_of_states(q: int, L: int) -> np.ndarray:
+    g = np.zeros(2 * L * L + 1, dtype=np.uint64)
+    rc = lib().orc_density_of_states(q, L, _p(g))
+    if rc != 0:
+        raise ValueError("lattice too large for enumeration")
+    return g
+
+
+def site_matrix(q: int, L: int, site: int, beta: float) -> np.ndarray:
+    n = q ** (L * L)
+    P = np.zeros((n, n), dtype=np.float64)
+    rc = lib().orc_site_matrix(q, L, site, float(beta), _p(P))
+    if rc != 0:
+        raise ValueError("state space too large")
+    return P
+
+
+def reweight(E: np.ndarray, dbeta: float, O: np.ndarray | None = None):
+    """Returns (lnQ, <E>_tau, <O>_tau, cov_tau(O, E))."""
+    e = np.ascontiguousarray(E, dtype=np.int32)
+    o = np.ascontiguousarray(O, dtype=np.float64) if O is not None else None
+    a, b, c, d = (ctypes.c_double() for _ in range(4))
+    lib().orc_reweight(e.size, _p(e), _p(o) if o is not None else None, float(dbeta),
+                       ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
+    return a.value, b.value, (c.value if o is not None else None), (d.value if o is not None else None)

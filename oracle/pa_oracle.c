@@ -1,0 +1,559 @@
+/*
+ * pa_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, single-threaded, deliberately slow CPU restatement of population
+ * annealing (PA) for the two-dimensional q-state Potts model, following
+ * Barash, Weigel, Shchur & Janke, "Exploring first-order phase transitions
+ * with population annealing" (arXiv:1704.01888).  Only the test suite,
+ * __graft_entry__.smoke() and the CPU-baseline / reference legs of bench.py
+ * may load this file's library.  The CUDA library never links or calls it and
+ * the two share no source.
+ *
+ * Every function follows the paper's definitions in their plain order:
+ *   - the Hamiltonian H = -J sum_<ij> delta(s_i, s_j), J = 1, periodic
+ *     square lattice (Sec. 3, Eq. 3);
+ *   - the magnetisation through the occupation of the most common state
+ *     (Sec. 3, Eq. 5);
+ *   - the PA loop: resample with tau_i(E_j) = exp(-(beta_i-beta_{i-1})E_j)/Q_i,
+ *     Q_i = sum_j exp(-(beta_i-beta_{i-1})E_j)/R_{i-1}, then theta Metropolis
+ *     rounds at beta_i, then population averages (Sec. 2, steps 1-5);
+ *   - the free-energy estimator -beta_i F = ln Z_{beta_0} + sum_m ln Q_m
+ *     (Sec. 2, Eq. 2), with Z_{beta_0=0} = q^N (Sec. 6) and the zero-temperature
+ *     normalisation Z = q exp(-beta E_0), E_0 = -2N (Sec. 6, Eqs. 7-8);
+ *   - ground-state initialisation for heating runs (Sec. 5, Eq. 6).
+ * Choices the paper leaves open (random-number keying, the Metropolis proposal,
+ * the copy-count rounding rule, the family-entropy definition) are fixed here
+ * exactly as the CUDA library fixes them; each is marked "reading:".
+ *
+ * Floating point is IEEE double with contraction disabled (-ffp-contract=off);
+ * spins, energies, counts and histograms are integers.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from Salmon, Moraes, Dror & Shaw, "Parallel random numbers:  */
+/* as easy as 1, 2, 3" (SC'11): 10 rounds of two 32x32->64 multiplies, the    */
+/* high halves xored with the other counter words and the round key, the key  */
+/* bumped by the Weyl constants between rounds.                               */
+/* ------------------------------------------------------------------------- */
+ORC_API void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* reading: the counter word c1 carries a 2-bit domain tag in its top bits so
+ * that initialisation, sweeps, resampling and ground-state draws never share
+ * a counter. */
+#define ORC_DOM_SWEEP    0x00000000u
+#define ORC_DOM_INIT     0x40000000u
+#define ORC_DOM_RESAMPLE 0x80000000u
+#define ORC_DOM_GROUND   0xC0000000u
+
+static void orc_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t out[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* floor(u * n / 2^32): an integer in [0, n) from one 32-bit word. */
+static uint32_t orc_scale(uint32_t u, uint32_t n)
+{
+    return (uint32_t)(((uint64_t)u * (uint64_t)n) >> 32);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Model: Sec. 3, Eq. 3 and Eq. 5.  Lattices are stored row-major, s[y*L+x], */
+/* states 0..q-1 (the paper's 1..q shifted by one).                           */
+/* ------------------------------------------------------------------------- */
+
+/* E = -sum over the 2N bonds of delta(s_i, s_j); each bond is visited once as
+ * the (right, down) bond of its left/upper site.  reading: for L = 2 the right
+ * and left neighbours coincide, so that pair is one site's right bond and the
+ * other's, counted twice, which keeps E_0 = -2N (Sec. 6). */
+ORC_API int64_t orc_energy(int L, const uint8_t *s)
+{
+    int64_t e = 0;
+    for (int y = 0; y < L; ++y) {
+        for (int x = 0; x < L; ++x) {
+            int here = s[y * L + x];
+            int right = s[y * L + (x + 1) % L];
+            int down = s[((y + 1) % L) * L + x];
+            if (here == right) e -= 1;
+            if (here == down) e -= 1;
+        }
+    }
+    return e;
+}
+
+/* M~ = max over states alpha of the number of sites in state alpha (Eq. 5). */
+ORC_API int64_t orc_max_count(int q, int L, const uint8_t *s)
+{
+    int64_t counts[256];
+    for (int a = 0; a < q; ++a) counts[a] = 0;
+    for (int i = 0; i < L * L; ++i) counts[s[i]] += 1;
+    int64_t best = 0;
+    for (int a = 0; a < q; ++a)
+        if (counts[a] > best) best = counts[a];
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Metropolis single-spin-flip update (Sec. 2 step 3, Sec. 3).                */
+/* reading: the proposal is uniform over the q-1 other states,                 */
+/*   s' = (s + 1 + floor(u0 (q-1) / 2^32)) mod q,                              */
+/* and the move is accepted iff u1 < T[dE], where dE = E(s') - E(s) is an      */
+/* integer in [-4, 4] and T[d] = min(2^32 - 1, floor(min(1, exp(-beta d)) 2^32)). */
+/* ------------------------------------------------------------------------- */
+ORC_API void orc_thresholds(double beta, uint32_t thr[9])
+{
+    for (int d = -4; d <= 4; ++d) {
+        double a = exp(-beta * (double)d);
+        if (a >= 1.0)
+            thr[d + 4] = 0xFFFFFFFFu;
+        else
+            thr[d + 4] = (uint32_t)(a * 4294967296.0);
+    }
+}
+
+/* One attempt on a site in state `cur` whose four neighbours are nb[0..3].
+ * Returns the state after the attempt. */
+ORC_API int orc_metropolis_decide(int q, int cur, const int nb[4], uint32_t u0, uint32_t u1,
+                                  const uint32_t thr[9])
+{
+    int prop = (cur + 1 + (int)orc_scale(u0, (uint32_t)(q - 1))) % q;
+    int n_cur = 0, n_prop = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (nb[k] == cur) n_cur += 1;
+        if (nb[k] == prop) n_prop += 1;
+    }
+    /* E = -(number of satisfied bonds): moving cur -> prop changes E by
+     * n_cur - n_prop. */
+    int dE = n_cur - n_prop;
+    if (u1 < thr[dE + 4]) return prop;
+    return cur;
+}
+
+static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
+{
+    nb[0] = s[y * L + (x + L - 1) % L];
+    nb[1] = s[y * L + (x + 1) % L];
+    nb[2] = s[((y + L - 1) % L) * L + x];
+    nb[3] = s[((y + 1) % L) * L + x];
+}
+
+/* theta checkerboard sweeps of one replica at the thresholds `thr`.
+ * reading: one sweep updates the colour-0 sites ((x+y) even) and then the
+ * colour-1 sites.  With L even no two sites of one colour are neighbours, so
+ * this in-place row-major order equals a simultaneous update of each colour.
+ * Random words: site (x, y) has sublattice index h = (y L + x) >> 1; the
+ * Philox call with counter (h >> 1, SWEEP | (2k + colour), step, slot) serves
+ * the sites h and h^1, words (0,1) going to the even h and (2,3) to the odd. */
+ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint32_t thr[9], int theta,
+                               uint32_t step, uint32_t slot, uint64_t seed)
+{
+    for (int k = 0; k < theta; ++k) {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int y = 0; y < L; ++y) {
+                for (int x = 0; x < L; ++x) {
+                    if (((x + y) & 1) != colour) continue;
+                    uint32_t h = (uint32_t)(y * L + x) >> 1;
+                    uint32_t w[4];
+                    orc_draw(seed, h >> 1, ORC_DOM_SWEEP | (uint32_t)(2 * k + colour), step, slot, w);
+                    uint32_t u0 = w[2 * (h & 1)];
+                    uint32_t u1 = w[2 * (h & 1) + 1];
+                    int nb[4];
+                    orc_neighbours(L, s, x, y, nb);
+                    s[y * L + x] = (uint8_t)orc_metropolis_decide(q, s[y * L + x], nb, u0, u1, thr);
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Initial populations.                                                        */
+/* ------------------------------------------------------------------------- */
+
+/* beta_0 = 0: every site independently uniform over the q states (Sec. 2,
+ * step 1).  Site i = y L + x of slot r takes word (i & 3) of the call with
+ * counter (i >> 2, INIT, 0, r). */
+ORC_API void orc_init_random(int q, int L, int64_t slot_begin, int64_t count, uint64_t seed, uint8_t *spins)
+{
+    int N = L * L;
+    for (int64_t r = 0; r < count; ++r) {
+        uint32_t slot = (uint32_t)(slot_begin + r);
+        for (int i = 0; i < N; ++i) {
+            uint32_t w[4];
+            orc_draw(seed, (uint32_t)i >> 2, ORC_DOM_INIT, 0u, slot, w);
+            spins[r * N + i] = (uint8_t)orc_scale(w[i & 3], (uint32_t)q);
+        }
+    }
+}
+
+/* Heating runs: every replica in one of the q ground states, chosen uniformly
+ * (Sec. 5, Eq. 6).  Slot r takes word (r & 3) of counter (r >> 2, GROUND, 0, 0). */
+ORC_API void orc_init_ground(int q, int L, int64_t slot_begin, int64_t count, uint64_t seed, uint8_t *spins)
+{
+    int N = L * L;
+    for (int64_t r = 0; r < count; ++r) {
+        uint32_t slot = (uint32_t)(slot_begin + r);
+        uint32_t w[4];
+        orc_draw(seed, slot >> 2, ORC_DOM_GROUND, 0u, 0u, w);
+        uint8_t alpha = (uint8_t)orc_scale(w[slot & 3], (uint32_t)q);
+        for (int i = 0; i < N; ++i) spins[r * N + i] = alpha;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Resampling (Sec. 2, step 2).                                                */
+/* ------------------------------------------------------------------------- */
+enum { ORC_NEAREST_INT = 0, ORC_ROUND = 1 };
+
+/* Computes Q_i and the copy numbers r_j for the R_prev replicas with energies
+ * E[j], from beta_{i-1} to beta_i = beta_{i-1} + dbeta.
+ *
+ * The Boltzmann factors are evaluated relative to E_ref, the lowest energy for
+ * dbeta >= 0 and the highest for dbeta < 0, so that no factor overflows:
+ *   w_j = exp(-dbeta (E_j - E_ref)),  S = sum_j w_j (ascending j),
+ *   ln Q_i = -dbeta E_ref + ln(S / R_prev)          (= ln of the paper's Q_i),
+ *   rho_j = (R w_j) / S                              (= (R/R_{i-1}) tau_i(E_j)).
+ * reading: "nearest-integer" copy numbers draw r_j from the two integers
+ * nearest to rho_j with the mean kept exact: r_j = floor(rho_j) + [u_j <
+ * frac(rho_j) 2^32], u_j = word (j & 3) of counter (j >> 2, RESAMPLE, step, 0).
+ * ORC_ROUND instead takes the nearest integer, halves rounded up.
+ * rho_out (optional) receives rho_j.  Returns the new population size. */
+ORC_API int64_t orc_copy_numbers(int64_t R_prev, const int32_t *E, double dbeta, int64_t R_target,
+                                 int mode, uint32_t step, uint64_t seed, int32_t *r, double *lnQ,
+                                 double *rho_out)
+{
+    int32_t E_ref = E[0];
+    for (int64_t j = 1; j < R_prev; ++j) {
+        if (dbeta >= 0.0 ? (E[j] < E_ref) : (E[j] > E_ref)) E_ref = E[j];
+    }
+    double S = 0.0;
+    for (int64_t j = 0; j < R_prev; ++j) S += exp(-dbeta * (double)(E[j] - E_ref));
+    *lnQ = -dbeta * (double)E_ref + log(S / (double)R_prev);
+    int64_t total = 0;
+    for (int64_t j = 0; j < R_prev; ++j) {
+        double w = exp(-dbeta * (double)(E[j] - E_ref));
+        double rho = ((double)R_target * w) / S;
+        if (rho_out) rho_out[j] = rho;
+        double n = floor(rho);
+        double frac = rho - n;
+        int32_t up;
+        if (mode == ORC_ROUND) {
+            up = frac >= 0.5;
+        } else {
+            uint32_t u[4];
+            orc_draw(seed, (uint32_t)(j >> 2), ORC_DOM_RESAMPLE, step, 0u, u);
+            up = (double)u[j & 3] < frac * 4294967296.0;
+        }
+        r[j] = (int32_t)n + up;
+        total += r[j];
+    }
+    return total;
+}
+
+/* Children in ascending parent order: parent[sum_{l<j} r_l + c] = j, c < r_j. */
+ORC_API void orc_parents(int64_t R_prev, const int32_t *r, int32_t *parent)
+{
+    int64_t at = 0;
+    for (int64_t j = 0; j < R_prev; ++j)
+        for (int32_t c = 0; c < r[j]; ++c) parent[at++] = (int32_t)j;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Population estimators (Sec. 3, Eq. 4; Sec. 2 step 4).                       */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double beta, lnQ, lnZ, meanE, meanE2, C, meanM, S_f;
+    int64_t R, n_families, sumE, sumE2, sumMt;
+} orc_obs;
+
+/* Population averages over R replicas with energies E and largest-state
+ * occupations Mt at inverse temperature beta:
+ *   <E> = sum E / R, <E^2> = sum E^2 / R (integer sums, one division each),
+ *   C = beta^2 (<E^2> - <E>^2) / N           (fluctuation formula),
+ *   <M> = (q sum Mt - N R) / ((q-1) R)       (Eq. 5 averaged, Eq. 4).
+ * Family entropy (reading; the paper does not define it): with n_f the number
+ * of current replicas descending from initial replica f and nu_f = n_f / R,
+ * S_f = -sum_f nu_f ln nu_f, summed over ascending f. */
+static void orc_measure(int q, int N, int64_t R, const int32_t *E, const int32_t *Mt, double beta,
+                        const int32_t *anc, int64_t R0, orc_obs *o)
+{
+    int64_t sE = 0, sE2 = 0, sM = 0;
+    for (int64_t j = 0; j < R; ++j) {
+        sE += E[j];
+        sE2 += (int64_t)E[j] * (int64_t)E[j];
+        sM += Mt[j];
+    }
+    o->R = R;
+    o->sumE = sE; o->sumE2 = sE2; o->sumMt = sM;
+    o->beta = beta;
+    o->meanE = (double)sE / (double)R;
+    o->meanE2 = (double)sE2 / (double)R;
+    o->C = ((beta * beta) * (o->meanE2 - o->meanE * o->meanE)) / (double)N;
+    o->meanM = (double)((int64_t)q * sM - (int64_t)N * R) / ((double)(q - 1) * (double)R);
+    o->S_f = 0.0;
+    o->n_families = 0;
+    if (anc) {
+        int64_t *count = (int64_t *)calloc((size_t)R0, sizeof(int64_t));
+        for (int64_t j = 0; j < R; ++j) count[anc[j]] += 1;
+        double sf = 0.0;
+        for (int64_t f = 0; f < R0; ++f) {
+            if (count[f] == 0) continue;
+            double nu = (double)count[f] / (double)R;
+            sf -= nu * log(nu);
+            o->n_families += 1;
+        }
+        o->S_f = sf;
+        free(count);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* The PA driver (Sec. 2, steps 1-5).                                          */
+/* ------------------------------------------------------------------------- */
+enum { ORC_INIT_RANDOM = 0, ORC_INIT_GROUND = 1 };
+
+/* Runs K temperature steps over betas[0..K].  Step 0 is the initial
+ * population at betas[0] (no sweeps there); step i >= 1 resamples from
+ * betas[i-1] to betas[i], sweeps theta times at betas[i] and measures.
+ *   obs[0..K]          per-step estimators (orc_obs, see above);
+ *   hist (optional)    (K+1) x (2N+1) energy histograms, bin E + 2N;
+ *   spins/E/anc        final population, R_cap * N bytes / R_cap ints;
+ * ln Z_0 = N ln q for random starts (Sec. 6) and ln q - beta_0 E_0 with
+ * E_0 = -2N for ground-state starts (Sec. 6, Eqs. 7-8).
+ * Returns the final population size, or -1 if a population outgrew R_cap
+ * (outputs then hold the last complete step). */
+ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, int theta, int K,
+                        const double *betas, int mode, int init_mode, orc_obs *obs, int32_t *hist,
+                        uint8_t *spins_out, int32_t *E_out, int32_t *anc_out)
+{
+    int N = L * L;
+    uint8_t *cur = (uint8_t *)malloc((size_t)R_cap * N);
+    uint8_t *nxt = (uint8_t *)malloc((size_t)R_cap * N);
+    int32_t *E = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *Mt = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *anc2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *r = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int64_t Rc = R;
+    int64_t result = R;
+
+    if (init_mode == ORC_INIT_GROUND)
+        orc_init_ground(q, L, 0, R, seed, cur);
+    else
+        orc_init_random(q, L, 0, R, seed, cur);
+    for (int64_t j = 0; j < R; ++j) {
+        E[j] = (int32_t)orc_energy(L, cur + j * N);
+        Mt[j] = (int32_t)orc_max_count(q, L, cur + j * N);
+        anc[j] = (int32_t)j;
+    }
+    double lnZ;
+    if (init_mode == ORC_INIT_GROUND)
+        lnZ = log((double)q) - betas[0] * (double)(-2 * N);
+    else
+        lnZ = (double)N * log((double)q);
+    orc_measure(q, N, Rc, E, Mt, betas[0], anc, R, &obs[0]);
+    obs[0].lnQ = 0.0;
+    obs[0].lnZ = lnZ;
+    if (hist) {
+        memset(hist, 0, sizeof(int32_t) * (size_t)(2 * N + 1));
+        for (int64_t j = 0; j < Rc; ++j) hist[E[j] + 2 * N] += 1;
+    }
+
+    for (int i = 1; i <= K; ++i) {
+        double dbeta = betas[i] - betas[i - 1];
+        double lnQ;
+        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, r, &lnQ, NULL);
+        if (Rn > R_cap || Rn <= 0) {
+            result = -1;
+            break;
+        }
+        orc_parents(Rc, r, parent);
+        for (int64_t t = 0; t < Rn; ++t) {
+            memcpy(nxt + t * N, cur + (int64_t)parent[t] * N, (size_t)N);
+            anc2[t] = anc[parent[t]];
+        }
+        uint8_t *tmp = cur; cur = nxt; nxt = tmp;
+        int32_t *ta = anc; anc = anc2; anc2 = ta;
+        Rc = Rn;
+
+        uint32_t thr[9];
+        orc_thresholds(betas[i], thr);
+        for (int64_t t = 0; t < Rc; ++t) {
+            orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed);
+            E[t] = (int32_t)orc_energy(L, cur + t * N);
+            Mt[t] = (int32_t)orc_max_count(q, L, cur + t * N);
+        }
+        lnZ = lnZ + lnQ;
+        orc_measure(q, N, Rc, E, Mt, betas[i], anc, R, &obs[i]);
+        obs[i].lnQ = lnQ;
+        obs[i].lnZ = lnZ;
+        if (hist) {
+            int32_t *h = hist + (int64_t)i * (2 * N + 1);
+            memset(h, 0, sizeof(int32_t) * (size_t)(2 * N + 1));
+            for (int64_t j = 0; j < Rc; ++j) h[E[j] + 2 * N] += 1;
+        }
+        result = Rc;
+    }
+    if (spins_out) memcpy(spins_out, cur, (size_t)Rc * N);
+    if (E_out) memcpy(E_out, E, sizeof(int32_t) * (size_t)Rc);
+    if (anc_out) memcpy(anc_out, anc, sizeof(int32_t) * (size_t)Rc);
+    free(cur); free(nxt); free(E); free(Mt); free(anc); free(anc2); free(r); free(parent);
+    return result;
+}
+
+ORC_API int orc_obs_size(void) { return (int)sizeof(orc_obs); }
+
+/* ------------------------------------------------------------------------- */
+/* Exact results on tiny lattices (pins for the oracle itself).               */
+/* ------------------------------------------------------------------------- */
+
+/* Density of states g(E) by visiting all q^N configurations; g[E + 2N].
+ * Any L >= 2 (odd L allowed).  Returns 0, or -1 if q^N exceeds 2^40. */
+ORC_API int orc_density_of_states(int q, int L, uint64_t *g)
+{
+    int N = L * L;
+    double states = pow((double)q, (double)N);
+    if (states > 1099511627776.0) return -1;
+    for (int k = 0; k <= 2 * N; ++k) g[k] = 0;
+    uint8_t s[64];
+    memset(s, 0, sizeof(s));
+    for (;;) {
+        int64_t e = orc_energy(L, s);
+        g[e + 2 * N] += 1;
+        int i = 0;
+        while (i < N) {
+            s[i] += 1;
+            if (s[i] < q) break;
+            s[i] = 0;
+            ++i;
+        }
+        if (i == N) break;
+    }
+    return 0;
+}
+
+/* Exact transition matrix of one Metropolis attempt at `site` (= y L + x) of an
+ * L x L lattice, over all q^N configurations (index = sum_i s_i q^i).  The
+ * probabilities are read off orc_metropolis_decide itself: the proposal classes
+ * {u0 : floor(u0 (q-1)/2^32) = m} are located by bisection on u0, and for each
+ * class the number of accepting u1 values by bisection on u1, so a mistake in
+ * the update rule shows up in the matrix.  P is (q^N)^2 row-major, P[a][b] =
+ * Prob(a -> b).  Returns -1 if q^N > 4096. */
+ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
+{
+    int N = L * L;
+    int64_t n = 1;
+    for (int i = 0; i < N; ++i) n *= q;
+    if (n > 4096) return -1;
+    uint32_t thr[9];
+    orc_thresholds(beta, thr);
+    memset(P, 0, sizeof(double) * (size_t)(n * n));
+    int x = site % L, y = site / L;
+    for (int64_t a = 0; a < n; ++a) {
+        uint8_t s[64];
+        int64_t t = a;
+        for (int i = 0; i < N; ++i) { s[i] = (uint8_t)(t % q); t /= q; }
+        int nb[4];
+        orc_neighbours(L, s, x, y, nb);
+        int cur = s[site];
+        /* class boundaries lo[m] = smallest u0 with scale(u0, q-1) >= m */
+        for (int m = 0; m < q - 1; ++m) {
+            uint64_t lo_m, lo_next;
+            {
+                uint64_t lo = 0, hi = 4294967296ull;
+                while (lo < hi) {
+                    uint64_t mid = (lo + hi) / 2;
+                    if (orc_scale((uint32_t)mid, (uint32_t)(q - 1)) >= (uint32_t)m) hi = mid; else lo = mid + 1;
+                }
+                lo_m = lo;
+            }
+            {
+                uint64_t lo = 0, hi = 4294967296ull;
+                while (lo < hi) {
+                    uint64_t mid = (lo + hi) / 2;
+                    if (orc_scale((uint32_t)mid, (uint32_t)(q - 1)) >= (uint32_t)(m + 1)) hi = mid; else lo = mid + 1;
+                }
+                lo_next = lo;
+            }
+            double p_class = (double)(lo_next - lo_m) / 4294967296.0;
+            uint32_t u0 = (uint32_t)lo_m;
+            /* accepted iff the state changes; acceptance is u1 < T, so find the
+             * smallest rejecting u1 */
+            uint64_t lo = 0, hi = 4294967296ull;
+            while (lo < hi) {
+                uint64_t mid = (lo + hi) / 2;
+                if (orc_metropolis_decide(q, cur, nb, u0, (uint32_t)mid, thr) == cur) hi = mid; else lo = mid + 1;
+            }
+            double p_acc = (double)lo / 4294967296.0;
+            int prop = cur;
+            if (lo > 0) prop = orc_metropolis_decide(q, cur, nb, u0, 0u, thr);
+            int64_t b = a;
+            if (prop != cur) {
+                int64_t place = 1;
+                for (int i = 0; i < site; ++i) place *= q;
+                b = a + (int64_t)(prop - cur) * place;
+            }
+            P[a * n + b] += p_class * p_acc;
+            P[a * n + a] += p_class * (1.0 - p_acc);
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reweighting as a function of dbeta (Sec. 2, step 2), for the differentiable */
+/* form:  ln Q(dbeta) = ln( sum_j exp(-dbeta E_j) / R ),                        */
+/*   d ln Q / d dbeta = -<E>_tau,   <O>_tau = sum_j O_j tau_j / R,              */
+/*   d <O>_tau / d dbeta = -(<O E>_tau - <O>_tau <E>_tau),                      */
+/* with tau_j = exp(-dbeta E_j) / Q.  Sums run over ascending j, shifted by     */
+/* E_ref as in orc_copy_numbers.                                                */
+/* ------------------------------------------------------------------------- */
+ORC_API void orc_reweight(int64_t R, const int32_t *E, const double *O, double dbeta, double *lnQ,
+                          double *meanE_tau, double *meanO_tau, double *covOE_tau)
+{
+    int32_t E_ref = E[0];
+    for (int64_t j = 1; j < R; ++j)
+        if (dbeta >= 0.0 ? (E[j] < E_ref) : (E[j] > E_ref)) E_ref = E[j];
+    double S = 0.0, SE = 0.0, SO = 0.0, SOE = 0.0;
+    for (int64_t j = 0; j < R; ++j) {
+        double w = exp(-dbeta * (double)(E[j] - E_ref));
+        S += w;
+        SE += w * (double)E[j];
+        if (O) {
+            SO += w * O[j];
+            SOE += w * O[j] * (double)E[j];
+        }
+    }
+    *lnQ = -dbeta * (double)E_ref + log(S / (double)R);
+    *meanE_tau = SE / S;
+    if (O) {
+        *meanO_tau = SO / S;
+        *covOE_tau = SOE / S - (SO / S) * (SE / S);
+    }
+}

@@ -1,0 +1,376 @@
+"""Pins for the CPU oracle against facts it does not compute itself.
+
+The oracle (oracle/pa_oracle.c) is the reference every GPU parity test trusts,
+so it is checked here against published known-answer vectors, closed forms
+from the paper and from the exact Ising solution, exact enumeration, detailed
+balance of the exact transition matrix, and invariants of the resampling step.
+"""
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10
+# --------------------------------------------------------------------------
+def _kat_rows():
+    rows = []
+    with open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t, 16) for t in line.split()]
+            rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,expect", _kat_rows())
+def test_philox_known_answers(ctr, key, expect):
+    assert [int(x) for x in oracle.philox(ctr, key)] == expect
+
+
+_TRITON_SCRIPT = r"""
+import os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+@triton.jit
+def k(c_ptr, out_ptr, seed, BLOCK: tl.constexpr):
+    i = tl.arange(0, BLOCK)
+    c0 = tl.load(c_ptr + 4 * i + 0); c1 = tl.load(c_ptr + 4 * i + 1)
+    c2 = tl.load(c_ptr + 4 * i + 2); c3 = tl.load(c_ptr + 4 * i + 3)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+    tl.store(out_ptr + 4 * i + 0, a); tl.store(out_ptr + 4 * i + 1, b)
+    tl.store(out_ptr + 4 * i + 2, c); tl.store(out_ptr + 4 * i + 3, d)
+ctr = np.fromfile(sys.argv[1], dtype=np.uint32)
+seed = int(sys.argv[2])
+c = torch.from_numpy(ctr.view(np.int32).copy())
+out = torch.zeros_like(c)
+k[(1,)](c, out, seed, BLOCK=ctr.size // 4)
+out.numpy().view(np.uint32).tofile(sys.argv[3])
+"""
+
+
+def test_philox_matches_triton_library(tmp_path):
+    """An independent library implementation (triton.language.philox, run by
+    its CPU interpreter) agrees on 256 random counters."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2**32, size=(256, 4), dtype=np.uint64).astype(np.uint32)
+    seed = 0x1234_5678_9ABC_DEF1
+    cf, of = tmp_path / "c.bin", tmp_path / "o.bin"
+    ctr.tofile(cf)
+    script = tmp_path / "t.py"
+    script.write_text(_TRITON_SCRIPT)
+    res = subprocess.run([sys.executable, str(script), str(cf), str(seed), str(of)],
+                         capture_output=True, text=True, timeout=600)
+    if res.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + res.stderr[-200:])
+    got = np.fromfile(of, dtype=np.uint32).reshape(256, 4)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(256):
+        assert list(oracle.philox(ctr[i], key)) == list(got[i])
+
+
+# --------------------------------------------------------------------------
+# Hamiltonian (Sec. 3, Eq. 3) and exact enumeration
+# --------------------------------------------------------------------------
+def _kaufman_lnZ(K, m, n):
+    """ln Z of the Ising model sum exp(K sum_<ij> s_i s_j) on an m x n torus,
+    B. Kaufman, Phys. Rev. 76, 1232 (1949)."""
+    def gamma(l):
+        if l == 0:
+            return 2 * K + math.log(math.tanh(K))
+        return math.acosh(math.cosh(2 * K) / math.tanh(2 * K) - math.cos(math.pi * l / n))
+    z = [1.0, 1.0, 1.0, 1.0]
+    for r in range(n):
+        g1, g0 = gamma(2 * r + 1), gamma(2 * r)
+        z[0] *= 2 * math.cosh(m * g1 / 2)
+        z[1] *= 2 * math.sinh(m * g1 / 2)
+        z[2] *= 2 * math.cosh(m * g0 / 2)
+        z[3] *= 2 * math.sinh(m * g0 / 2)
+    return math.log(0.5) + (m * n / 2) * math.log(2 * math.sinh(2 * K)) + math.log(sum(z))
+
+
+def _lnZ_from_dos(g, N, beta):
+    E = np.arange(-2 * N, 1, dtype=np.float64)
+    gg = g.astype(np.float64)
+    a = np.where(gg > 0, np.log(np.maximum(gg, 1)) - beta * E, -np.inf)
+    mx = a.max()
+    return mx + math.log(np.exp(a - mx).sum())
+
+
+def _mean_E_from_dos(g, N, beta):
+    E = np.arange(-2 * N, 1, dtype=np.float64)
+    gg = g.astype(np.float64)
+    a = np.where(gg > 0, np.log(np.maximum(gg, 1)) - beta * E, -np.inf)
+    w = np.exp(a - a.max())
+    return float((w * E).sum() / w.sum())
+
+
+@pytest.mark.parametrize("L", [3, 4])
+@pytest.mark.parametrize("beta", [0.3, 0.9, 1.7])
+def test_q2_partition_function_matches_kaufman(L, beta):
+    """q = 2 Potts is Ising with K = beta/2 shifted by e^{beta N}:
+    delta(s,s') = (1 + sigma sigma')/2, so Z_Potts(beta) = e^{beta N} Z_Ising(beta/2)."""
+    N = L * L
+    g = oracle.density_of_states(2, L)
+    assert _lnZ_from_dos(g, N, beta) == pytest.approx(beta * N + _kaufman_lnZ(beta / 2, L, L), rel=1e-12)
+
+
+@pytest.mark.parametrize("q,L", [(5, 3), (3, 4), (4, 3), (2, 4)])
+def test_density_of_states_closed_forms(q, L):
+    N = L * L
+    g = oracle.density_of_states(q, L)
+    assert int(g.sum()) == q ** N
+    # ground states: the q uniform configurations, E_0 = -2N (Sec. 6, Eqs. 7-8)
+    assert int(g[0]) == q
+    # nothing between E_0 and one flipped spin, which breaks its 4 bonds
+    assert int(g[1:4].sum()) == 0
+    assert int(g[4]) == q * N * (q - 1)
+    # at beta = 0 every bond is satisfied with probability 1/q: <E> = -2N/q
+    E = np.arange(-2 * N, 1)
+    assert float((g.astype(np.float64) * E).sum()) == pytest.approx(-2 * N * q ** N / q, rel=1e-14)
+    # relabelling a state leaves H unchanged: g is symmetric under nothing
+    # simpler, but E is never positive and -2N is reached
+    assert g[-1] >= 0
+
+
+def test_energy_and_max_count_small_cases():
+    s = np.zeros((4, 4), np.uint8)
+    assert oracle.energy(s) == -32
+    assert oracle.max_count(3, s) == 16
+    s[1, 2] = 2
+    assert oracle.energy(s) == -28
+    s[1, 3] = 2  # a domino of equal flipped spins breaks 6 bonds
+    assert oracle.energy(s) == -26
+    s[1, 3] = 1  # unequal neighbours inside the domino break 7
+    assert oracle.energy(s) == -25
+    assert oracle.max_count(3, s) == 14
+    chk = (np.add.outer(np.arange(4), np.arange(4)) % 2).astype(np.uint8)
+    assert oracle.energy(chk) == 0  # checkerboard: no bond satisfied
+    # L = 2: both horizontal bonds of a row join the same two sites
+    assert oracle.energy(np.zeros((2, 2), np.uint8)) == -8
+
+
+# --------------------------------------------------------------------------
+# Metropolis update: exact detailed balance (Sec. 2 step 3)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [2, 3, 4])
+@pytest.mark.parametrize("beta", [0.4, 1.3])
+def test_site_kernels_satisfy_detailed_balance(q, beta):
+    L = 2
+    N = L * L
+    n = q ** N
+    E = np.zeros(n)
+    for a in range(n):
+        s = np.array([(a // q ** i) % q for i in range(N)], np.uint8).reshape(L, L)
+        E[a] = oracle.energy(s)
+    pi = np.exp(-beta * (E - E.min()))
+    pi /= pi.sum()
+    order = [0, 3, 1, 2]  # colour 0 ((x+y) even) row-major, then colour 1
+    sweep = np.eye(n)
+    for site in order:
+        P = oracle.site_matrix(q, L, site, beta)
+        assert np.allclose(P.sum(axis=1), 1.0, atol=1e-14)
+        flow = pi[:, None] * P
+        # the 32-bit quantisation of proposals and thresholds bounds the asymmetry
+        assert np.max(np.abs(flow - flow.T)) <= 1e-8 * pi.max()
+        sweep = sweep @ P
+    assert np.max(np.abs(pi @ sweep - pi)) < 1e-8
+    # the chain moves: the sweep matrix is not the identity
+    assert np.min(np.diag(sweep)) < 0.999
+
+
+def test_thresholds_are_quantised_boltzmann_factors():
+    for beta in (0.0, 0.37, 1.426, 3.0):
+        t = oracle.thresholds(beta)
+        for d in range(-4, 5):
+            if d <= 0:
+                assert t[d + 4] == 0xFFFFFFFF
+            else:
+                exact = math.exp(-beta * d) * 2**32
+                assert t[d + 4] == min(2**32 - 1, math.floor(exact))
+
+
+def test_proposal_never_repeats_current_state():
+    thr = oracle.thresholds(0.0)
+    rng = np.random.default_rng(3)
+    for q in (2, 3, 10, 20):
+        for _ in range(200):
+            cur = int(rng.integers(q))
+            u0 = int(rng.integers(2**32))
+            new = oracle.metropolis_decide(q, cur, [cur, cur, cur, cur], u0, 0, thr)
+            assert new != cur and 0 <= new < q
+
+
+# --------------------------------------------------------------------------
+# Initial populations
+# --------------------------------------------------------------------------
+def test_random_init_is_uniform_and_at_beta_zero():
+    q, L, R = 10, 16, 4000
+    s = oracle.init_random(q, L, 0, R, seed=1)
+    counts = np.bincount(s.ravel(), minlength=q)
+    expect = s.size / q
+    chi2 = float(((counts - expect) ** 2 / expect).sum())
+    assert chi2 < 40.0  # 9 degrees of freedom; p < 1e-5 beyond this
+    N = L * L
+    E = np.array([oracle.energy(x) for x in s])
+    sigma = math.sqrt(2 * N * (1 / q) * (1 - 1 / q))  # bonds are pairwise independent
+    assert abs(E.mean() + 2 * N / q) < 5 * sigma / math.sqrt(R)
+    # slots are independent streams: a range call equals the full call
+    assert np.array_equal(oracle.init_random(q, L, 1234, 7, seed=1), s[1234:1241])
+
+
+def test_ground_init_uniform_over_ground_states():
+    q, L, R = 6, 8, 6000
+    s = oracle.init_ground(q, L, 0, R, seed=5)
+    assert all(oracle.energy(x) == -2 * L * L for x in s[:50])
+    alpha = s[:, 0, 0]
+    assert np.all(s == alpha[:, None, None])
+    counts = np.bincount(alpha, minlength=q)
+    chi2 = float(((counts - R / q) ** 2 / (R / q)).sum())
+    assert chi2 < 30.0
+
+
+# --------------------------------------------------------------------------
+# Resampling (Sec. 2 step 2, Eq. 2)
+# --------------------------------------------------------------------------
+def test_equal_energies_give_exact_Q_and_single_copies():
+    R, N = 500, 64
+    E = np.full(R, -2 * N, np.int32)  # a ground-state population
+    for dbeta in (0.01, 0.5, -0.2):
+        r, lnQ, Rn, rho = oracle.copy_numbers(E, dbeta, R, oracle.NEAREST_INT, 3, 9)
+        assert lnQ == -dbeta * (-2 * N)
+        assert np.all(rho == 1.0) and np.all(r == 1) and Rn == R
+
+
+def test_copy_numbers_properties():
+    rng = np.random.default_rng(11)
+    R = 4000
+    E = rng.integers(-400, -100, size=R).astype(np.int32)
+    dbeta = 0.02
+    r, lnQ, Rn, rho = oracle.copy_numbers(E, dbeta, R, oracle.NEAREST_INT, 5, 1)
+    assert rho.sum() == pytest.approx(R, rel=1e-12)
+    # the two nearest integers only
+    assert np.all((r == np.floor(rho)) | (r == np.floor(rho) + 1))
+    # log-sum-exp through numpy's own reduction
+    Emin = E.min()
+    ref = -dbeta * Emin + math.log(np.exp(-dbeta * (E - Emin).astype(np.float64)).sum() / R)
+    assert lnQ == pytest.approx(ref, rel=1e-13)
+    # deterministic rounding: nearest integer with halves up
+    r2, _, _, rho2 = oracle.copy_numbers(E, dbeta, R, oracle.ROUND, 5, 1)
+    assert np.array_equal(r2, np.floor(rho2 + 0.5).astype(np.int32))
+    # the parent map lists j exactly r_j times, in ascending order
+    par = oracle.parents(r)
+    assert par.size == Rn and np.array_equal(np.bincount(par, minlength=R), r)
+    assert np.all(np.diff(par) >= 0)
+
+
+def test_stochastic_rounding_is_unbiased():
+    """E[r_j] = rho_j: average over many steps (fresh counters per step)."""
+    rng = np.random.default_rng(2)
+    R = 64
+    E = rng.integers(-60, -20, size=R).astype(np.int32)
+    acc = np.zeros(R)
+    steps = 3000
+    for step in range(1, steps + 1):
+        r, _, _, rho = oracle.copy_numbers(E, 0.05, R, oracle.NEAREST_INT, step, 4)
+        acc += r
+    frac = rho - np.floor(rho)
+    sd = np.sqrt(frac * (1 - frac) / steps) + 1e-12
+    assert np.all(np.abs(acc / steps - rho) < 6 * sd + 1e-12)
+
+
+def test_reweight_derivatives():
+    rng = np.random.default_rng(5)
+    # a population-like spread of energies (width ~ sqrt(N) for N = 256)
+    E = np.rint(rng.normal(-300.0, 12.0, size=3000)).astype(np.int32)
+    O = rng.normal(size=3000)
+    d = 0.013
+    lnQ, mE, mO, cov = oracle.reweight(E, d, O)
+    h = 1e-4
+    lp = oracle.reweight(E, d + h, O)
+    lm = oracle.reweight(E, d - h, O)
+    assert (lp[0] - lm[0]) / (2 * h) == pytest.approx(-mE, rel=1e-6)
+    assert (lp[2] - lm[2]) / (2 * h) == pytest.approx(-cov, rel=1e-5, abs=1e-9)
+    l0 = oracle.reweight(E, 0.0, O)
+    assert l0[0] == 0.0
+    assert l0[1] == pytest.approx(E.mean(), rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# PA as a whole against exact enumeration (Sec. 2 Eq. 2, Sec. 6)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("q,L", [(3, 4), (5, 3)])
+def test_pa_free_energy_and_energy_match_exact_enumeration(q, L):
+    """PA estimates of ln Z(beta) and <E>(beta) agree with exact values from
+    the density of states within 5 standard errors (over seeds).  L = 3 is odd:
+    the colour-ordered in-place sweep is still a sequence of single-site
+    Metropolis updates and keeps the Boltzmann distribution stationary."""
+    N = L * L
+    g = oracle.density_of_states(q, L)
+    K = 16
+    betas = np.linspace(0.0, 1.6, K + 1)
+    R = 6000
+    lnz, me = [], []
+    for seed in range(1, 7):
+        out = oracle.run(q, L, R, seed, 5, betas, want_state=False)
+        lnz.append(out["lnZ"])
+        me.append(out["meanE"])
+    lnz, me = np.array(lnz), np.array(me)
+    for i in (0, 4, 8, 12, 16):
+        ex = _lnZ_from_dos(g, N, betas[i])
+        se = lnz[:, i].std(ddof=1) / math.sqrt(lnz.shape[0])
+        if i == 0:
+            assert lnz[0, 0] == pytest.approx(N * math.log(q), rel=1e-15)
+            continue
+        assert abs(lnz[:, i].mean() - ex) < 5 * se + 2e-3, (i, lnz[:, i].mean(), ex, se)
+        exE = _mean_E_from_dos(g, N, betas[i])
+        seE = me[:, i].std(ddof=1) / math.sqrt(me.shape[0])
+        assert abs(me[:, i].mean() - exE) < 5 * seE + 2e-2, (i, me[:, i].mean(), exE, seE)
+
+
+def test_heating_run_recovers_infinite_temperature_free_energy():
+    """Ground-state start at beta = 3 with the zero-temperature normalisation
+    ln Z = ln q - beta E_0 (Sec. 6, Eqs. 7-8), negative dbeta (Sec. 5),
+    arrives at ln Z(0) = N ln q."""
+    q, L = 3, 4
+    N = L * L
+    g = oracle.density_of_states(q, L)
+    betas = np.linspace(3.0, 0.0, 31)
+    ends = []
+    for seed in range(1, 5):
+        out = oracle.run(q, L, 4000, seed, 5, betas, init_mode=oracle.INIT_GROUND, want_state=False)
+        assert out["lnZ"][0] == math.log(q) + 2 * N * 3.0
+        ends.append(out["lnZ"][-1])
+    # the normalisation itself is exact up to the excited states at beta = 3
+    assert _lnZ_from_dos(g, N, 3.0) == pytest.approx(math.log(q) + 2 * N * 3.0, abs=1e-3)
+    assert abs(np.mean(ends) - N * math.log(q)) < 0.05
+
+
+def test_run_invariants_and_families():
+    q, L, R = 10, 8, 800
+    betas = np.linspace(0.0, 1.5, 21)
+    out = oracle.run(q, L, R, 3, 4, betas, want_hist=True)
+    N = L * L
+    assert out["S_f"][0] == pytest.approx(math.log(R), rel=1e-14)
+    assert out["n_families"][0] == R
+    assert np.all(np.diff(out["n_families"]) <= 0)  # families never come back
+    assert np.all(out["hist"].sum(axis=1) == out["R"])
+    assert np.all(np.abs(out["R"] - R) < 60)
+    # ln Z is the running sum of ln Q on top of N ln q (Eq. 2)
+    assert np.allclose(out["lnZ"], N * math.log(q) + np.cumsum(out["lnQ"]), rtol=0, atol=1e-9)
+    # final energies are the energies of the final spins
+    for j in range(0, out["R_final"], 97):
+        assert oracle.energy(out["spins"][j]) == out["E"][j]
+    # past beta_t = ln(1 + sqrt 10) = 1.426 order grows (Eq. 5), even though a
+    # fast cooling stays partly metastable (Sec. 4)
+    assert out["meanM"][-1] > 3 * out["meanM"][0]
