@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: population annealing of the 2D q-state Potts model on GB300.
+
+One benchmark step is one PA temperature step over the whole population
+(resampling with the replica gather, theta checkerboard Metropolis sweeps,
+measurements), the hot path of Sec. 2 of arXiv:1704.01888.  The workload is
+plain PA with q = 10, L = 64, R = 100000, theta = 10, beta from 0 to 1.6 in
+200 equal steps; warm-up steps are the first steps of that schedule and the
+timed steps follow (past step 200 the same spacing continues).
+
+Prints one JSON line.  --impl reference times the CPU oracle instead (the
+only reference this method has), on a bounded sample of the same workload.
+Under torchrun each rank runs its own independent population (seed + rank);
+value = attempts of all ranks / max over ranks of the timed span.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1704_01888_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "spin-flip attempts/ns & PA steps/s, q=10 L=64 R=1e5; batched vs plain, %roofline"
+UNIT = "attempts/ns"
+# Algorithmic integer operations per Metropolis attempt: half a Philox4x32-10
+# call (10 rounds of 2 wide multiplies + 2 three-input xors = 40 per call, 20
+# per attempt), the proposal, the neighbour comparison and the threshold test
+# (about 30 more) -- the per-attempt figure the issue roofline is taken over.
+OPS_PER_ATTEMPT = 50
+LANES_PER_SM_PER_CLK = 128  # 4 schedulers x 32 lanes issue one integer op each per clock
+PA_OBS_BYTES = 104
+DEVSTATE_BYTES = 48
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=197)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c5"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(name):
+    return {"c1": wl.C1, "c2": wl.C2, "c5": wl.C5}[name]
+
+
+def _betas(w, n):
+    """beta_i = beta_end * i / K for i = 0..n (continues past K at the same spacing)."""
+    return np.array([w.beta_end * i / w.K for i in range(n + 1)], dtype=np.float64)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _sweep_traffic_per_replica():
+    """DRAM bytes per replica per sweep launch from the committed ncu summary,
+    valid only while the sweep kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = open(os.path.join(ROOT, "paper_1704_01888_gb300", "csrc", "pa_sweep.cu"), "rb").read()
+    if rec.get("pa_sweep_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("dram_bytes_per_replica")
+
+
+def _cpu_baseline(w, R_sample=1000, steps=3):
+    """The oracle as it stands, single-threaded, on R_sample replicas for the
+    first `steps` temperature steps of the same workload."""
+    import oracle
+
+    oracle.build()
+    b = _betas(w, steps)
+    t0 = time.perf_counter()
+    out = oracle.run(w.q, w.L, R_sample, w.seed, w.theta, b, want_state=False)
+    dt = time.perf_counter() - t0
+    attempts = int(sum(out["R"][1:]) * w.N * w.theta)
+    return {"value": attempts / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{w.name} with R={R_sample} replicas, init + {steps} steps, single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    w = _workload(args.workload)
+    R_sample = 64 if w.N >= 16384 else 256
+    W, K = args.warmup, args.steps
+    bw = _betas(w, W)
+    ball = _betas(w, W + K)
+    t0 = time.perf_counter()
+    oracle.run(w.q, w.L, R_sample, w.seed, w.theta, bw, want_state=False)
+    t1 = time.perf_counter()
+    out = oracle.run(w.q, w.L, R_sample, w.seed, w.theta, ball, want_state=False)
+    t2 = time.perf_counter()
+    timed = (t2 - t1) - (t1 - t0)
+    attempts = int(sum(out["R"][W + 1:]) * w.N * w.theta)
+    value = attempts / (timed * 1e9)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": timed * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "q": w.q, "L": w.L, "R": w.R, "theta": w.theta, "sample_R": R_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{w.name} with R={R_sample} replicas per step, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1704_01888_gb300 as pa
+    from paper_1704_01888_gb300 import build as pabuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or not os.path.exists(pa.LIB_PATH):
+        pabuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+
+    w = _workload(args.workload)
+    W, K = args.warmup, args.steps
+    betas = _betas(w, W + K)
+    params = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed + rank, track_families=w.track_families)
+    stream = torch.cuda.current_stream()
+
+    pop = pa.Population(params)
+    for i in range(1, W + 1):
+        pop.resample(betas[i] - betas[i - 1], i)
+        pop.sweep(betas[i], w.theta, i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    pop.profile(True)
+    launches0 = pa.kernel_launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        start.record(stream)
+        for i in range(W + 1, W + K + 1):
+            pop.resample(betas[i] - betas[i - 1], i)
+            pop.sweep(betas[i], w.theta, i)
+        stop.record(stream)
+        stop.synchronize()
+    launches = pa.kernel_launch_count() - launches0
+    elapsed_ms = start.elapsed_time(stop)
+    prof = pop.profile_read()
+    hist = pop.history(K)
+    R_steps = [h["R"] for h in hist]
+    attempts = int(sum(R_steps)) * w.N * w.theta
+    final_obs = hist[-1]
+    pop.close()
+
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        a = torch.tensor([attempts], dtype=torch.float64, device="cuda")
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        elapsed_ms, total_attempts = float(t.item()), float(a.item())
+    else:
+        total_attempts = float(attempts)
+
+    value = total_attempts / (elapsed_ms * 1e6)
+    ms_per_step = elapsed_ms / K
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (the fused gather + sweeps + measurement)
+    sweep_ms, sweep_n = prof["sweep"]
+    sweep_avg_s = sweep_ms / sweep_n / 1e3
+    per_launch_attempts = attempts / sweep_n
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = _peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    achieved = OPS_PER_ATTEMPT * per_launch_attempts / sweep_avg_s / 1e12
+    peak = sms * LANES_PER_SM_PER_CLK * f_max / 1e12
+    tpr = _sweep_traffic_per_replica()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": (tpr * per_launch_attempts / (w.N * w.theta)) if tpr else None,
+                "kernel": "k_sweep_words", "ops_per_attempt": OPS_PER_ATTEMPT,
+                "kernel_ms_avg": sweep_avg_s * 1e3, "kernel_share": sweep_ms / elapsed_ms,
+                "peak_basis": f"{sms} SMs x {LANES_PER_SM_PER_CLK} lanes x {f_max / 1e6:.0f} MHz (max SM clock)"}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (sms * LANES_PER_SM_PER_CLK * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(pa, w, params, betas, W, K, rank, world)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = _cpu_baseline(w)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "q": w.q, "L": w.L, "R": w.R, "theta": w.theta,
+                   "beta": f"0 -> {w.beta_end} in {w.K} equal steps (timed steps {W + 1}..{W + K})",
+                   "parallelism": f"independent populations x{world}",
+                   "l2": f"inputs larger than L2: 2 x {w.R * w.N / 1e6:.0f} MB spin buffers",
+                   "launch": None},
+        "pa_steps_per_s": K / (elapsed_ms / 1e3),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "final": {"beta": final_obs["beta"], "lnZ": final_obs["lnZ"], "meanE_per_site": final_obs["meanE"] / w.N,
+                  "R": final_obs["R"]},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _e2e(pa, w, params, betas, W, K, rank, world):
+    """The same metric through the public API as a user drives it: each step
+    resamples with a host read of ln Q and R_i, sweeps, and reads the step's
+    estimators and energy histogram into host memory."""
+    import torch
+
+    pop = pa.Population(params)
+    for i in range(1, W + 1):
+        pop.resample(betas[i] - betas[i - 1], i)
+        pop.sweep(betas[i], w.theta, i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    attempts = 0
+    t0 = time.perf_counter()
+    for i in range(W + 1, W + K + 1):
+        _, R_i = pop.resample(betas[i] - betas[i - 1], i, sync=True)
+        pop.sweep(betas[i], w.theta, i)
+        obs, hist = pop.observables(with_hist=True)
+        attempts += obs["R"] * w.N * w.theta
+    dt = time.perf_counter() - t0
+    pop.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        a = torch.tensor([attempts], dtype=torch.float64, device="cuda")
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        dt, attempts = float(t.item()), float(a.item())
+    d2h = DEVSTATE_BYTES + DEVSTATE_BYTES + PA_OBS_BYTES + 4 * (2 * w.N + 1)
+    return {"value": attempts / (dt * 1e9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+            "note": "population generated on the device from the seed; per step beta and dbeta travel as "
+                    "kernel arguments; per step the host reads ln Q, R_i, the estimators and the histogram"}
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

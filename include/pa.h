@@ -1,0 +1,210 @@
+/*
+ * pa.h -- C ABI of the GB300 (sm_103a) population-annealing library for the
+ * two-dimensional q-state Potts model.
+ *
+ * The method is population annealing (PA) as defined in Barash, Weigel, Shchur
+ * & Janke, "Exploring first-order phase transitions with population annealing"
+ * (arXiv:1704.01888):
+ *   Sec. 2, steps 1-5    the PA loop: start an equilibrium population at beta_0,
+ *                        resample it to beta_i with the normalised Boltzmann
+ *                        factors tau_i(E_j), update every replica by theta
+ *                        Metropolis rounds at beta_i, measure population
+ *                        averages, repeat;
+ *   Sec. 2, Eq. 2        -beta_i F = ln Z_{beta_0} + sum_{m<=i} ln Q_m;
+ *   Sec. 3, Eqs. 3-5     H = -sum_<ij> delta(s_i, s_j) on the periodic square
+ *                        lattice, population averages, magnetisation;
+ *   Sec. 5, Eq. 6        ground-state starts for heating runs (negative dbeta);
+ *   Sec. 6, Eqs. 7-8     Z_{beta_0 = 0} = q^N and Z_{beta -> inf} = q e^{-beta E_0}.
+ *
+ * Conventions shared by every entry point
+ *   - Spins take the values 0..q-1 (the paper's 1..q shifted by one).  Host
+ *     copies use the canonical layout [replica][y][x], one byte per spin.
+ *   - A context owns all of its device memory and runs all of its work on the
+ *     CUDA stream given at creation (a cudaStream_t passed as void*, NULL for
+ *     the legacy default stream).  Unless stated otherwise a call only enqueues
+ *     work and returns; calls that hand results to host memory synchronise that
+ *     stream first.
+ *   - Host pointers passed in are read (inputs) or written (outputs) during the
+ *     call only; the library keeps no reference to them.
+ *   - Every call returns a pa_status.  Nothing aborts the process.  A call that
+ *     fails leaves the context at its last complete temperature step.
+ *   - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *     the 64-bit seed and a counter made of (site pair, sweep/colour, step,
+ *     slot) for sweeps, (site/4, init) for initial states and (replica/4,
+ *     resample, step) for copy numbers, so results do not depend on launch
+ *     shapes, stream timing or the number of replicas per block.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PA_OK = 0,
+    PA_ERR_INVALID = 1,  /* an argument is out of range, see each call         */
+    PA_ERR_CAPACITY = 2, /* a resampled population would exceed R_cap          */
+    PA_ERR_CUDA = 3,     /* a CUDA runtime call failed; see pa_last_cuda_error */
+    PA_ERR_TIMEOUT = 4,  /* a bounded device wait gave up                      */
+    PA_ERR_STATE = 5,    /* calls in the wrong order, or a failed context      */
+    PA_ERR_NOMEM = 6     /* device or host allocation failed                   */
+} pa_status;
+
+/* Copy-number rule for the resampling step (Sec. 2, step 2).  The paper draws
+ * r_j from a Poisson law with mean (R/R_{i-1}) tau_i(E_j) (Eq. 1).  NEAREST_INT
+ * takes one of the two integers nearest to that mean, floor(rho_j) + 1 with
+ * probability frac(rho_j), so the mean is kept and the spread is minimal;
+ * ROUND takes the nearest integer outright (halves up). */
+enum { PA_RESAMPLE_NEAREST_INT = 0, PA_RESAMPLE_ROUND = 1 };
+
+/* Initial population (Sec. 2 step 1; Sec. 5 Eq. 6). */
+enum { PA_INIT_RANDOM = 0, /* beta_0 = 0: independent uniform spins, ln Z_0 = N ln q        */
+       PA_INIT_GROUND = 1  /* each replica a uniformly chosen ground state, ln Z_0 = ln q + 2 N beta_0 */ };
+
+typedef struct {
+    int32_t q;             /* Potts states, 2..128                                   */
+    int32_t L;             /* linear size, even, 2..1024; N = L*L sites              */
+    int32_t R;             /* target population size R (= R_0), >= 1                 */
+    int32_t R_cap;         /* capacity; 0 selects R + R/4 + 1024                     */
+    uint64_t seed;         /* Philox key                                             */
+    int32_t resample_mode; /* PA_RESAMPLE_*                                          */
+    int32_t init_mode;     /* PA_INIT_*                                              */
+    double beta0;          /* inverse temperature of the initial population         */
+    int32_t track_families;/* 1: keep ancestor ids and family statistics             */
+    int32_t reserved;      /* must be 0                                              */
+} pa_config;
+
+/* Population estimators of one temperature step (Sec. 2 step 4, Sec. 3 Eq. 4):
+ *   meanE = sum_j E_j / R_i, meanE2 = sum_j E_j^2 / R_i (exact integer sums);
+ *   C     = beta^2 (meanE2 - meanE^2) / N, the specific heat per site;
+ *   meanM = (q sum_j Mt_j - N R_i) / ((q - 1) R_i) with Mt_j the occupation of
+ *           replica j's most common state (Eq. 5);
+ *   lnQ   = ln Q_i of the resampling into this step (0 at step 0);
+ *   lnZ   = ln Z_{beta_0} + sum_{m<=i} ln Q_m = -beta_i F (Eq. 2);
+ *   S_f   = -sum_f nu_f ln nu_f, nu_f the fraction of replicas descending from
+ *           initial replica f (family entropy; the paper does not define it),
+ *           n_families the number of such f with nu_f > 0.  Both 0 unless
+ *           track_families. */
+typedef struct {
+    double beta, lnQ, lnZ, meanE, meanE2, C, meanM, S_f;
+    int64_t R, n_families, sumE, sumE2, sumMt;
+} pa_obs;
+
+typedef struct pa_ctx pa_ctx;
+
+/* Creates a context, allocates its device buffers (two spin buffers of R_cap*N
+ * bytes plus O(R_cap + N) words) and enqueues the initial population at
+ * cfg->beta0 (Sec. 2 step 1 or Sec. 5 Eq. 6) with its energies, largest-state
+ * occupations, energy histogram and step-0 estimators.
+ * Errors: PA_ERR_INVALID for q outside 2..128, odd or out-of-range L, R < 1,
+ * R_cap < R, beta0 < 0, an unknown mode, or reserved != 0; PA_ERR_NOMEM or
+ * PA_ERR_CUDA if allocation or a launch fails (nothing is leaked; *out = NULL). */
+pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
+
+/* Resampling from beta_{i-1} to beta_i = beta_{i-1} + dbeta (Sec. 2 step 2):
+ * computes ln Q_i from the current energy histogram, the copy numbers r_j
+ * (per resample_mode), their exclusive scan and the parent map of the new
+ * population.  The replica gather itself is fused into the next pa_sweep.
+ * `step` is the temperature-step index i >= 1 (part of the random key) and
+ * must exceed the previous step's.  dbeta may be negative (heating, Sec. 5).
+ * If lnQ_out or R_out is non-NULL the call synchronises and writes ln Q_i and
+ * the new size R_i; otherwise it only enqueues.
+ * Errors: PA_ERR_STATE if a resample is already pending or step does not
+ * increase; PA_ERR_INVALID for a non-finite dbeta; PA_ERR_CAPACITY (reported
+ * here when synchronising, else by the next synchronising call) if R_i would
+ * exceed R_cap -- the population is then left at step i-1. */
+pa_status pa_resample(pa_ctx *ctx, double dbeta, int32_t step, double *lnQ_out, int32_t *R_out);
+
+/* theta checkerboard Metropolis sweeps at inverse temperature beta over every
+ * replica of the current population (Sec. 2 step 3), fused with the pending
+ * replica gather and followed by the per-replica energies, largest-state
+ * occupations, the energy histogram and the step's estimators.  One sweep
+ * updates the colour (x+y) even sites, then the odd ones; each attempt
+ * proposes one of the q-1 other states uniformly and accepts it with
+ * probability min(1, exp(-beta dE)) quantised to 32 bits.
+ * `step` must equal the step of the pending resample (or 0 for extra sweeps
+ * at step 0 before any resample).  theta >= 0.
+ * Errors: PA_ERR_INVALID for theta < 0 or beta < 0; PA_ERR_STATE for a step
+ * mismatch or a failed context. */
+pa_status pa_sweep(pa_ctx *ctx, double beta, int32_t theta, int32_t step);
+
+/* Per-replica energies E_j of the current population, int32, in slot order.
+ * on_device = 1: E_out is a device pointer with room for R_cap values (the
+ * copy is enqueued); 0: E_out is host memory with room for R_cap values (the
+ * call synchronises).  Only the first R_i values are written. */
+pa_status pa_energy(pa_ctx *ctx, int32_t *E_out, int32_t on_device);
+
+/* Synchronises and returns the estimators of the latest completed step.  If
+ * hist_out is non-NULL, also the energy histogram of the current population:
+ * hist_out[k] = number of replicas with E = k - 2N, k = 0..2N, so hist_len
+ * must be >= 2N+1.  Errors: PA_ERR_CAPACITY / PA_ERR_TIMEOUT from enqueued
+ * work, PA_ERR_INVALID for a short hist buffer. */
+pa_status pa_observables(pa_ctx *ctx, pa_obs *out, int32_t *hist_out, int32_t hist_len);
+
+/* Synchronises and copies the estimators of the last `count` completed steps
+ * (oldest first) into out[0..count).  The context keeps at least the last
+ * 1024 records (more after a longer pa_run).  PA_ERR_INVALID if count < 1 or
+ * more records are asked for than are kept. */
+pa_status pa_observables_history(pa_ctx *ctx, int32_t count, pa_obs *out);
+
+/* Current population size R_i (synchronises). */
+pa_status pa_population_size(pa_ctx *ctx, int32_t *R_out);
+
+/* Copies replicas [slot_begin, slot_begin + count) of the current population
+ * into host memory in the canonical layout [count][L][L] (synchronises).
+ * Errors: PA_ERR_INVALID if the range exceeds R_i or host is NULL. */
+pa_status pa_get_spins(pa_ctx *ctx, int64_t slot_begin, int64_t count, uint8_t *host);
+
+/* Initial-replica (family) ids of the current population, host int32[R_i]
+ * (synchronises).  PA_ERR_STATE unless track_families. */
+pa_status pa_get_ancestors(pa_ctx *ctx, int32_t *host);
+
+/* Runs the temperature schedule betas[1..K] from the context's current step:
+ * for i = 1..K, resample by betas[i] - betas[i-1] then theta sweeps at
+ * betas[i]; betas[0] must equal the current inverse temperature.  obs_out
+ * (host, K entries, may be NULL) receives each step's estimators and hist_out
+ * (host, may be NULL) the energy histograms after the steps listed in
+ * hist_steps[0..n_hist) (each 2N+1 ints, in that order).  use_graph = 1
+ * captures the K steps as one CUDA graph and launches it; 0 launches the
+ * kernels directly.  Synchronises once at the end.
+ * Errors: as pa_resample / pa_sweep; PA_ERR_INVALID for K < 1. */
+pa_status pa_run(pa_ctx *ctx, const double *betas, int32_t K, int32_t theta, pa_obs *obs_out,
+                 const int32_t *hist_steps, int32_t n_hist, int32_t *hist_out, int32_t use_graph);
+
+/* Releases the context and its device memory (synchronises its stream). */
+void pa_destroy(pa_ctx *ctx);
+
+/* Static description of a status code. */
+const char *pa_status_str(pa_status s);
+
+/* The last CUDA error string recorded by any call on this thread ("" if none). */
+const char *pa_last_cuda_error(void);
+
+/* Launch-shape control for the sweep kernel: replicas per block and threads
+ * per block (0 = automatic).  Any choice gives bit-identical results; this
+ * exists for autotuning and for tests that check exactly that. */
+pa_status pa_set_launch(pa_ctx *ctx, int32_t replicas_per_block, int32_t threads_per_block);
+
+/* Number of kernels this library has launched on any context since the
+ * process started (a host-side counter; graph launches count their nodes). */
+int64_t pa_kernel_launch_count(void);
+
+/* Kernel timing with CUDA events recorded on the context's stream around each
+ * sweep launch (the fused gather + theta sweeps + measurement kernel) and
+ * around each resampling sequence.  enable = 1 clears the totals and starts
+ * recording; 0 stops.  Not available inside pa_run(use_graph = 1). */
+pa_status pa_profile(pa_ctx *ctx, int32_t enable);
+
+/* Synchronises and returns the summed event times (milliseconds) and launch
+ * counts recorded since profiling was enabled: [0] sweep kernel, [1]
+ * resampling kernels.  Any pointer may be NULL. */
+pa_status pa_profile_read(pa_ctx *ctx, double *ms_out2, int64_t *launches_out2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H */

@@ -1,0 +1,271 @@
+"""GB300 population annealing for the 2D q-state Potts model.
+
+A thin ctypes binding over the C ABI in ``include/pa.h`` (library
+``libpa_gb300.so``, built by :mod:`paper_1704_01888_gb300.build`).  The
+binding only marshals arguments: every step of the method runs in the
+library's CUDA kernels.  PyTorch supplies the CUDA stream
+(``torch.cuda.current_stream()``).  If the library is missing the binding
+raises; there is no CPU fallback.
+
+The method is population annealing as in Barash, Weigel, Shchur & Janke,
+"Exploring first-order phase transitions with population annealing"
+(arXiv:1704.01888), Sec. 2 (algorithm, Eq. 2), Sec. 3 (model, Eqs. 3-5),
+Sec. 5 (heating, Eq. 6) and Sec. 6 (free-energy normalisations, Eqs. 7-8).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
+
+PA_OK, PA_ERR_INVALID, PA_ERR_CAPACITY, PA_ERR_CUDA, PA_ERR_TIMEOUT, PA_ERR_STATE, PA_ERR_NOMEM = range(7)
+RESAMPLE_NEAREST_INT = 0
+RESAMPLE_ROUND = 1
+INIT_RANDOM = 0
+INIT_GROUND = 1
+
+# Every extern "C" symbol declared in include/pa.h.
+EXPORTED = (
+    "pa_init", "pa_resample", "pa_sweep", "pa_energy", "pa_observables", "pa_population_size",
+    "pa_get_spins", "pa_get_ancestors", "pa_run", "pa_destroy", "pa_status_str", "pa_last_cuda_error",
+    "pa_set_launch", "pa_kernel_launch_count", "pa_profile", "pa_profile_read", "pa_observables_history",
+)
+
+
+class PAError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(what)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("q", ctypes.c_int32), ("L", ctypes.c_int32), ("R", ctypes.c_int32), ("R_cap", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("resample_mode", ctypes.c_int32), ("init_mode", ctypes.c_int32),
+        ("beta0", ctypes.c_double), ("track_families", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("beta", ctypes.c_double), ("lnQ", ctypes.c_double), ("lnZ", ctypes.c_double),
+        ("meanE", ctypes.c_double), ("meanE2", ctypes.c_double), ("C", ctypes.c_double),
+        ("meanM", ctypes.c_double), ("S_f", ctypes.c_double),
+        ("R", ctypes.c_int64), ("n_families", ctypes.c_int64), ("sumE", ctypes.c_int64),
+        ("sumE2", ctypes.c_int64), ("sumMt", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Loads libpa_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing: run paper_1704_01888_gb300.build.build() first")
+    lib = ctypes.CDLL(p)
+    P = ctypes.c_void_p
+    i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "pa_init": ([ctypes.POINTER(Config), P, ctypes.POINTER(P)], st),
+        "pa_resample": ([P, f64, i32, P, P], st),
+        "pa_sweep": ([P, f64, i32, i32], st),
+        "pa_energy": ([P, P, i32], st),
+        "pa_observables": ([P, ctypes.POINTER(Obs), P, i32], st),
+        "pa_population_size": ([P, P], st),
+        "pa_get_spins": ([P, i64, i64, P], st),
+        "pa_get_ancestors": ([P, P], st),
+        "pa_run": ([P, P, i32, i32, P, P, i32, P, i32], st),
+        "pa_destroy": ([P], None),
+        "pa_status_str": ([st], ctypes.c_char_p),
+        "pa_last_cuda_error": ([], ctypes.c_char_p),
+        "pa_set_launch": ([P, i32, i32], st),
+        "pa_kernel_launch_count": ([], i64),
+        "pa_profile": ([P, i32], st),
+        "pa_profile_read": ([P, P, P], st),
+        "pa_observables_history": ([P, i32, P], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != PA_OK:
+        lib = load_library()
+        msg = lib.pa_status_str(status).decode()
+        cuda = lib.pa_last_cuda_error().decode()
+        raise PAError(status, f"{what}: {msg}" + (f" ({cuda})" if cuda and status == PA_ERR_CUDA else ""))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _current_stream() -> int:
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("population annealing runs on a CUDA GPU; none is available")
+    return torch.cuda.current_stream().cuda_stream
+
+
+def kernel_launch_count() -> int:
+    return int(load_library().pa_kernel_launch_count())
+
+
+@dataclass
+class PAParams:
+    q: int
+    L: int
+    R: int
+    seed: int = 1
+    R_cap: int = 0
+    resample_mode: int = RESAMPLE_NEAREST_INT
+    init_mode: int = INIT_RANDOM
+    beta0: float = 0.0
+    track_families: bool = False
+
+
+class Population:
+    """One PA run on the GPU: a population of R_i replicas of the L x L Potts
+    lattice at the current inverse temperature (Sec. 2)."""
+
+    def __init__(self, params: PAParams, stream: int | None = None):
+        self.params = params
+        self.lib = load_library()
+        cfg = Config(params.q, params.L, params.R, params.R_cap, params.seed, params.resample_mode,
+                     params.init_mode, params.beta0, int(params.track_families), 0)
+        self._stream = _current_stream() if stream is None else stream
+        self._ctx = ctypes.c_void_p()
+        _check(self.lib.pa_init(ctypes.byref(cfg), ctypes.c_void_p(self._stream), ctypes.byref(self._ctx)),
+               "pa_init")
+        self.N = params.L * params.L
+        self.step = 0
+        self.beta = params.beta0
+
+    # -- lifecycle -------------------------------------------------------
+    def close(self):
+        if self._ctx:
+            self.lib.pa_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the PA step (Sec. 2 steps 2-4) -----------------------------------
+    def resample(self, dbeta: float, step: int | None = None, sync: bool = False):
+        """Sec. 2 step 2.  With sync=True returns (ln Q_i, R_i)."""
+        step = self.step + 1 if step is None else step
+        if sync:
+            lnq = ctypes.c_double()
+            rr = ctypes.c_int32()
+            _check(self.lib.pa_resample(self._ctx, float(dbeta), step, ctypes.byref(lnq), ctypes.byref(rr)),
+                   "pa_resample")
+            self._pending = step
+            return lnq.value, rr.value
+        _check(self.lib.pa_resample(self._ctx, float(dbeta), step, None, None), "pa_resample")
+        self._pending = step
+        return None
+
+    def sweep(self, beta: float, theta: int, step: int | None = None):
+        """Sec. 2 step 3: theta checkerboard Metropolis sweeps at beta."""
+        if step is None:
+            step = getattr(self, "_pending", None) or self.step
+        _check(self.lib.pa_sweep(self._ctx, float(beta), int(theta), int(step)), "pa_sweep")
+        self._pending = None
+        self.step = step
+        self.beta = beta
+
+    def observables(self, with_hist: bool = False):
+        obs = Obs()
+        hist = np.zeros(2 * self.N + 1, dtype=np.int32) if with_hist else None
+        _check(self.lib.pa_observables(self._ctx, ctypes.byref(obs), _ptr(hist) if with_hist else None,
+                                       hist.size if with_hist else 0), "pa_observables")
+        return (obs.as_dict(), hist) if with_hist else obs.as_dict()
+
+    def history(self, count: int) -> list:
+        """Estimators of the last `count` completed steps, oldest first."""
+        recs = (Obs * count)()
+        _check(self.lib.pa_observables_history(self._ctx, int(count), ctypes.cast(recs, ctypes.c_void_p)),
+               "pa_observables_history")
+        return [r.as_dict() for r in recs]
+
+    def size(self) -> int:
+        r = ctypes.c_int32()
+        _check(self.lib.pa_population_size(self._ctx, ctypes.byref(r)), "pa_population_size")
+        return r.value
+
+    def energies(self) -> np.ndarray:
+        cap = self.params.R_cap or (self.params.R + self.params.R // 4 + 1024)
+        out = np.zeros(cap, dtype=np.int32)
+        _check(self.lib.pa_energy(self._ctx, _ptr(out), 0), "pa_energy")
+        return out[: self.size()]
+
+    def energies_to_device(self, dev_ptr: int):
+        _check(self.lib.pa_energy(self._ctx, ctypes.c_void_p(dev_ptr), 1), "pa_energy")
+
+    def spins(self, begin: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = self.size() - begin
+        out = np.zeros((count, self.params.L, self.params.L), dtype=np.uint8)
+        _check(self.lib.pa_get_spins(self._ctx, begin, count, _ptr(out)), "pa_get_spins")
+        return out
+
+    def ancestors(self) -> np.ndarray:
+        out = np.zeros(self.size(), dtype=np.int32)
+        _check(self.lib.pa_get_ancestors(self._ctx, _ptr(out)), "pa_get_ancestors")
+        return out
+
+    def set_launch(self, replicas_per_block: int = 0, threads_per_block: int = 0):
+        _check(self.lib.pa_set_launch(self._ctx, replicas_per_block, threads_per_block), "pa_set_launch")
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.pa_profile(self._ctx, int(enable)), "pa_profile")
+
+    def profile_read(self):
+        """Returns {"sweep": (ms, launches), "resample": (ms, launches)}."""
+        ms = np.zeros(2, dtype=np.float64)
+        n = np.zeros(2, dtype=np.int64)
+        _check(self.lib.pa_profile_read(self._ctx, _ptr(ms), _ptr(n)), "pa_profile_read")
+        return {"sweep": (float(ms[0]), int(n[0])), "resample": (float(ms[1]), int(n[1]))}
+
+    def run(self, betas, theta: int, hist_steps=(), use_graph: bool = False):
+        """Runs betas[1..K] (betas[0] = current beta).  Returns (obs list, hists)."""
+        betas = np.ascontiguousarray(betas, dtype=np.float64)
+        K = betas.size - 1
+        obs = (Obs * K)()
+        hs = np.ascontiguousarray(hist_steps, dtype=np.int32)
+        hist = np.zeros((hs.size, 2 * self.N + 1), dtype=np.int32)
+        _check(self.lib.pa_run(self._ctx, _ptr(betas), K, int(theta), ctypes.cast(obs, ctypes.c_void_p),
+                               _ptr(hs) if hs.size else None, hs.size, _ptr(hist) if hs.size else None,
+                               int(use_graph)), "pa_run")
+        self.step += K
+        self.beta = float(betas[-1])
+        return [o.as_dict() for o in obs], hist

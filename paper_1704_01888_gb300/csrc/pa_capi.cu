@@ -1,0 +1,604 @@
+// pa_capi.cu -- host runtime and C ABI (include/pa.h) of the GB300
+// population-annealing library (Barash, Weigel, Shchur & Janke,
+// arXiv:1704.01888, Sec. 2 steps 1-5).
+//
+// A pa_ctx owns the device buffers of one PA run and enqueues its kernels on
+// one stream.  The run state that kernels need (population size, buffer
+// parity, pending normaliser, ln Z, error flag) lives in device memory, so a
+// whole temperature schedule can be enqueued or captured as one CUDA graph
+// without host round trips.  The host computes only the per-beta acceptance
+// thresholds (nine 32-bit integers, passed as kernel arguments), using the C
+// library's exp so that they are reproducible bit for bit on the host.
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pa.h"
+#include "pa_internal.cuh"
+
+namespace pa {
+
+static std::atomic<long long> g_launches{0};
+
+int64_t bump_launch_count(int64_t n) { return g_launches.fetch_add(n) + n; }
+
+}  // namespace pa
+
+namespace {
+
+thread_local std::string t_cuda_error;
+
+pa_status cuda_fail(cudaError_t e)
+{
+    t_cuda_error = cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PA_ERR_NOMEM : PA_ERR_CUDA;
+}
+
+#define PA_CK(expr)                                   \
+    do {                                              \
+        cudaError_t pa_e_ = (expr);                   \
+        if (pa_e_ != cudaSuccess) return cuda_fail(pa_e_); \
+    } while (0)
+
+// Acceptance thresholds T[dE + 4] = min(2^32 - 1, floor(min(1, exp(-beta dE)) 2^32)).
+void thresholds(double beta, uint32_t thr[9])
+{
+    for (int d = -4; d <= 4; ++d) {
+        const double a = std::exp(-beta * (double)d);
+        thr[d + 4] = a >= 1.0 ? 0xFFFFFFFFu : (uint32_t)(a * 4294967296.0);
+    }
+}
+
+}  // namespace
+
+struct pa_ctx {
+    pa_config cfg{};
+    int N = 0, nbins = 0, R_cap = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t k0 = 0, k1 = 0;
+    int sms = 0;
+
+    uint8_t *spins[2] = {nullptr, nullptr};
+    int32_t *anc[2] = {nullptr, nullptr};
+    int32_t *E = nullptr, *Mt = nullptr, *hist = nullptr, *fam = nullptr;
+    int32_t *counts = nullptr, *local_off = nullptr, *blocksum = nullptr, *parent = nullptr;
+    double *wtab = nullptr;
+    unsigned long long *acc = nullptr;
+    pa::DevState *st = nullptr;
+    pa::DevObs *obs = nullptr;
+    int obs_cap = 0;
+    long long n_obs = 0;  // estimator records written so far
+    uint8_t *stage = nullptr;
+    size_t stage_bytes = 0;
+
+    int step = 0;          // last completed temperature step
+    int pending_step = 0;  // step of an enqueued resample awaiting its sweep
+    double beta = 0.0;     // inverse temperature of the current population
+    bool failed = false;
+
+    int rpb = 1, threads = 32, grid = 1;
+    cudaStream_t capture_stream = nullptr;  // private stream for graph capture
+
+    // event timing (pa_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev[2];  // start/stop pairs per category
+    int64_t ev_used[2] = {0, 0};
+};
+
+namespace {
+
+template <typename T>
+pa_status dev_alloc(T **p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e);
+    }
+    return PA_OK;
+}
+
+void release_events(pa_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);
+        c->ev[k].clear();
+        c->ev_used[k] = 0;
+    }
+}
+
+// Records the start (first = true) or stop event of category k.
+pa_status profile_mark(pa_ctx *c, int k, bool first)
+{
+    if (!c->profiling) return PA_OK;
+    const size_t idx = (size_t)(first ? 2 * c->ev_used[k] : 2 * c->ev_used[k] + 1);
+    while (c->ev[k].size() <= idx) {
+        cudaEvent_t e;
+        PA_CK(cudaEventCreate(&e));
+        c->ev[k].push_back(e);
+    }
+    PA_CK(cudaEventRecord(c->ev[k][idx], c->stream));
+    if (!first) c->ev_used[k] += 1;
+    return PA_OK;
+}
+
+void release(pa_ctx *c)
+{
+    release_events(c);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    void *ptrs[] = {c->spins[0], c->spins[1], c->anc[0], c->anc[1], c->E, c->Mt, c->hist, c->fam,
+                    c->counts, c->local_off, c->blocksum, c->parent, c->wtab, c->acc, c->st, c->obs,
+                    c->stage};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
+{
+    const int L = c->cfg.L;
+    const int N = c->N;
+    const bool words = (L % 8) == 0;
+    int rpb = rpb_req;
+    if (rpb <= 0) {
+        int rpb_mem = (int)(65536 / (size_t)N);
+        if (rpb_mem < 1) rpb_mem = 1;
+        int rpb_fill = c->cfg.R / (4 * c->sms);
+        if (rpb_fill < 1) rpb_fill = 1;
+        rpb = rpb_mem < rpb_fill ? rpb_mem : rpb_fill;
+    }
+    if ((size_t)rpb * N > 200 * 1024) return PA_ERR_INVALID;
+    int threads = threads_req;
+    if (threads <= 0) {
+        const long long work = (long long)rpb * (words ? N / 8 : N / 2);
+        threads = (int)((work + 31) / 32 * 32);
+        if (threads > 512) threads = 512;
+        if (threads < 32) threads = 32;
+    }
+    if (threads % 32 != 0 || threads > 1024) return PA_ERR_INVALID;
+    const int per_sm = pa::sweep_max_blocks_per_sm(L, rpb, threads);
+    if (per_sm <= 0) return PA_ERR_INVALID;
+    const long long groups = ((long long)c->R_cap + rpb - 1) / rpb;
+    long long grid = (long long)per_sm * c->sms;
+    if (grid > groups) grid = groups;
+    c->rpb = rpb;
+    c->threads = threads;
+    c->grid = (int)grid;
+    return PA_OK;
+}
+
+pa::SweepArgs sweep_args(pa_ctx *c, double beta, int theta, int step, int gather)
+{
+    pa::SweepArgs a{};
+    a.buf[0] = c->spins[0];
+    a.buf[1] = c->spins[1];
+    a.anc[0] = c->anc[0];
+    a.anc[1] = c->anc[1];
+    a.parent = c->parent;
+    a.E = c->E;
+    a.Mt = c->Mt;
+    a.hist = c->hist;
+    a.acc = c->acc;
+    a.fam = c->cfg.track_families ? c->fam : nullptr;
+    a.st = c->st;
+    thresholds(beta, a.thr);
+    a.k0 = c->k0;
+    a.k1 = c->k1;
+    a.q = c->cfg.q;
+    a.L = c->cfg.L;
+    a.theta = theta;
+    a.step = step;
+    a.rpb = c->rpb;
+    a.gather = gather;
+    return a;
+}
+
+pa::DevObs *next_obs_slot(pa_ctx *c)
+{
+    pa::DevObs *slot = c->obs + (c->n_obs % c->obs_cap);
+    c->n_obs += 1;
+    return slot;
+}
+
+// Enqueues theta sweeps (with the pending gather, if any) and the estimators.
+pa_status enqueue_sweep(pa_ctx *c, double beta, int theta, int step)
+{
+    const int gather = c->pending_step != 0;
+    pa::SweepArgs a = sweep_args(c, beta, theta, step, gather);
+    pa_status s = profile_mark(c, 0, true);
+    if (s) return s;
+    PA_CK(pa::launch_sweep(a, c->threads, c->grid, c->stream));
+    if ((s = profile_mark(c, 0, false))) return s;
+    PA_CK(pa::launch_finalize(c->st, c->acc, a.fam, c->cfg.R, next_obs_slot(c), beta, c->cfg.q, c->N,
+                              gather, gather, c->stream));
+    c->pending_step = 0;
+    c->step = step;
+    c->beta = beta;
+    return PA_OK;
+}
+
+pa_status enqueue_resample(pa_ctx *c, double dbeta, int step)
+{
+    pa_status s = profile_mark(c, 1, true);
+    if (s) return s;
+    PA_CK(pa::launch_resample(c->hist, c->nbins, c->E, dbeta, c->cfg.R, c->R_cap, c->cfg.resample_mode, step,
+                              c->k0, c->k1, c->wtab, c->counts, c->local_off, c->blocksum, c->parent,
+                              c->hist, c->st, c->stream));
+    if ((s = profile_mark(c, 1, false))) return s;
+    c->pending_step = step;
+    return PA_OK;
+}
+
+// Reads the device state after synchronising; maps a kernel-raised error.
+pa_status sync_state(pa_ctx *c, pa::DevState *out)
+{
+    pa::DevState h;
+    PA_CK(cudaMemcpyAsync(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    PA_CK(cudaStreamSynchronize(c->stream));
+    if (out) *out = h;
+    if (h.err != 0) {
+        c->failed = true;
+        return (pa_status)h.err;
+    }
+    return PA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pa_status_str(pa_status s)
+{
+    switch (s) {
+    case PA_OK: return "ok";
+    case PA_ERR_INVALID: return "invalid argument";
+    case PA_ERR_CAPACITY: return "population exceeds capacity";
+    case PA_ERR_CUDA: return "CUDA error";
+    case PA_ERR_TIMEOUT: return "device wait timed out";
+    case PA_ERR_STATE: return "call out of order or context failed";
+    case PA_ERR_NOMEM: return "out of memory";
+    }
+    return "unknown status";
+}
+
+const char *pa_last_cuda_error(void) { return t_cuda_error.c_str(); }
+
+int64_t pa_kernel_launch_count(void) { return pa::g_launches.load(); }
+
+pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
+{
+    if (!out) return PA_ERR_INVALID;
+    *out = nullptr;
+    if (!cfg) return PA_ERR_INVALID;
+    const pa_config &g = *cfg;
+    if (g.q < 2 || g.q > 128 || g.L < 2 || g.L > 1024 || (g.L & 1) || g.R < 1 || g.reserved != 0)
+        return PA_ERR_INVALID;
+    if (g.resample_mode != PA_RESAMPLE_NEAREST_INT && g.resample_mode != PA_RESAMPLE_ROUND) return PA_ERR_INVALID;
+    if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
+    if (!(g.beta0 >= 0.0) || !std::isfinite(g.beta0)) return PA_ERR_INVALID;
+    long long R_cap = g.R_cap > 0 ? g.R_cap : (long long)g.R + g.R / 4 + 1024;
+    if (R_cap < g.R || R_cap > 0x7FFFFFFFLL - 1024) return PA_ERR_INVALID;
+
+    pa_ctx *c = new (std::nothrow) pa_ctx();
+    if (!c) return PA_ERR_NOMEM;
+    c->cfg = g;
+    c->cfg.R_cap = (int32_t)R_cap;
+    c->N = g.L * g.L;
+    c->nbins = 2 * c->N + 1;
+    c->R_cap = (int)R_cap;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->k0 = (uint32_t)(g.seed & 0xFFFFFFFFu);
+    c->k1 = (uint32_t)(g.seed >> 32);
+    c->beta = g.beta0;
+
+    pa_status s = PA_OK;
+    auto fail = [&](pa_status e) {
+        release(c);
+        delete c;
+        return e;
+    };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+
+    const size_t spin_bytes = (size_t)c->R_cap * c->N;
+    const int nb = (c->R_cap + 1023) / 1024;
+    if ((s = dev_alloc(&c->spins[0], spin_bytes)) || (s = dev_alloc(&c->spins[1], spin_bytes)) ||
+        (s = dev_alloc(&c->E, c->R_cap)) || (s = dev_alloc(&c->Mt, c->R_cap)) ||
+        (s = dev_alloc(&c->hist, c->nbins)) || (s = dev_alloc(&c->counts, c->R_cap)) ||
+        (s = dev_alloc(&c->local_off, c->R_cap)) || (s = dev_alloc(&c->blocksum, nb)) ||
+        (s = dev_alloc(&c->parent, c->R_cap)) || (s = dev_alloc(&c->wtab, c->nbins)) ||
+        (s = dev_alloc(&c->acc, 3)) || (s = dev_alloc(&c->st, 1)))
+        return fail(s);
+    if (g.track_families) {
+        if ((s = dev_alloc(&c->anc[0], c->R_cap)) || (s = dev_alloc(&c->anc[1], c->R_cap)) ||
+            (s = dev_alloc(&c->fam, g.R)))
+            return fail(s);
+    }
+    c->obs_cap = 1024;
+    if ((s = dev_alloc(&c->obs, c->obs_cap))) return fail(s);
+    c->stage_bytes = spin_bytes < (64u << 20) ? spin_bytes : (64u << 20);
+    if ((s = dev_alloc(&c->stage, c->stage_bytes))) return fail(s);
+
+    if ((s = choose_launch(c, 0, 0))) return fail(s);
+
+    pa::DevState h{};
+    h.pop = g.R;
+    if (g.init_mode == PA_INIT_GROUND)
+        h.lnZ = std::log((double)g.q) - g.beta0 * (double)(-2 * c->N);
+    else
+        h.lnZ = (double)c->N * std::log((double)g.q);
+    e = cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->hist, 0, sizeof(int32_t) * c->nbins, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 3, c->stream);
+    if (e == cudaSuccess && c->fam) e = cudaMemsetAsync(c->fam, 0, sizeof(int32_t) * g.R, c->stream);
+    if (e == cudaSuccess)
+        e = pa::launch_init(c->spins[0], c->anc[0], g.q, g.L, g.R, c->k0, c->k1, g.init_mode == PA_INIT_GROUND,
+                            c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    if ((s = enqueue_sweep(c, g.beta0, 0, 0))) return fail(s);
+    if ((s = sync_state(c, nullptr))) return fail(s);
+    *out = c;
+    return PA_OK;
+}
+
+void pa_destroy(pa_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+}
+
+pa_status pa_set_launch(pa_ctx *c, int32_t replicas_per_block, int32_t threads_per_block)
+{
+    if (!c) return PA_ERR_INVALID;
+    if (replicas_per_block < 0 || threads_per_block < 0) return PA_ERR_INVALID;
+    return choose_launch(c, replicas_per_block, threads_per_block);
+}
+
+pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, int32_t *R_out)
+{
+    if (!c) return PA_ERR_INVALID;
+    if (c->failed || c->pending_step != 0 || step <= c->step) return PA_ERR_STATE;
+    if (!std::isfinite(dbeta) || !(c->beta + dbeta >= 0.0)) return PA_ERR_INVALID;
+    pa_status s = enqueue_resample(c, dbeta, step);
+    if (s) return s;
+    if (lnQ_out || R_out) {
+        pa::DevState h;
+        s = sync_state(c, &h);
+        if (s == PA_ERR_CAPACITY) {
+            // undo: clear the flag, the population is still the previous step's
+            pa::DevState fix = h;
+            fix.err = 0;
+            PA_CK(cudaMemcpyAsync(c->st, &fix, sizeof(fix), cudaMemcpyHostToDevice, c->stream));
+            PA_CK(cudaStreamSynchronize(c->stream));
+            c->failed = false;
+            c->pending_step = 0;
+            return PA_ERR_CAPACITY;
+        }
+        if (s) return s;
+        if (lnQ_out) *lnQ_out = h.lnQ;
+        if (R_out) *R_out = h.pop_next;
+    }
+    return PA_OK;
+}
+
+pa_status pa_sweep(pa_ctx *c, double beta, int32_t theta, int32_t step)
+{
+    if (!c) return PA_ERR_INVALID;
+    if (theta < 0 || !(beta >= 0.0) || !std::isfinite(beta)) return PA_ERR_INVALID;
+    if (c->failed) return PA_ERR_STATE;
+    if (c->pending_step != 0 ? step != c->pending_step : step != c->step) return PA_ERR_STATE;
+    return enqueue_sweep(c, beta, theta, step);
+}
+
+pa_status pa_energy(pa_ctx *c, int32_t *E_out, int32_t on_device)
+{
+    if (!c || !E_out) return PA_ERR_INVALID;
+    pa::DevState h;
+    pa_status s = sync_state(c, &h);
+    if (s) return s;
+    PA_CK(cudaMemcpyAsync(E_out, c->E, sizeof(int32_t) * h.pop,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) PA_CK(cudaStreamSynchronize(c->stream));
+    return PA_OK;
+}
+
+pa_status pa_observables_history(pa_ctx *c, int32_t count, pa_obs *out)
+{
+    if (!c || !out || count < 1) return PA_ERR_INVALID;
+    if (count > c->n_obs || count > c->obs_cap) return PA_ERR_INVALID;
+    pa_status s = sync_state(c, nullptr);
+    if (s) return s;
+    for (int32_t i = 0; i < count;) {
+        const long long rec = c->n_obs - count + i;
+        const int at = (int)(rec % c->obs_cap);
+        int run = c->obs_cap - at;
+        if (run > count - i) run = count - i;
+        PA_CK(cudaMemcpyAsync(out + i, c->obs + at, sizeof(pa_obs) * run, cudaMemcpyDeviceToHost, c->stream));
+        i += run;
+    }
+    PA_CK(cudaStreamSynchronize(c->stream));
+    return PA_OK;
+}
+
+pa_status pa_population_size(pa_ctx *c, int32_t *R_out)
+{
+    if (!c || !R_out) return PA_ERR_INVALID;
+    pa::DevState h;
+    pa_status s = sync_state(c, &h);
+    if (s) return s;
+    *R_out = h.pop;
+    return PA_OK;
+}
+
+pa_status pa_observables(pa_ctx *c, pa_obs *out, int32_t *hist_out, int32_t hist_len)
+{
+    if (!c || !out) return PA_ERR_INVALID;
+    if (hist_out && hist_len < c->nbins) return PA_ERR_INVALID;
+    pa_status s = sync_state(c, nullptr);
+    if (s) return s;
+    const pa::DevObs *slot = c->obs + ((c->n_obs - 1) % c->obs_cap);
+    static_assert(sizeof(pa::DevObs) == sizeof(pa_obs), "pa_obs layout");
+    PA_CK(cudaMemcpyAsync(out, slot, sizeof(pa_obs), cudaMemcpyDeviceToHost, c->stream));
+    if (hist_out)
+        PA_CK(cudaMemcpyAsync(hist_out, c->hist, sizeof(int32_t) * c->nbins, cudaMemcpyDeviceToHost, c->stream));
+    PA_CK(cudaStreamSynchronize(c->stream));
+    return PA_OK;
+}
+
+pa_status pa_get_spins(pa_ctx *c, int64_t slot_begin, int64_t count, uint8_t *host)
+{
+    if (!c || !host || slot_begin < 0 || count < 0) return PA_ERR_INVALID;
+    pa::DevState h;
+    pa_status s = sync_state(c, &h);
+    if (s) return s;
+    if (slot_begin + count > h.pop) return PA_ERR_INVALID;
+    const int64_t per = (int64_t)(c->stage_bytes / c->N);
+    for (int64_t done = 0; done < count; done += per) {
+        const int64_t n = count - done < per ? count - done : per;
+        PA_CK(pa::launch_to_canonical(c->spins[h.parity] + (size_t)(slot_begin + done) * c->N, c->stage, c->cfg.L, n,
+                                      c->stream));
+        PA_CK(cudaMemcpyAsync(host + (size_t)done * c->N, c->stage, (size_t)n * c->N, cudaMemcpyDeviceToHost,
+                              c->stream));
+        PA_CK(cudaStreamSynchronize(c->stream));
+    }
+    return PA_OK;
+}
+
+pa_status pa_get_ancestors(pa_ctx *c, int32_t *host)
+{
+    if (!c || !host) return PA_ERR_INVALID;
+    if (!c->cfg.track_families) return PA_ERR_STATE;
+    pa::DevState h;
+    pa_status s = sync_state(c, &h);
+    if (s) return s;
+    PA_CK(cudaMemcpyAsync(host, c->anc[h.parity], sizeof(int32_t) * h.pop, cudaMemcpyDeviceToHost, c->stream));
+    PA_CK(cudaStreamSynchronize(c->stream));
+    return PA_OK;
+}
+
+pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_obs *obs_out,
+                 const int32_t *hist_steps, int32_t n_hist, int32_t *hist_out, int32_t use_graph)
+{
+    if (!c || !betas || K < 1 || theta < 0 || n_hist < 0 || (n_hist > 0 && (!hist_steps || !hist_out)))
+        return PA_ERR_INVALID;
+    if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
+    for (int i = 0; i <= K; ++i)
+        if (!std::isfinite(betas[i]) || !(betas[i] >= 0.0)) return PA_ERR_INVALID;
+    for (int h = 0; h < n_hist; ++h)
+        if (hist_steps[h] < 1 || hist_steps[h] > K) return PA_ERR_INVALID;
+
+    // estimator slots for K steps, contiguous
+    if (c->obs_cap < K + 1) {
+        PA_CK(cudaStreamSynchronize(c->stream));
+        pa::DevObs *bigger = nullptr;
+        pa_status s = dev_alloc(&bigger, (size_t)K + 1);
+        if (s) return s;
+        PA_CK(cudaMemcpy(bigger, c->obs + ((c->n_obs - 1) % c->obs_cap), sizeof(pa::DevObs), cudaMemcpyDeviceToDevice));
+        cudaFree(c->obs);
+        c->obs = bigger;
+        c->obs_cap = K + 1;
+        c->n_obs = 1;
+    }
+    int32_t *hstore = nullptr;
+    if (n_hist > 0) {
+        pa_status s = dev_alloc(&hstore, (size_t)n_hist * c->nbins);
+        if (s) return s;
+    }
+    const long long first_obs = c->n_obs;
+    const int step0 = c->step;
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    pa_status s = PA_OK;
+    // The graph is captured on a private stream (the legacy default stream
+    // cannot be captured) and launched on the context's stream.
+    const bool was_profiling = c->profiling;
+    cudaStream_t user_stream = c->stream;
+    if (use_graph) {
+        c->profiling = false;
+        cudaError_t e = cudaSuccess;
+        if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            c->profiling = was_profiling;
+            if (hstore) cudaFree(hstore);
+            return cuda_fail(e);
+        }
+        c->stream = c->capture_stream;
+    }
+    for (int i = 1; i <= K && s == PA_OK; ++i) {
+        s = enqueue_resample(c, betas[i] - betas[i - 1], step0 + i);
+        if (s == PA_OK) s = enqueue_sweep(c, betas[i], theta, step0 + i);
+        for (int h = 0; h < n_hist && s == PA_OK; ++h) {
+            if (hist_steps[h] == i) {
+                cudaError_t e = cudaMemcpyAsync(hstore + (size_t)h * c->nbins, c->hist, sizeof(int32_t) * c->nbins,
+                                                cudaMemcpyDeviceToDevice, c->stream);
+                if (e != cudaSuccess) s = cuda_fail(e);
+            }
+        }
+    }
+    if (use_graph) {
+        cudaError_t e = cudaStreamEndCapture(c->capture_stream, &graph);
+        c->stream = user_stream;
+        if (e == cudaSuccess && s == PA_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess && s == PA_OK) e = cudaGraphLaunch(exec, c->stream);
+        if (e != cudaSuccess && s == PA_OK) s = cuda_fail(e);
+    }
+    c->profiling = was_profiling;
+    if (s == PA_OK) s = sync_state(c, nullptr);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (s == PA_OK && obs_out) {
+        for (int i = 0; i < K; ++i) {
+            const pa::DevObs *slot = c->obs + ((first_obs + i) % c->obs_cap);
+            cudaError_t e = cudaMemcpy(obs_out + i, slot, sizeof(pa_obs), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                s = cuda_fail(e);
+                break;
+            }
+        }
+    }
+    if (s == PA_OK && n_hist > 0) {
+        cudaError_t e = cudaMemcpy(hist_out, hstore, sizeof(int32_t) * (size_t)n_hist * c->nbins,
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) s = cuda_fail(e);
+    }
+    if (hstore) cudaFree(hstore);
+    return s;
+}
+
+pa_status pa_profile(pa_ctx *c, int32_t enable)
+{
+    if (!c) return PA_ERR_INVALID;
+    PA_CK(cudaStreamSynchronize(c->stream));
+    c->ev_used[0] = c->ev_used[1] = 0;
+    c->profiling = enable != 0;
+    return PA_OK;
+}
+
+pa_status pa_profile_read(pa_ctx *c, double *ms_out2, int64_t *launches_out2)
+{
+    if (!c) return PA_ERR_INVALID;
+    PA_CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 2; ++k) {
+        double total = 0.0;
+        for (int64_t i = 0; i < c->ev_used[k]; ++i) {
+            float ms = 0.f;
+            PA_CK(cudaEventElapsedTime(&ms, c->ev[k][2 * i], c->ev[k][2 * i + 1]));
+            total += ms;
+        }
+        if (ms_out2) ms_out2[k] = total;
+        if (launches_out2) launches_out2[k] = c->ev_used[k];
+    }
+    return PA_OK;
+}
+
+}  // extern "C"

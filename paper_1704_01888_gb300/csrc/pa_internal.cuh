@@ -1,0 +1,108 @@
+// pa_internal.cuh -- device helpers and host<->device structures shared by the
+// translation units of the GB300 population-annealing library.
+//
+// Device layout of one replica (N = L*L bytes, one byte per spin):
+//   byte (c * N/2 + y * L/2 + m) holds site (x, y) with colour c = (x + y) & 1
+//   and x = 2m + ((y + c) & 1).
+// Each colour's sites of one row are contiguous, so the four neighbours of
+// four consecutive same-colour sites are four aligned or byte-shifted 32-bit
+// words of the other colour (left/right in the same row, up/down in the rows
+// above and below).  Replicas are stored back to back: replica s starts at
+// byte s*N of its buffer.  The canonical [y][x] layout exists only at the API
+// boundary (pa_get_spins).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pa {
+
+// Top two bits of the second Philox counter word separate the uses of the
+// generator (initial spins, sweeps, copy numbers, ground states).
+constexpr uint32_t DOM_SWEEP = 0x00000000u;
+constexpr uint32_t DOM_INIT = 0x40000000u;
+constexpr uint32_t DOM_RESAMPLE = 0x80000000u;
+constexpr uint32_t DOM_GROUND = 0xC0000000u;
+
+// Device-resident run state.  Kernels read and update it so that a whole
+// schedule can be enqueued (or captured in a graph) with no host round trip.
+struct DevState {
+    int32_t pop;       // current population size R_i
+    int32_t pop_next;  // size after the pending resample
+    int32_t err;       // 0, or a pa_status code set by a kernel
+    int32_t parity;    // spin / ancestor buffer holding the current population
+    int32_t E_ref;     // reference energy of the pending resample
+    int32_t pad0;
+    double S;          // sum of shifted Boltzmann factors of the pending resample
+    double lnQ;        // ln Q of the pending resample
+    double lnZ;        // running ln Z (Eq. 2)
+};
+
+// Per-step estimators; field order matches pa_obs in include/pa.h.
+struct DevObs {
+    double beta, lnQ, lnZ, meanE, meanE2, C, meanM, S_f;
+    int64_t R, n_families, sumE, sumE2, sumMt;
+};
+
+struct SweepArgs {
+    uint8_t *buf[2];           // spin double buffer
+    int32_t *anc[2];           // ancestor double buffer (null: no families)
+    const int32_t *parent;     // parent map of the pending resample (null: in place)
+    int32_t *E;                // per-replica energies
+    int32_t *Mt;               // per-replica occupation of the most common state
+    int32_t *hist;             // energy histogram, bin E + 2N
+    unsigned long long *acc;   // [3] running sums of E, E^2, Mt (two's complement)
+    int32_t *fam;              // family counts (null: no families)
+    DevState *st;
+    uint32_t thr[9];           // acceptance thresholds T[dE + 4]
+    uint32_t k0, k1;           // Philox key (seed low / high word)
+    int32_t q, L, theta, step;
+    int32_t rpb;               // replicas per block iteration
+    int32_t gather;            // 1: read parents from buf[parity], write buf[parity^1]
+};
+
+// Launchers (pa_sweep.cu)
+cudaError_t launch_sweep(const SweepArgs &a, int threads, int grid, cudaStream_t s);
+size_t sweep_smem_bytes(int L, int rpb);
+int sweep_max_blocks_per_sm(int L, int rpb, int threads);
+
+// Launchers (pa_resample.cu)
+cudaError_t launch_init(uint8_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
+                        int ground, cudaStream_t s);
+cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, double dbeta, int R_target,
+                            int R_cap, int mode, int step, uint32_t k0, uint32_t k1, double *wtab,
+                            int32_t *counts, int32_t *local_off, int32_t *blocksum, int32_t *parent,
+                            int32_t *hist_zero, DevState *st, cudaStream_t s);
+cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,
+                            double beta, int q, int N, int gathered, int resampled, cudaStream_t s);
+cudaError_t launch_to_canonical(const uint8_t *spins, uint8_t *out, int L, int64_t count,
+                                cudaStream_t s);
+
+int64_t bump_launch_count(int64_t n);
+
+}  // namespace pa
+
+namespace pa {
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32 -> 64 bit products whose high halves are xored with the other counter
+// words and the round key; the key advances by the Weyl constants each round.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t pick_word(const uint4 &w, int i)
+{
+    return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
+}
+
+}  // namespace pa

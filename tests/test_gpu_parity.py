@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bar: spins, energies, largest-state occupations, histograms, population sizes
+and family ids bit-exact; <E>, <E^2>, C and <M> bit-exact (they come from
+exact integer sums through the same IEEE operations); ln Q and ln Z within
+1e-10 relative (the device evaluates exp/log with CUDA's libm, the oracle
+with the C library's); family entropy within 1e-12 relative.
+"""
+import math
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1704_01888_gb300 as pa
+from paper_1704_01888_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+LNZ_RTOL = 1e-10
+SF_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1704_01888_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+def _gpu_run(q, L, R, seed, theta, betas, mode=pa.RESAMPLE_NEAREST_INT, init=pa.INIT_RANDOM, fam=False,
+             R_cap=0, launch=None, graph=False, stepwise=False, hist_steps=()):
+    p = pa.PAParams(q=q, L=L, R=R, seed=seed, R_cap=R_cap, resample_mode=mode, init_mode=init,
+                    beta0=float(betas[0]), track_families=fam)
+    with pa.Population(p) as pop:
+        if launch:
+            pop.set_launch(*launch)
+        obs0 = pop.observables()
+        hists = {}
+        if stepwise:
+            obs = []
+            for i in range(1, len(betas)):
+                pop.resample(betas[i] - betas[i - 1], i)
+                pop.sweep(betas[i], theta, i)
+                o, h = pop.observables(with_hist=True)
+                obs.append(o)
+                hists[i] = h
+        else:
+            obs, hs = pop.run(betas, theta, hist_steps=hist_steps, use_graph=graph)
+            hists = {s: hs[k] for k, s in enumerate(hist_steps)}
+        out = {"obs": [obs0] + list(obs), "spins": pop.spins(), "E": pop.energies(), "hists": hists}
+        _, out["hist_final"] = pop.observables(with_hist=True)
+        if fam:
+            out["anc"] = pop.ancestors()
+    return out
+
+
+def _oracle_run(q, L, R, seed, theta, betas, mode=0, init=0, R_cap=None):
+    return oracle.run(q, L, R, seed, theta, betas, mode=mode, init_mode=init, R_cap=R_cap, want_hist=True)
+
+
+def _compare(g, o, fam=False, check_hists=True):
+    K = len(g["obs"]) - 1
+    for i in range(K + 1):
+        go = g["obs"][i]
+        assert go["R"] == o["R"][i], ("R", i)
+        for key in ("sumE", "sumE2", "sumMt"):
+            assert go[key] == o[key][i], (key, i)
+        for key in ("meanE", "meanE2", "C", "meanM", "beta"):
+            assert go[key] == o[key][i], (key, i, go[key], o[key][i])
+        assert go["lnZ"] == pytest.approx(o["lnZ"][i], rel=LNZ_RTOL, abs=1e-12), ("lnZ", i)
+        if i > 0:
+            assert go["lnQ"] == pytest.approx(o["lnQ"][i], rel=LNZ_RTOL, abs=1e-12), ("lnQ", i)
+        if fam:
+            assert go["n_families"] == o["n_families"][i], ("n_families", i)
+            assert go["S_f"] == pytest.approx(o["S_f"][i], rel=SF_RTOL, abs=1e-14), ("S_f", i)
+    Rf = o["R_final"]
+    assert g["spins"].shape[0] == Rf
+    assert np.array_equal(g["spins"], o["spins"])
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["hist_final"], o["hist"][K])
+    if check_hists:
+        for s, h in g["hists"].items():
+            assert np.array_equal(h, o["hist"][s]), ("hist", s)
+    if fam:
+        assert np.array_equal(g["anc"], o["anc"])
+
+
+# ---------------------------------------------------------------------------
+# Plain PA, q = 10, L = 16, R = 1000, 100 steps, theta = 10: the whole run.
+# ---------------------------------------------------------------------------
+def test_plain_small_full_run_bit_exact():
+    w = wl.C1
+    b = w.betas()
+    g = _gpu_run(w.q, w.L, w.R, w.seed, w.theta, b, hist_steps=(1, 50, 100))
+    o = _oracle_run(w.q, w.L, w.R, w.seed, w.theta, b)
+    _compare(g, o)
+
+
+def test_step_api_graph_and_launch_shapes_agree():
+    """The step-by-step calls, the enqueued run, the graph-captured run and
+    other block shapes all give the same bits (reduced K)."""
+    w = wl.C1
+    b = w.betas()[:21]
+    ref = _gpu_run(w.q, w.L, w.R, w.seed, w.theta, b)
+    for kw in (dict(stepwise=True), dict(graph=True), dict(launch=(7, 64)), dict(launch=(40, 256)),
+               dict(launch=(1, 32), graph=True)):
+        g = _gpu_run(w.q, w.L, w.R, w.seed, w.theta, b, **kw)
+        assert np.array_equal(g["spins"], ref["spins"]), kw
+        assert [x["lnZ"] for x in g["obs"]] == [x["lnZ"] for x in ref["obs"]], kw
+        assert [x["sumE"] for x in g["obs"]] == [x["sumE"] for x in ref["obs"]], kw
+
+
+# ---------------------------------------------------------------------------
+# Edge cases: tiny and ragged lattices (site kernel for L % 8 != 0), the word
+# kernel with a run-time L, q = 2 and q = 128, R = 1, theta = 0, rounding
+# mode, heating from the ground state, families.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("q,L,R,theta,K,extra", [
+    (3, 2, 64, 3, 8, {}),
+    (5, 4, 200, 4, 10, {}),
+    (10, 6, 150, 2, 10, {}),
+    (10, 8, 300, 3, 10, {}),            # word kernel, run-time L
+    (2, 16, 257, 5, 12, {}),            # Ising-like q = 2, ragged R
+    (128, 16, 100, 2, 6, {}),           # largest q
+    (10, 24, 90, 2, 6, {}),             # word kernel, run-time L, 3 words per row
+    (10, 16, 1, 3, 10, {}),             # one replica
+    (6, 16, 500, 0, 8, {}),             # resampling only
+    (8, 16, 400, 3, 10, {"mode": pa.RESAMPLE_ROUND}),
+])
+def test_edge_cases_bit_exact(q, L, R, theta, K, extra):
+    b = np.array([1.5 * i / K for i in range(K + 1)])
+    g = _gpu_run(q, L, R, 11, theta, b, **extra)
+    o = _oracle_run(q, L, R, 11, theta, b, **extra)
+    _compare(g, o)
+
+
+def test_heating_from_ground_state_with_families():
+    q, L, R, K = 6, 16, 600, 15
+    b = np.array([3.0 - 3.0 * i / K for i in range(K + 1)])
+    g = _gpu_run(q, L, R, 5, 3, b, init=pa.INIT_GROUND, fam=True)
+    o = _oracle_run(q, L, R, 5, 3, b, init=1)
+    _compare(g, o, fam=True)
+    assert g["obs"][0]["lnZ"] == math.log(q) + 2 * L * L * 3.0
+
+
+def test_families_cooling():
+    w = wl.C1
+    b = w.betas()[:31]
+    g = _gpu_run(w.q, w.L, w.R, 2, w.theta, b, fam=True)
+    o = _oracle_run(w.q, w.L, w.R, 2, w.theta, b)
+    _compare(g, o, fam=True)
+
+
+def test_capacity_overflow_keeps_previous_population():
+    q, L, R = 10, 16, 1000
+    p = pa.PAParams(q=q, L=L, R=R, seed=3, R_cap=R)
+    with pa.Population(p) as pop:
+        beta = 0.0
+        hit = False
+        for i in range(1, 40):
+            before = pop.spins()
+            try:
+                pop.resample(0.05, i, sync=True)
+            except pa.PAError as e:
+                assert e.status == pa.PA_ERR_CAPACITY
+                assert np.array_equal(pop.spins(), before)
+                hit = True
+                break
+            beta += 0.05
+            pop.sweep(beta, 2, i)
+        assert hit, "population never exceeded a capacity equal to R"
+        # the context is usable again at the previous step
+        pop.resample(0.0, i + 1, sync=True)
+        pop.sweep(beta, 1, i + 1)
+
+
+def test_call_order_is_enforced():
+    p = pa.PAParams(q=4, L=8, R=50, seed=1)
+    with pa.Population(p) as pop:
+        with pytest.raises(pa.PAError) as e:
+            pop.sweep(0.1, 1, 3)  # no resample pending for step 3
+        assert e.value.status == pa.PA_ERR_STATE
+        pop.resample(0.1, 1)
+        with pytest.raises(pa.PAError):
+            pop.resample(0.1, 2)  # one already pending
+        pop.sweep(0.1, 1, 1)
+        with pytest.raises(pa.PAError):
+            pop.resample(0.1, 1)  # step must increase
+
+
+# ---------------------------------------------------------------------------
+# Plain PA at scale (q = 10, L = 64, R = 100000, theta = 10) in the launch
+# shape the benchmark uses: step 1 on sampled slots, which the oracle can
+# recompute one by one from the initial state, plus every initial energy.
+# ---------------------------------------------------------------------------
+def _init_energies(args):
+    q, L, begin, count, seed = args
+    import oracle as orc
+
+    s = orc.init_random(q, L, begin, count, seed)
+    return np.array([orc.energy(x) for x in s], dtype=np.int32)
+
+
+def test_plain_at_scale_step_one_sampled():
+    w = wl.C2
+    b = w.betas()
+    p = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed)
+    rng = np.random.default_rng(2024)
+    with pa.Population(p) as pop:
+        E0 = pop.energies()
+        lnq, R1 = pop.resample(b[1] - b[0], 1, sync=True)
+        pop.sweep(b[1], w.theta, 1)
+        E1 = pop.energies()
+        assert E1.size == R1
+        sample = np.unique(np.concatenate([rng.integers(0, R1, 48), [0, R1 - 1]]))
+        spins = {int(s): pop.spins(int(s), 1)[0] for s in sample}
+        o1, h1 = pop.observables(with_hist=True)
+
+    chunks = [(w.q, w.L, k, min(6250, w.R - k), w.seed) for k in range(0, w.R, 6250)]
+    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as poolp:
+        E0_ref = np.concatenate(poolp.map(_init_energies, chunks))
+    assert np.array_equal(E0, E0_ref)
+    r, lnq_ref, R1_ref, rho = oracle.copy_numbers(E0_ref, b[1] - b[0], w.R, oracle.NEAREST_INT, 1, w.seed)
+    assert R1 == R1_ref
+    assert lnq == pytest.approx(lnq_ref, rel=LNZ_RTOL)
+    parents = oracle.parents(r)
+    for s, got in spins.items():
+        init = oracle.init_random(w.q, w.L, int(parents[s]), 1, w.seed)[0]
+        ref = oracle.sweep_replica(w.q, init, b[1], w.theta, 1, s, w.seed)
+        assert np.array_equal(got, ref), s
+        assert E1[s] == oracle.energy(ref)
+    # properties that hold at any size
+    assert h1.sum() == R1 and np.array_equal(np.bincount(E1 + 2 * w.N, minlength=2 * w.N + 1), h1)
+    assert o1["sumE"] == int(E1.astype(np.int64).sum())
+
+
+def test_plain_at_scale_launch_shape_reduced_population():
+    """Three full steps at L = 64, q = 10, theta = 10 with R = 3000 in the
+    block shape the benchmark picks for R = 100000 (16 replicas x 512 threads)."""
+    w = wl.C2
+    b = w.betas()[:4]
+    R = 3000
+    g = _gpu_run(w.q, w.L, R, w.seed, w.theta, b, launch=(16, 512))
+    o = _oracle_run(w.q, w.L, R, w.seed, w.theta, b)
+    _compare(g, o)
