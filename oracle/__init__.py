@@ -64,7 +64,7 @@ def lib():
         L.orc_max_count.argtypes = [ctypes.c_int, ctypes.c_int, P]
         L.orc_max_count.restype = i64
         L.orc_thresholds.argtypes = [f64, P]
-        L.orc_metropolis_decide.argtypes = [ctypes.c_int, ctypes.c_int, P, u32, u32, P]
+        L.orc_metropolis_decide.argtypes = [ctypes.c_int, ctypes.c_int, P, u32, P]
         L.orc_metropolis_decide.restype = ctypes.c_int
         L.orc_sweep_replica.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, u32, u32, u64]
         L.orc_init_random.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, P]
@@ -114,10 +114,10 @@ def thresholds(beta: float) -> np.ndarray:
     return t
 
 
-def metropolis_decide(q, cur, nb, u0, u1, thr) -> int:
+def metropolis_decide(q, cur, nb, u, thr) -> int:
     n = np.ascontiguousarray(nb, dtype=np.int32)
     t = np.ascontiguousarray(thr, dtype=np.uint32)
-    return int(lib().orc_metropolis_decide(q, cur, _p(n), int(u0), int(u1), _p(t)))
+    return int(lib().orc_metropolis_decide(q, cur, _p(n), int(u), _p(t)))
 
 
 def sweep_replica(q: int, spins: np.ndarray, beta: float, theta: int, step: int, slot: int, seed: int) -> np.ndarray:

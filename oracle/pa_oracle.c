@@ -120,10 +120,15 @@ ORC_API int64_t orc_max_count(int q, int L, const uint8_t *s)
 
 /* ------------------------------------------------------------------------- */
 /* Metropolis single-spin-flip update (Sec. 2 step 3, Sec. 3).                */
-/* reading: the proposal is uniform over the q-1 other states,                 */
-/*   s' = (s + 1 + floor(u0 (q-1) / 2^32)) mod q,                              */
-/* and the move is accepted iff u1 < T[dE], where dE = E(s') - E(s) is an      */
-/* integer in [-4, 4] and T[d] = min(2^32 - 1, floor(min(1, exp(-beta d)) 2^32)). */
+/* reading: one 32-bit random word u per attempt.  With k = q - 1, the 64-bit */
+/* product u k splits into a high word, the proposal offset m = floor(u k /   */
+/* 2^32), uniform over 0..q-2, and a low word v = u k mod 2^32, the position  */
+/* of u inside its proposal bin, which serves as the acceptance uniform:      */
+/*   s' = (s + 1 + m) mod q,  accepted iff v < T[dE],                         */
+/* where dE = E(s') - E(s) is an integer in [-4, 4] and                       */
+/* T[d] = min(2^32 - 1, floor(min(1, exp(-beta d)) 2^32)).  Given m, v runs   */
+/* over every (q-1)-th value of [0, 2^32), so the acceptance probability is   */
+/* T / 2^32 to within (q-1) / 2^32.                                           */
 /* ------------------------------------------------------------------------- */
 ORC_API void orc_thresholds(double beta, uint32_t thr[9])
 {
@@ -136,12 +141,14 @@ ORC_API void orc_thresholds(double beta, uint32_t thr[9])
     }
 }
 
-/* One attempt on a site in state `cur` whose four neighbours are nb[0..3].
- * Returns the state after the attempt. */
-ORC_API int orc_metropolis_decide(int q, int cur, const int nb[4], uint32_t u0, uint32_t u1,
-                                  const uint32_t thr[9])
+/* One attempt on a site in state `cur` whose four neighbours are nb[0..3],
+ * driven by the random word u.  Returns the state after the attempt. */
+ORC_API int orc_metropolis_decide(int q, int cur, const int nb[4], uint32_t u, const uint32_t thr[9])
 {
-    int prop = (cur + 1 + (int)orc_scale(u0, (uint32_t)(q - 1))) % q;
+    uint64_t prod = (uint64_t)u * (uint64_t)(q - 1);
+    int m = (int)(prod >> 32);
+    uint32_t v = (uint32_t)prod;
+    int prop = (cur + 1 + m) % q;
     int n_cur = 0, n_prop = 0;
     for (int k = 0; k < 4; ++k) {
         if (nb[k] == cur) n_cur += 1;
@@ -150,7 +157,7 @@ ORC_API int orc_metropolis_decide(int q, int cur, const int nb[4], uint32_t u0, 
     /* E = -(number of satisfied bonds): moving cur -> prop changes E by
      * n_cur - n_prop. */
     int dE = n_cur - n_prop;
-    if (u1 < thr[dE + 4]) return prop;
+    if (v < thr[dE + 4]) return prop;
     return cur;
 }
 
@@ -167,8 +174,8 @@ static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
  * colour-1 sites.  With L even no two sites of one colour are neighbours, so
  * this in-place row-major order equals a simultaneous update of each colour.
  * Random words: site (x, y) has sublattice index h = (y L + x) >> 1; the
- * Philox call with counter (h >> 1, SWEEP | (2k + colour), step, slot) serves
- * the sites h and h^1, words (0,1) going to the even h and (2,3) to the odd. */
+ * Philox call with counter (h >> 2, SWEEP | (2k + colour), step, slot) serves
+ * the four sites with the same h >> 2 of that colour, word h & 3 going to h. */
 ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint32_t thr[9], int theta,
                                uint32_t step, uint32_t slot, uint64_t seed)
 {
@@ -179,12 +186,10 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint32_t thr[9], 
                     if (((x + y) & 1) != colour) continue;
                     uint32_t h = (uint32_t)(y * L + x) >> 1;
                     uint32_t w[4];
-                    orc_draw(seed, h >> 1, ORC_DOM_SWEEP | (uint32_t)(2 * k + colour), step, slot, w);
-                    uint32_t u0 = w[2 * (h & 1)];
-                    uint32_t u1 = w[2 * (h & 1) + 1];
+                    orc_draw(seed, h >> 2, ORC_DOM_SWEEP | (uint32_t)(2 * k + colour), step, slot, w);
                     int nb[4];
                     orc_neighbours(L, s, x, y, nb);
-                    s[y * L + x] = (uint8_t)orc_metropolis_decide(q, s[y * L + x], nb, u0, u1, thr);
+                    s[y * L + x] = (uint8_t)orc_metropolis_decide(q, s[y * L + x], nb, w[h & 3], thr);
                 }
             }
         }
@@ -460,11 +465,22 @@ ORC_API int orc_density_of_states(int q, int L, uint64_t *g)
 
 /* Exact transition matrix of one Metropolis attempt at `site` (= y L + x) of an
  * L x L lattice, over all q^N configurations (index = sum_i s_i q^i).  The
- * probabilities are read off orc_metropolis_decide itself: the proposal classes
- * {u0 : floor(u0 (q-1)/2^32) = m} are located by bisection on u0, and for each
- * class the number of accepting u1 values by bisection on u1, so a mistake in
- * the update rule shows up in the matrix.  P is (q^N)^2 row-major, P[a][b] =
- * Prob(a -> b).  Returns -1 if q^N > 4096. */
+ * probabilities are read off orc_metropolis_decide itself: the random word u
+ * is split into the proposal bins {u : floor(u (q-1) / 2^32) = m}, located by
+ * bisection, and inside each bin (where acceptance holds for a prefix of u)
+ * the first rejecting u is located by bisection, so a mistake in the update
+ * rule shows up in the matrix.  P is (q^N)^2 row-major, P[a][b] = Prob(a -> b).
+ * Returns -1 if q^N > 4096. */
+static uint64_t orc_first_u_in_bin(int q, int m)
+{
+    uint64_t lo = 0, hi = 4294967296ull;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) / 2;
+        if (((uint64_t)mid * (uint64_t)(q - 1) >> 32) >= (uint64_t)m) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
 ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
 {
     int N = L * L;
@@ -475,6 +491,8 @@ ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
     orc_thresholds(beta, thr);
     memset(P, 0, sizeof(double) * (size_t)(n * n));
     int x = site % L, y = site / L;
+    int64_t place = 1;
+    for (int i = 0; i < site; ++i) place *= q;
     for (int64_t a = 0; a < n; ++a) {
         uint8_t s[64];
         int64_t t = a;
@@ -482,45 +500,22 @@ ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
         int nb[4];
         orc_neighbours(L, s, x, y, nb);
         int cur = s[site];
-        /* class boundaries lo[m] = smallest u0 with scale(u0, q-1) >= m */
         for (int m = 0; m < q - 1; ++m) {
-            uint64_t lo_m, lo_next;
-            {
-                uint64_t lo = 0, hi = 4294967296ull;
-                while (lo < hi) {
-                    uint64_t mid = (lo + hi) / 2;
-                    if (orc_scale((uint32_t)mid, (uint32_t)(q - 1)) >= (uint32_t)m) hi = mid; else lo = mid + 1;
-                }
-                lo_m = lo;
-            }
-            {
-                uint64_t lo = 0, hi = 4294967296ull;
-                while (lo < hi) {
-                    uint64_t mid = (lo + hi) / 2;
-                    if (orc_scale((uint32_t)mid, (uint32_t)(q - 1)) >= (uint32_t)(m + 1)) hi = mid; else lo = mid + 1;
-                }
-                lo_next = lo;
-            }
-            double p_class = (double)(lo_next - lo_m) / 4294967296.0;
-            uint32_t u0 = (uint32_t)lo_m;
-            /* accepted iff the state changes; acceptance is u1 < T, so find the
-             * smallest rejecting u1 */
-            uint64_t lo = 0, hi = 4294967296ull;
+            uint64_t first = orc_first_u_in_bin(q, m);
+            uint64_t end = orc_first_u_in_bin(q, m + 1);
+            /* smallest u in [first, end) whose attempt is rejected */
+            uint64_t lo = first, hi = end;
             while (lo < hi) {
                 uint64_t mid = (lo + hi) / 2;
-                if (orc_metropolis_decide(q, cur, nb, u0, (uint32_t)mid, thr) == cur) hi = mid; else lo = mid + 1;
+                if (orc_metropolis_decide(q, cur, nb, (uint32_t)mid, thr) == cur) hi = mid; else lo = mid + 1;
             }
-            double p_acc = (double)lo / 4294967296.0;
+            double p_acc = (double)(lo - first) / 4294967296.0;
+            double p_rej = (double)(end - lo) / 4294967296.0;
             int prop = cur;
-            if (lo > 0) prop = orc_metropolis_decide(q, cur, nb, u0, 0u, thr);
-            int64_t b = a;
-            if (prop != cur) {
-                int64_t place = 1;
-                for (int i = 0; i < site; ++i) place *= q;
-                b = a + (int64_t)(prop - cur) * place;
-            }
-            P[a * n + b] += p_class * p_acc;
-            P[a * n + a] += p_class * (1.0 - p_acc);
+            if (lo > first) prop = orc_metropolis_decide(q, cur, nb, (uint32_t)first, thr);
+            int64_t b = a + (int64_t)(prop - cur) * place;
+            P[a * n + b] += p_acc;
+            P[a * n + a] += p_rej;
         }
     }
     return 0;

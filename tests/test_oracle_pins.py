@@ -181,7 +181,8 @@ def test_site_kernels_satisfy_detailed_balance(q, beta):
         P = oracle.site_matrix(q, L, site, beta)
         assert np.allclose(P.sum(axis=1), 1.0, atol=1e-14)
         flow = pi[:, None] * P
-        # the 32-bit quantisation of proposals and thresholds bounds the asymmetry
+        # the 32-bit quantisation of proposals, thresholds and acceptance words
+        # bounds the asymmetry by about (q - 1) 2^-32 relative to pi
         assert np.max(np.abs(flow - flow.T)) <= 1e-8 * pi.max()
         sweep = sweep @ P
     assert np.max(np.abs(pi @ sweep - pi)) < 1e-8
@@ -201,14 +202,39 @@ def test_thresholds_are_quantised_boltzmann_factors():
 
 
 def test_proposal_never_repeats_current_state():
+    """At beta = 0 every move is accepted (T = 2^32 - 1 > v except for the
+    single low word 2^32 - 1): the proposal is always another state, and the
+    q - 1 others are reached from bins of equal width."""
     thr = oracle.thresholds(0.0)
     rng = np.random.default_rng(3)
     for q in (2, 3, 10, 20):
-        for _ in range(200):
+        seen = np.zeros(q, int)
+        for _ in range(400):
             cur = int(rng.integers(q))
-            u0 = int(rng.integers(2**32))
-            new = oracle.metropolis_decide(q, cur, [cur, cur, cur, cur], u0, 0, thr)
+            u = int(rng.integers(2**32))
+            new = oracle.metropolis_decide(q, cur, [cur, cur, cur, cur], u, thr)
             assert new != cur and 0 <= new < q
+            seen[(new - cur - 1) % q] += 1
+        assert seen[: q - 1].min() > 0 and seen[q - 1] == 0
+
+
+def test_acceptance_uses_position_inside_proposal_bin():
+    """Inside one proposal bin, acceptance holds exactly for the words whose
+    low product word is below the threshold: a prefix of the bin of length
+    about T / (q - 1)."""
+    q = 10
+    beta = 1.3
+    thr = oracle.thresholds(beta)
+    nb = [0, 0, 0, 0]  # a site in state 0 with all neighbours 0: any move costs dE = 4
+    for m in (0, 4, 8):
+        first = -(-(m << 32) // (q - 1))
+        end = -(-((m + 1) << 32) // (q - 1))
+        acc = [oracle.metropolis_decide(q, 0, nb, u, thr) != 0 for u in (first, first + 1, end - 1)]
+        assert acc == [True, True, False]
+        # the first rejected word: v = u (q - 1) mod 2^32 reaches T[4]
+        k = -(-(int(thr[8]) + (m << 32)) // (q - 1))
+        assert oracle.metropolis_decide(q, 0, nb, k - 1, thr) != 0
+        assert oracle.metropolis_decide(q, 0, nb, k, thr) == 0
 
 
 # --------------------------------------------------------------------------
