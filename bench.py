@@ -34,11 +34,13 @@ from paper_1704_01888_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "spin-flip attempts/ns & PA steps/s, q=10 L=64 R=1e5; batched vs plain, %roofline"
 UNIT = "attempts/ns"
-# Algorithmic integer operations per Metropolis attempt: half a Philox4x32-10
-# call (10 rounds of 2 wide multiplies + 2 three-input xors = 40 per call, 20
-# per attempt), the proposal, the neighbour comparison and the threshold test
-# (about 30 more) -- the per-attempt figure the issue roofline is taken over.
-OPS_PER_ATTEMPT = 50
+# Algorithmic integer issue slots per Metropolis attempt, counted for a scalar
+# implementation with a 64-bit product as two slots: a quarter of a
+# Philox4x32-10 call (10 rounds x (2 products x 2 + 2 three-input xors) = 60
+# per call, 15 per attempt), the product u (q - 1) (2), the proposal modulo q
+# (2), eight neighbour equality tests with their two sums (9), the threshold
+# compare and select (2): 30 in all.  The issue roofline divides by this.
+OPS_PER_ATTEMPT = 30
 LANES_PER_SM_PER_CLK = 128  # 4 schedulers x 32 lanes issue one integer op each per clock
 PA_OBS_BYTES = 104
 DEVSTATE_BYTES = 48
@@ -53,11 +55,14 @@ def _args():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c5"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--R", type=int, default=0, help="override the population size (profiling runs)")
+    ap.add_argument("--launch", default="", help="replicas_per_block,threads_per_block for the sweep kernel")
     return ap.parse_args()
 
 
-def _workload(name):
-    return {"c1": wl.C1, "c2": wl.C2, "c5": wl.C5}[name]
+def _workload(name, R=0):
+    w = {"c1": wl.C1, "c2": wl.C2, "c5": wl.C5}[name]
+    return wl.scaled(w, R=R, name=f"{w.name}-R{R}") if R else w
 
 
 def _betas(w, n):
@@ -131,16 +136,21 @@ class Clocks:
 
 def _sweep_traffic_per_replica():
     """DRAM bytes per replica per sweep launch from the committed ncu summary,
-    valid only while the sweep kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    valid only while the sweep kernel sources are unchanged."""
+    rec = {}
     try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
+        for line in open(os.path.join(ROOT, "profiles", "sweep_traffic.txt")):
+            if line.startswith("#") or ":" not in line:
+                continue
+            key, val = line.split(":", 1)
+            rec[key.strip()] = val.strip()
+    except OSError:
         return None
-    src = open(os.path.join(ROOT, "paper_1704_01888_gb300", "csrc", "pa_sweep.cu"), "rb").read()
-    if rec.get("pa_sweep_cu_sha256") != hashlib.sha256(src).hexdigest():
+    csrc = os.path.join(ROOT, "paper_1704_01888_gb300", "csrc")
+    src = open(os.path.join(csrc, "pa_sweep.cu"), "rb").read() + open(os.path.join(csrc, "pa_internal.cuh"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
-    return rec.get("dram_bytes_per_replica")
+    return float(rec["dram_bytes_per_replica"])
 
 
 def _cpu_baseline(w, R_sample=1000, steps=3):
@@ -166,7 +176,7 @@ def run_reference(args):
     import oracle
 
     oracle.build()
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.R)
     R_sample = 64 if w.N >= 16384 else 256
     W, K = args.warmup, args.steps
     bw = _betas(w, W)
@@ -213,13 +223,16 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
 
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.R)
     W, K = args.warmup, args.steps
     betas = _betas(w, W + K)
+    launch = tuple(int(x) for x in args.launch.split(",")) if args.launch else None
     params = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed + rank, track_families=w.track_families)
     stream = torch.cuda.current_stream()
 
     pop = pa.Population(params)
+    if launch:
+        pop.set_launch(*launch)
     for i in range(1, W + 1):
         pop.resample(betas[i] - betas[i - 1], i)
         pop.sweep(betas[i], w.theta, i)
@@ -227,6 +240,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    launch_used = pop.launch_shape()
 
     pop.profile(True)
     launches0 = pa.kernel_launch_count()
@@ -275,7 +289,9 @@ def run_ours(args):
     tpr = _sweep_traffic_per_replica()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": (tpr * per_launch_attempts / (w.N * w.theta)) if tpr else None,
-                "kernel": "k_sweep_words", "ops_per_attempt": OPS_PER_ATTEMPT,
+                "traffic_unit": "bytes per launch (ncu dram read + write, scaled by replicas)",
+                "algorithmic_bytes_per_launch": 2 * w.N * per_launch_attempts / (w.N * w.theta),
+                "kernel": "k_sweep_rows", "ops_per_attempt": OPS_PER_ATTEMPT,
                 "kernel_ms_avg": sweep_avg_s * 1e3, "kernel_share": sweep_ms / elapsed_ms,
                 "peak_basis": f"{sms} SMs x {LANES_PER_SM_PER_CLK} lanes x {f_max / 1e6:.0f} MHz (max SM clock)"}
     if clocks.get("sm_mhz"):
@@ -283,7 +299,7 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = _e2e(pa, w, params, betas, W, K, rank, world)
+        e2e = _e2e(pa, w, params, betas, W, K, rank, world, launch)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -297,7 +313,8 @@ def run_ours(args):
                    "beta": f"0 -> {w.beta_end} in {w.K} equal steps (timed steps {W + 1}..{W + K})",
                    "parallelism": f"independent populations x{world}",
                    "l2": f"inputs larger than L2: 2 x {w.R * w.N / 1e6:.0f} MB spin buffers",
-                   "launch": None},
+                   "launch": {"replicas_per_block": launch_used[0], "threads_per_block": launch_used[1],
+                              "blocks": launch_used[2]}},
         "pa_steps_per_s": K / (elapsed_ms / 1e3),
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -315,13 +332,15 @@ def run_ours(args):
     return 0
 
 
-def _e2e(pa, w, params, betas, W, K, rank, world):
+def _e2e(pa, w, params, betas, W, K, rank, world, launch):
     """The same metric through the public API as a user drives it: each step
     resamples with a host read of ln Q and R_i, sweeps, and reads the step's
     estimators and energy histogram into host memory."""
     import torch
 
     pop = pa.Population(params)
+    if launch:
+        pop.set_launch(*launch)
     for i in range(1, W + 1):
         pop.resample(betas[i] - betas[i - 1], i)
         pop.sweep(betas[i], w.theta, i)

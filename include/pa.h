@@ -188,6 +188,10 @@ const char *pa_last_cuda_error(void);
  * exists for autotuning and for tests that check exactly that. */
 pa_status pa_set_launch(pa_ctx *ctx, int32_t replicas_per_block, int32_t threads_per_block);
 
+/* The sweep kernel's current launch shape: replicas per block, threads per
+ * block and blocks (persistent grid).  Any pointer may be NULL. */
+pa_status pa_get_launch(pa_ctx *ctx, int32_t *replicas_per_block, int32_t *threads_per_block, int32_t *blocks);
+
 /* Number of kernels this library has launched on any context since the
  * process started (a host-side counter; graph launches count their nodes). */
 int64_t pa_kernel_launch_count(void);

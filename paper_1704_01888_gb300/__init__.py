@@ -34,6 +34,7 @@ EXPORTED = (
     "pa_init", "pa_resample", "pa_sweep", "pa_energy", "pa_observables", "pa_population_size",
     "pa_get_spins", "pa_get_ancestors", "pa_run", "pa_destroy", "pa_status_str", "pa_last_cuda_error",
     "pa_set_launch", "pa_kernel_launch_count", "pa_profile", "pa_profile_read", "pa_observables_history",
+    "pa_get_launch",
 )
 
 
@@ -97,6 +98,7 @@ def load_library(path: str | None = None):
         "pa_profile": ([P, i32], st),
         "pa_profile_read": ([P, P, P], st),
         "pa_observables_history": ([P, i32, P], st),
+        "pa_get_launch": ([P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +247,12 @@ class Population:
 
     def set_launch(self, replicas_per_block: int = 0, threads_per_block: int = 0):
         _check(self.lib.pa_set_launch(self._ctx, replicas_per_block, threads_per_block), "pa_set_launch")
+
+    def launch_shape(self):
+        """(replicas per block, threads per block, blocks) of the sweep kernel."""
+        v = [ctypes.c_int32() for _ in range(3)]
+        _check(self.lib.pa_get_launch(self._ctx, *[ctypes.byref(x) for x in v]), "pa_get_launch")
+        return tuple(x.value for x in v)
 
     def profile(self, enable: bool = True):
         _check(self.lib.pa_profile(self._ctx, int(enable)), "pa_profile")

@@ -188,6 +188,10 @@ pa::SweepArgs sweep_args(pa_ctx *c, double beta, int theta, int step, int gather
     thresholds(beta, a.thr);
     a.k0 = c->k0;
     a.k1 = c->k1;
+    for (int r = 0; r < 10; ++r) {
+        a.rk0[r] = c->k0 + 0x9E3779B9u * (uint32_t)r;
+        a.rk1[r] = c->k1 + 0xBB67AE85u * (uint32_t)r;
+    }
     a.q = c->cfg.q;
     a.L = c->cfg.L;
     a.theta = theta;
@@ -360,6 +364,15 @@ pa_status pa_set_launch(pa_ctx *c, int32_t replicas_per_block, int32_t threads_p
     if (!c) return PA_ERR_INVALID;
     if (replicas_per_block < 0 || threads_per_block < 0) return PA_ERR_INVALID;
     return choose_launch(c, replicas_per_block, threads_per_block);
+}
+
+pa_status pa_get_launch(pa_ctx *c, int32_t *rpb, int32_t *threads, int32_t *blocks)
+{
+    if (!c) return PA_ERR_INVALID;
+    if (rpb) *rpb = c->rpb;
+    if (threads) *threads = c->threads;
+    if (blocks) *blocks = c->grid;
+    return PA_OK;
 }
 
 pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, int32_t *R_out)

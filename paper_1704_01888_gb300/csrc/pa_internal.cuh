@@ -55,6 +55,7 @@ struct SweepArgs {
     DevState *st;
     uint32_t thr[9];           // acceptance thresholds T[dE + 4]
     uint32_t k0, k1;           // Philox key (seed low / high word)
+    uint32_t rk0[10], rk1[10]; // Philox round keys k + r * (Weyl constant), r = 0..9
     int32_t q, L, theta, step;
     int32_t rpb;               // replicas per block iteration
     int32_t gather;            // 1: read parents from buf[parity], write buf[parity^1]
@@ -96,6 +97,20 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
                        (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The same generator with its ten round keys supplied by the caller (kernel
+// parameters), so no key arithmetic runs per call.
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t *rk0, const uint32_t *rk1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[round], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk1[round], (uint32_t)p0);
     }
     return c;
 }

@@ -13,10 +13,10 @@
 // same-colour sites held in one 32-bit word.  Their neighbours are the
 // aligned words of the other colour in the rows above and below and in the
 // same row, plus that row word shifted by one byte.  Neighbour agreement is
-// counted four bytes at a time (SWAR), and each site draws its proposal and
-// acceptance words from Philox.  Lattices with other even L use a per-site
-// kernel with the same random-number assignment, so both give identical
-// results.
+// counted four bytes at a time (SWAR).  Each site takes one 32-bit Philox
+// word u: the high and low halves of u (q-1) are its proposal offset and its
+// acceptance uniform.  Lattices with other even L use a per-site kernel with
+// the same random-number assignment, so both give identical results.
 #include "pa_internal.cuh"
 
 namespace pa {
@@ -85,12 +85,51 @@ __device__ __forceinline__ void record_replica(const SweepArgs &a, int slot, int
 }
 
 // ---------------------------------------------------------------------------
-// Word kernel: L % 8 == 0.  LT > 0 fixes L at compile time.
+// Row-segment kernel: L % 8 == 0.  LT > 0 fixes L at compile time; S is the
+// number of 32-bit words (4 same-colour sites each) one thread updates per
+// step of its loop: S consecutive words of one row of one colour, read and
+// written with one vector access per neighbour row.
 // ---------------------------------------------------------------------------
+template <int S>
+struct Vec;
+template <>
+struct Vec<1> {
+    uint32_t v[1];
+    __device__ __forceinline__ void load(const uint32_t *p) { v[0] = p[0]; }
+    __device__ __forceinline__ void store(uint32_t *p) const { p[0] = v[0]; }
+};
+template <>
+struct Vec<2> {
+    uint32_t v[2];
+    __device__ __forceinline__ void load(const uint32_t *p)
+    {
+        const uint2 x = *reinterpret_cast<const uint2 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    }
+    __device__ __forceinline__ void store(uint32_t *p) const { *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]); }
+};
+template <>
+struct Vec<4> {
+    uint32_t v[4];
+    __device__ __forceinline__ void load(const uint32_t *p)
+    {
+        const uint4 x = *reinterpret_cast<const uint4 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    }
+    __device__ __forceinline__ void store(uint32_t *p) const
+    {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+};
+
 using KernelFnPtr = void (*)(const SweepArgs);
 
-template <int LT>
-__global__ void __launch_bounds__(1024) k_sweep_words(const SweepArgs a)
+template <int LT, int S>
+__global__ void __launch_bounds__(1024) k_sweep_rows(const SweepArgs a)
 {
     extern __shared__ uint4 smem4[];
     __shared__ uint32_t s_thr[9];
@@ -98,10 +137,12 @@ __global__ void __launch_bounds__(1024) k_sweep_words(const SweepArgs a)
 
     const int L = LT > 0 ? LT : a.L;
     const int N = L * L;
-    const int L8 = L / 8;
+    const int L8 = L / 8;    // words per row of one colour
     const int WPC = N / 8;   // words per colour per replica
     const int WPR = N / 4;   // words per replica
     const int UPR = N / 16;  // uint4 per replica
+    const int SPR = L8 / S;  // segments per row
+    const int UPC = L * SPR; // segments per colour per replica
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -119,6 +160,7 @@ __global__ void __launch_bounds__(1024) k_sweep_words(const SweepArgs a)
     const uint32_t qm1 = (uint32_t)(a.q - 1);
     const uint32_t qb = (uint32_t)a.q;
     const bool write_back = a.gather || a.theta > 0;
+    const char *thr_bytes = reinterpret_cast<const char *>(s_thr);
 
     long long sE = 0, sE2 = 0, sM = 0;
     for (int g = blockIdx.x; g * a.rpb < R; g += gridDim.x) {
@@ -138,41 +180,61 @@ __global__ void __launch_bounds__(1024) k_sweep_words(const SweepArgs a)
         for (int k = 0; k < a.theta; ++k) {
             for (int c = 0; c < 2; ++c) {
                 const uint32_t ctr1 = DOM_SWEEP | (uint32_t)(2 * k + c);
-                for (int i = tid; i < nrep * WPC; i += blockDim.x) {
-                    const int r = i / WPC;
-                    const int w = i - r * WPC;
-                    const int y = w / L8;
-                    const int t = w - y * L8;
-                    uint32_t *rep = sw + r * WPR;
-                    uint32_t *own = rep + c * WPC;
-                    const uint32_t *oth = rep + (c ^ 1) * WPC;
-                    const Neighbours nb = load_neighbours(oth, L, L8, y, t, (y + c) & 1);
-                    const uint32_t W = own[w];
-
-                    // sublattice index of byte 0 is y*L/2 + 4t; pairs (h>>1) and (h>>1)+1
-                    const uint32_t pair = (uint32_t)(y * (L / 2) + 4 * t) >> 1;
+                for (int i = tid; i < nrep * UPC; i += blockDim.x) {
+                    const int r = i / UPC;
+                    const int u = i - r * UPC;
+                    const int y = u / SPR;
+                    const int t0 = (u - y * SPR) * S;
+                    uint32_t *own = sw + r * WPR + c * WPC;
+                    const uint32_t *oth = sw + r * WPR + (c ^ 1) * WPC;
+                    const int p = (y + c) & 1;  // 0: horizontal neighbours at m-1, m; 1: at m, m+1
+                    const int row = y * L8;
+                    const int yu = (y == 0) ? L - 1 : y - 1;
+                    const int yd = (y == L - 1) ? 0 : y + 1;
+                    Vec<S> W, U, D, H;
+                    W.load(own + row + t0);
+                    U.load(oth + yu * L8 + t0);
+                    D.load(oth + yd * L8 + t0);
+                    H.load(oth + row + t0);
+                    const int te = p ? (t0 + S == L8 ? 0 : t0 + S) : (t0 == 0 ? L8 - 1 : t0 - 1);
+                    const uint32_t edge = oth[row + te];
+                    const uint32_t sh = p ? 8u : 24u;
+                    // sublattice index of byte 0 of word t0 is y*L/2 + 4*t0; one Philox
+                    // call serves the four sites of a word (counter = index / 4)
+                    const uint32_t quad0 = (uint32_t)(y * (L / 8) + t0);
                     const uint32_t slot = (uint32_t)(first + r);
-                    const uint4 ra = philox10(make_uint4(pair, ctr1, (uint32_t)a.step, slot), a.k0, a.k1);
-                    const uint4 rb = philox10(make_uint4(pair + 1, ctr1, (uint32_t)a.step, slot), a.k0, a.k1);
-
-                    // proposals s' = s + 1 + floor(u0 (q-1) / 2^32), reduced mod q bytewise
-                    const uint32_t m = __umulhi(ra.x, qm1) | (__umulhi(ra.z, qm1) << 8) |
-                                       (__umulhi(rb.x, qm1) << 16) | (__umulhi(rb.z, qm1) << 24);
-                    uint32_t P = W + m + 0x01010101u;
-                    const uint32_t ge = (P + (0x80u - qb) * 0x01010101u) & 0x80808080u;
-                    P -= (ge >> 7) * qb;
-
-                    // dE + 4 = differ(s') - differ(s) + 4 per byte, in 0..8
-                    const uint32_t dW = count_differ(W, nb.up, nb.down, nb.same, nb.shifted);
-                    const uint32_t dP = count_differ(P, nb.up, nb.down, nb.same, nb.shifted);
-                    const uint32_t idx = dP + 0x04040404u - dW;
-
-                    uint32_t sel = 0x3210u;
-                    if (ra.y < s_thr[idx & 0xFFu]) sel += 0x4u;
-                    if (ra.w < s_thr[(idx >> 8) & 0xFFu]) sel += 0x40u;
-                    if (rb.y < s_thr[(idx >> 16) & 0xFFu]) sel += 0x400u;
-                    if (rb.w < s_thr[idx >> 24]) sel += 0x4000u;
-                    own[w] = __byte_perm(W, P, sel);
+                    Vec<S> NW;
+#pragma unroll
+                    for (int j = 0; j < S; ++j) {
+                        const uint32_t lo = p ? H.v[j] : (j == 0 ? edge : H.v[j > 0 ? j - 1 : 0]);
+                        const uint32_t hi = p ? (j == S - 1 ? edge : H.v[j < S - 1 ? j + 1 : 0]) : H.v[j];
+                        const uint32_t shifted = __funnelshift_r(lo, hi, sh);
+                        const uint32_t Wj = W.v[j];
+                        // one word per site: (high, low) of u (q-1) = (proposal offset, acceptance uniform)
+                        const uint4 ru = philox10_rk(make_uint4(quad0 + j, ctr1, (uint32_t)a.step, slot), a.rk0,
+                                                     a.rk1);
+                        const uint32_t m = __umulhi(ru.x, qm1) | (__umulhi(ru.y, qm1) << 8) |
+                                           (__umulhi(ru.z, qm1) << 16) | (__umulhi(ru.w, qm1) << 24);
+                        // proposals s' = s + 1 + m, reduced mod q bytewise
+                        uint32_t P = Wj + m + 0x01010101u;
+                        const uint32_t ge = (P + (0x80u - qb) * 0x01010101u) & 0x80808080u;
+                        P -= (ge >> 7) * qb;
+                        // 4 (dE + 4) per byte: byte offsets into the threshold table
+                        const uint32_t dW = count_differ(Wj, U.v[j], D.v[j], H.v[j], shifted);
+                        const uint32_t dP = count_differ(P, U.v[j], D.v[j], H.v[j], shifted);
+                        const uint32_t idx4 = (dP + 0x04040404u - dW) << 2;
+                        const uint32_t T0 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4440));
+                        const uint32_t T1 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4441));
+                        const uint32_t T2 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4442));
+                        const uint32_t T3 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4443));
+                        uint32_t sel = 0x3210u;
+                        sel += (ru.x * qm1 < T0) ? 0x4u : 0u;
+                        sel += (ru.y * qm1 < T1) ? 0x40u : 0u;
+                        sel += (ru.z * qm1 < T2) ? 0x400u : 0u;
+                        sel += (ru.w * qm1 < T3) ? 0x4000u : 0u;
+                        NW.v[j] = __byte_perm(Wj, P, sel);
+                    }
+                    NW.store(own + row + t0);
                 }
                 __syncthreads();
             }
@@ -281,16 +343,15 @@ __global__ void __launch_bounds__(1024) k_sweep_sites(const SweepArgs a)
                     const int n0 = oth[yu * L2 + m], n1 = oth[yd * L2 + m], n2 = oth[y * L2 + m],
                               n3 = oth[y * L2 + mo];
                     const int s = own[h];
-                    const uint4 rw = philox10(make_uint4((uint32_t)h >> 1, ctr1, (uint32_t)a.step,
-                                                         (uint32_t)(first + r)),
-                                              a.k0, a.k1);
-                    const uint32_t u0 = (h & 1) ? rw.z : rw.x;
-                    const uint32_t u1 = (h & 1) ? rw.w : rw.y;
-                    int prop = s + 1 + (int)__umulhi(u0, qm1);
+                    const uint4 rw = philox10_rk(make_uint4((uint32_t)h >> 2, ctr1, (uint32_t)a.step,
+                                                            (uint32_t)(first + r)),
+                                                 a.rk0, a.rk1);
+                    const uint32_t u = pick_word(rw, h & 3);
+                    int prop = s + 1 + (int)__umulhi(u, qm1);
                     if (prop >= a.q) prop -= a.q;
                     const int ns = (n0 == s) + (n1 == s) + (n2 == s) + (n3 == s);
                     const int np = (n0 == prop) + (n1 == prop) + (n2 == prop) + (n3 == prop);
-                    if (u1 < s_thr[ns - np + 4]) own[h] = (uint8_t)prop;
+                    if (u * qm1 < s_thr[ns - np + 4]) own[h] = (uint8_t)prop;
                 }
                 __syncthreads();
             }
@@ -356,13 +417,16 @@ KernelFnPtr pick_kernel(int L)
 {
     if (L % 8 != 0) return k_sweep_sites;
     switch (L) {
-    case 16: return k_sweep_words<16>;
-    case 32: return k_sweep_words<32>;
-    case 48: return k_sweep_words<48>;
-    case 64: return k_sweep_words<64>;
-    case 128: return k_sweep_words<128>;
-    case 256: return k_sweep_words<256>;
-    default: return k_sweep_words<0>;
+    case 16: return k_sweep_rows<16, 2>;
+    case 32: return k_sweep_rows<32, 4>;
+    case 48: return k_sweep_rows<48, 2>;
+    case 64: return k_sweep_rows<64, 4>;
+    case 128: return k_sweep_rows<128, 4>;
+    case 256: return k_sweep_rows<256, 4>;
+    default:
+        if ((L / 8) % 4 == 0) return k_sweep_rows<0, 4>;
+        if ((L / 8) % 2 == 0) return k_sweep_rows<0, 2>;
+        return k_sweep_rows<0, 1>;
     }
 }
 
