@@ -50,7 +50,9 @@ typedef enum {
     PA_ERR_CUDA = 3,     /* a CUDA runtime call failed; see pa_last_cuda_error */
     PA_ERR_TIMEOUT = 4,  /* a bounded device wait gave up                      */
     PA_ERR_STATE = 5,    /* calls in the wrong order, or a failed context      */
-    PA_ERR_NOMEM = 6     /* device or host allocation failed                   */
+    PA_ERR_NOMEM = 6,    /* device or host allocation failed                   */
+    PA_ERR_TOO_LARGE = 7 /* a size exceeds the fixed working memory of
+                            pa_resample_noalloc                              */
 } pa_status;
 
 /* Copy-number rule for the resampling step (Sec. 2, step 2).  The paper draws
@@ -206,6 +208,36 @@ pa_status pa_profile(pa_ctx *ctx, int32_t enable);
  * counts recorded since profiling was enabled: [0] sweep kernel, [1]
  * resampling kernels.  Any pointer may be NULL. */
 pa_status pa_profile_read(pa_ctx *ctx, double *ms_out2, int64_t *launches_out2);
+
+/* Resampling without any device allocation.  This call has no counterpart in
+ * the paper: it exists for callers that may not allocate device memory --
+ * code running while a CUDA graph is being captured in a mode that forbids
+ * allocation, plug-ins whose host framework owns every device allocation,
+ * and runtimes that must not call the allocator once set up.
+ *
+ * It computes, for the R_prev energies E[0..R_prev) (device int32, each in
+ * [-2N, 0], N = L*L) of a population, the same quantities as pa_resample: ln Q
+ * for the step dbeta, the copy numbers under `mode` (random words keyed by
+ * seed and step) and the parent map of the new population,
+ * parent[0..R_i) (device int32, capacity parent_cap >= R_prev), with the new
+ * size in *R_out and ln Q in *lnQ_out (both device pointers).  The work is
+ * only enqueued on cuda_stream; read the outputs after synchronising.  If an
+ * energy lies outside [-2N, 0] *R_out becomes -PA_ERR_INVALID, and if R_i would
+ * exceed parent_cap, -PA_ERR_CAPACITY; parent is then unspecified.
+ *
+ * Working memory: one fixed array of about 3.6 MB inside the library's device
+ * image, held by every GPU that loads the library until the process exits.
+ * Limits: L <= 256, R_prev <= 262144, parent_cap <= 262144; larger sizes
+ * return PA_ERR_TOO_LARGE.  The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device current); make
+ * that first call before any stream capture.  All calls share the array and
+ * overwrite it: calls whose work overlaps on the GPU race, calls ordered on
+ * one stream do not.  Returns PA_ERR_INVALID for null pointers, odd L, R_prev
+ * < 1, R_target < 1, parent_cap < R_prev, an unknown mode or a non-finite
+ * dbeta, and PA_ERR_CUDA if a launch fails. */
+pa_status pa_resample_noalloc(const int32_t *E, int32_t R_prev, int32_t L, double dbeta, int32_t R_target,
+                              int32_t mode, int32_t step, uint64_t seed, int32_t *parent, int32_t parent_cap,
+                              double *lnQ_out, int32_t *R_out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
 
-PA_OK, PA_ERR_INVALID, PA_ERR_CAPACITY, PA_ERR_CUDA, PA_ERR_TIMEOUT, PA_ERR_STATE, PA_ERR_NOMEM = range(7)
+(PA_OK, PA_ERR_INVALID, PA_ERR_CAPACITY, PA_ERR_CUDA, PA_ERR_TIMEOUT, PA_ERR_STATE, PA_ERR_NOMEM,
+ PA_ERR_TOO_LARGE) = range(8)
 RESAMPLE_NEAREST_INT = 0
 RESAMPLE_ROUND = 1
 INIT_RANDOM = 0
@@ -34,7 +35,7 @@ EXPORTED = (
     "pa_init", "pa_resample", "pa_sweep", "pa_energy", "pa_observables", "pa_population_size",
     "pa_get_spins", "pa_get_ancestors", "pa_run", "pa_destroy", "pa_status_str", "pa_last_cuda_error",
     "pa_set_launch", "pa_kernel_launch_count", "pa_profile", "pa_profile_read", "pa_observables_history",
-    "pa_get_launch",
+    "pa_get_launch", "pa_resample_noalloc",
 )
 
 
@@ -99,6 +100,7 @@ def load_library(path: str | None = None):
         "pa_profile_read": ([P, P, P], st),
         "pa_observables_history": ([P, i32, P], st),
         "pa_get_launch": ([P, P, P, P], st),
+        "pa_resample_noalloc": ([P, i32, i32, f64, i32, i32, i32, ctypes.c_uint64, P, i32, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -127,6 +129,16 @@ def _current_stream() -> int:
     if not torch.cuda.is_available():
         raise RuntimeError("population annealing runs on a CUDA GPU; none is available")
     return torch.cuda.current_stream().cuda_stream
+
+
+def resample_noalloc(E_ptr: int, R_prev: int, L: int, dbeta: float, R_target: int, mode: int, step: int,
+                     seed: int, parent_ptr: int, parent_cap: int, lnQ_ptr: int, R_ptr: int, stream: int) -> None:
+    """pa_resample_noalloc on device pointers (see include/pa.h): resampling
+    for callers that may not allocate device memory.  Raises PAError on a
+    rejected call; the results land in the device outputs."""
+    _check(load_library().pa_resample_noalloc(
+        ctypes.c_void_p(E_ptr), R_prev, L, float(dbeta), R_target, mode, step, seed, ctypes.c_void_p(parent_ptr),
+        parent_cap, ctypes.c_void_p(lnQ_ptr), ctypes.c_void_p(R_ptr), ctypes.c_void_p(stream)), "pa_resample_noalloc")
 
 
 def kernel_launch_count() -> int:

@@ -265,6 +265,7 @@ const char *pa_status_str(pa_status s)
     case PA_ERR_TIMEOUT: return "device wait timed out";
     case PA_ERR_STATE: return "call out of order or context failed";
     case PA_ERR_NOMEM: return "out of memory";
+    case PA_ERR_TOO_LARGE: return "size exceeds the fixed working memory of the no-allocation entry point";
     }
     return "unknown status";
 }
