@@ -80,7 +80,13 @@ def lib():
         L.orc_density_of_states.restype = ctypes.c_int
         L.orc_site_matrix.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, f64, P]
         L.orc_site_matrix.restype = ctypes.c_int
-        L.orc_reweight.argtypes = [i64, P, P, f64, P, P, P, P]
+        L.orc_reweight.argtypes = [i64, P, P, f64, P]
+        L.orc_overlap.argtypes = [i64, P, f64, P]
+        L.orc_newton_dbeta.argtypes = [i64, P, f64, f64, ctypes.c_int]
+        L.orc_newton_dbeta.restype = f64
+        L.orc_run_adaptive.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, ctypes.c_int, f64, f64, f64,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P]
+        L.orc_run_adaptive.restype = ctypes.c_int
         assert L.orc_obs_size() == ctypes.sizeof(Obs)
         del i32
     return _lib
@@ -207,9 +213,50 @@ def site_matrix(q: int, L: int, site: int, beta: float) -> np.ndarray:
 
 def reweight(E: np.ndarray, dbeta: float, O: np.ndarray | None = None):
     """Returns (lnQ, <E>_tau, <O>_tau, cov_tau(O, E))."""
+    r = reweight_all(E, dbeta, O)
+    return r[0], r[1], (r[3] if O is not None else None), (r[4] if O is not None else None)
+
+
+def reweight_all(E: np.ndarray, dbeta: float, O: np.ndarray | None = None) -> np.ndarray:
+    """[lnQ, <E>_tau, var_tau(E), <O>_tau, cov_tau(O, E), E_ref, S]."""
     e = np.ascontiguousarray(E, dtype=np.int32)
     o = np.ascontiguousarray(O, dtype=np.float64) if O is not None else None
-    a, b, c, d = (ctypes.c_double() for _ in range(4))
-    lib().orc_reweight(e.size, _p(e), _p(o) if o is not None else None, float(dbeta),
-                       ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
-    return a.value, b.value, (c.value if o is not None else None), (d.value if o is not None else None)
+    out = np.zeros(7, dtype=np.float64)
+    lib().orc_reweight(e.size, _p(e), _p(o) if o is not None else None, float(dbeta), _p(out))
+    return out
+
+
+def overlap(E: np.ndarray, dbeta: float):
+    """(alpha, alpha') of the weight overlap."""
+    e = np.ascontiguousarray(E, dtype=np.int32)
+    out = np.zeros(2, dtype=np.float64)
+    lib().orc_overlap(e.size, _p(e), float(dbeta), _p(out))
+    return float(out[0]), float(out[1])
+
+
+def newton_dbeta(E: np.ndarray, target: float, dbeta_max: float, iters: int = 12) -> float:
+    e = np.ascontiguousarray(E, dtype=np.int32)
+    return float(lib().orc_newton_dbeta(e.size, _p(e), float(target), float(dbeta_max), int(iters)))
+
+
+def run_adaptive(q, L, R, seed, theta, beta_end, target=0.85, dbeta_max=0.05, iters=12, max_steps=10000,
+                 mode=NEAREST_INT, R_cap=None):
+    """PA with the Newton step on the weight overlap; returns a dict with the
+    per-step estimators, the betas taken and the final population."""
+    N = L * L
+    if R_cap is None:
+        R_cap = R + R // 4 + 64
+    obs = (Obs * (max_steps + 1))()
+    betas = np.zeros(max_steps + 1, dtype=np.float64)
+    spins = np.zeros((R_cap, L, L), dtype=np.uint8)
+    E = np.zeros(R_cap, dtype=np.int32)
+    K = lib().orc_run_adaptive(q, L, R, R_cap, seed, theta, float(beta_end), float(target), float(dbeta_max),
+                               iters, max_steps, mode, ctypes.cast(obs, ctypes.c_void_p), _p(betas), _p(spins), _p(E))
+    out = {name: np.array([getattr(o, name) for o in obs[: max(K, 0) + 1]]) for name, _ in Obs._fields_}
+    out["K"] = K
+    out["betas"] = betas[: max(K, 0) + 1]
+    if K >= 0:
+        Rf = int(out["R"][-1])
+        out["spins"] = spins[:Rf]
+        out["E"] = E[:Rf]
+    return out

@@ -524,31 +524,158 @@ ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
 /* ------------------------------------------------------------------------- */
 /* Reweighting as a function of dbeta (Sec. 2, step 2), for the differentiable */
 /* form:  ln Q(dbeta) = ln( sum_j exp(-dbeta E_j) / R ),                        */
-/*   d ln Q / d dbeta = -<E>_tau,   <O>_tau = sum_j O_j tau_j / R,              */
-/*   d <O>_tau / d dbeta = -(<O E>_tau - <O>_tau <E>_tau),                      */
+/*   d ln Q / d dbeta = -<E>_tau,  d^2 ln Q / d dbeta^2 = var_tau(E),           */
+/*   <O>_tau = sum_j O_j tau_j / R,  d <O>_tau / d dbeta = -cov_tau(O, E),      */
 /* with tau_j = exp(-dbeta E_j) / Q.  Sums run over ascending j, shifted by     */
-/* E_ref as in orc_copy_numbers.                                                */
+/* E_ref as in orc_copy_numbers.  out[0..6] = ln Q, <E>_tau, var_tau(E),         */
+/* <O>_tau, cov_tau(O, E), E_ref, S (the shifted sum).                          */
 /* ------------------------------------------------------------------------- */
-ORC_API void orc_reweight(int64_t R, const int32_t *E, const double *O, double dbeta, double *lnQ,
-                          double *meanE_tau, double *meanO_tau, double *covOE_tau)
+ORC_API void orc_reweight(int64_t R, const int32_t *E, const double *O, double dbeta, double out[7])
 {
     int32_t E_ref = E[0];
     for (int64_t j = 1; j < R; ++j)
         if (dbeta >= 0.0 ? (E[j] < E_ref) : (E[j] > E_ref)) E_ref = E[j];
-    double S = 0.0, SE = 0.0, SO = 0.0, SOE = 0.0;
+    double S = 0.0, SE = 0.0, SE2 = 0.0, SO = 0.0, SOE = 0.0;
     for (int64_t j = 0; j < R; ++j) {
         double w = exp(-dbeta * (double)(E[j] - E_ref));
+        double e = (double)E[j];
         S += w;
-        SE += w * (double)E[j];
+        SE += w * e;
+        SE2 += w * e * e;
         if (O) {
             SO += w * O[j];
-            SOE += w * O[j] * (double)E[j];
+            SOE += w * O[j] * e;
         }
     }
-    *lnQ = -dbeta * (double)E_ref + log(S / (double)R);
-    *meanE_tau = SE / S;
-    if (O) {
-        *meanO_tau = SO / S;
-        *covOE_tau = SOE / S - (SO / S) * (SE / S);
+    double mE = SE / S;
+    out[0] = -dbeta * (double)E_ref + log(S / (double)R);
+    out[1] = mE;
+    out[2] = SE2 / S - mE * mE;
+    out[3] = O ? SO / S : 0.0;
+    out[4] = O ? SOE / S - (SO / S) * mE : 0.0;
+    out[5] = (double)E_ref;
+    out[6] = S;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive temperature step.  reading (the paper uses constant steps and does */
+/* not define an overlap): with mean-one weights tau'_j = R w_j / S, the weight */
+/* overlap between the populations at beta and beta + dbeta is                  */
+/*   alpha(dbeta) = (1/R) sum_j min(1, tau'_j),                                  */
+/*   alpha'(dbeta) = (1/R) sum_{tau'_j < 1} tau'_j (<E>_tau - E_j).             */
+/* out[0..1] = alpha, alpha'.                                                     */
+/* ------------------------------------------------------------------------- */
+ORC_API void orc_overlap(int64_t R, const int32_t *E, double dbeta, double out[2])
+{
+    double rw[7];
+    orc_reweight(R, E, NULL, dbeta, rw);
+    double E_ref = rw[5], S = rw[6], mE = rw[1];
+    double a = 0.0, da = 0.0;
+    for (int64_t j = 0; j < R; ++j) {
+        double t = ((double)R * exp(-dbeta * ((double)E[j] - E_ref))) / S;
+        if (t < 1.0) {
+            a += t;
+            da += t * (mE - (double)E[j]);
+        } else {
+            a += 1.0;
+        }
     }
+    out[0] = a / (double)R;
+    out[1] = da / (double)R;
+}
+
+/* reading: the step solves alpha(dbeta) = target on [0, dbeta_max] by Newton
+ * iterations safeguarded by bisection: the bracket [lo, hi] starts as [0,
+ * dbeta_max]; if alpha(dbeta_max) >= target the step is dbeta_max; otherwise
+ * exactly `iters` iterations follow (a Newton step from the bracket midpoint
+ * first, then from the last iterate; a step leaving the bracket is replaced by
+ * the bracket midpoint), and the bracket shrinks with each evaluation.  The
+ * result is rounded down to a multiple of 2^-24 so that runs with a different
+ * last-bit rounding of alpha agree, and so that beta + dbeta stays exact. */
+ORC_API double orc_newton_dbeta(int64_t R, const int32_t *E, double target, double dbeta_max, int iters)
+{
+    double ov[2];
+    orc_overlap(R, E, dbeta_max, ov);
+    if (ov[0] >= target) return dbeta_max;
+    double lo = 0.0, hi = dbeta_max;
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < iters; ++it) {
+        orc_overlap(R, E, x, ov);
+        double f = ov[0] - target;
+        if (f > 0.0) lo = x; else hi = x;
+        double nx = ov[1] != 0.0 ? x - f / ov[1] : 0.5 * (lo + hi);
+        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        x = nx;
+    }
+    double q = floor(x * 16777216.0) / 16777216.0;
+    return q > 0.0 ? q : 1.0 / 16777216.0;
+}
+
+/* The PA driver with the adaptive step: from beta_0 = 0, step i uses
+ * dbeta_i = orc_newton_dbeta(E, target, min(dbeta_max, beta_end - beta), iters)
+ * and beta_i = beta_{i-1} + dbeta_i, the last step landing on beta_end
+ * exactly.  Otherwise as orc_run (random start, no histograms).  Writes up to
+ * max_steps + 1 estimator records and betas; returns the number of steps K
+ * taken (K <= max_steps), or -1 on a capacity overflow. */
+ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, int theta, double beta_end,
+                             double target, double dbeta_max, int iters, int max_steps, int mode, orc_obs *obs,
+                             double *betas, uint8_t *spins_out, int32_t *E_out)
+{
+    int N = L * L;
+    uint8_t *cur = (uint8_t *)malloc((size_t)R_cap * N);
+    uint8_t *nxt = (uint8_t *)malloc((size_t)R_cap * N);
+    int32_t *E = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *Mt = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *r = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
+    int64_t Rc = R;
+    orc_init_random(q, L, 0, R, seed, cur);
+    for (int64_t j = 0; j < R; ++j) {
+        E[j] = (int32_t)orc_energy(L, cur + j * N);
+        Mt[j] = (int32_t)orc_max_count(q, L, cur + j * N);
+    }
+    double beta = 0.0;
+    double lnZ = (double)N * log((double)q);
+    orc_measure(q, N, Rc, E, Mt, beta, NULL, R, &obs[0]);
+    obs[0].lnQ = 0.0;
+    obs[0].lnZ = lnZ;
+    betas[0] = beta;
+    int K = 0;
+    while (beta < beta_end && K < max_steps) {
+        double room = beta_end - beta;
+        double cap = dbeta_max < room ? dbeta_max : room;
+        double dbeta = orc_newton_dbeta(Rc, E, target, cap, iters);
+        double nb = (dbeta == room) ? beta_end : beta + dbeta;
+        int i = K + 1;
+        double lnQ;
+        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, r, &lnQ, NULL);
+        if (Rn > R_cap || Rn <= 0) {
+            K = -1;
+            break;
+        }
+        orc_parents(Rc, r, parent);
+        for (int64_t t = 0; t < Rn; ++t) memcpy(nxt + t * N, cur + (int64_t)parent[t] * N, (size_t)N);
+        uint8_t *tmp = cur; cur = nxt; nxt = tmp;
+        Rc = Rn;
+        uint32_t thr[9];
+        orc_thresholds(nb, thr);
+        for (int64_t t = 0; t < Rc; ++t) {
+            orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed);
+            E[t] = (int32_t)orc_energy(L, cur + t * N);
+            Mt[t] = (int32_t)orc_max_count(q, L, cur + t * N);
+        }
+        lnZ = lnZ + lnQ;
+        orc_measure(q, N, Rc, E, Mt, nb, NULL, R, &obs[i]);
+        obs[i].lnQ = lnQ;
+        obs[i].lnZ = lnZ;
+        betas[i] = nb;
+        beta = nb;
+        K = i;
+    }
+    if (K >= 0) {
+        if (spins_out) memcpy(spins_out, cur, (size_t)Rc * N);
+        if (E_out) memcpy(E_out, E, sizeof(int32_t) * (size_t)Rc);
+    }
+    free(cur); free(nxt); free(E); free(Mt); free(r); free(parent);
+    return K;
 }

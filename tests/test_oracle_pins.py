@@ -400,3 +400,70 @@ def test_run_invariants_and_families():
     # past beta_t = ln(1 + sqrt 10) = 1.426 order grows (Eq. 5), even though a
     # fast cooling stays partly metastable (Sec. 4)
     assert out["meanM"][-1] > 3 * out["meanM"][0]
+
+
+# --------------------------------------------------------------------------
+# Differentiable reweighting and the adaptive step
+# --------------------------------------------------------------------------
+def _population_energies(seed=5, n=4000, mean=-300.0, sd=12.0):
+    rng = np.random.default_rng(seed)
+    return np.rint(rng.normal(mean, sd, size=n)).astype(np.int32)
+
+
+def test_second_derivative_of_lnQ_is_the_reweighted_variance():
+    E = _population_energies()
+    for d in (0.0, 0.011, -0.007):
+        r = oracle.reweight_all(E, d)
+        h = 1e-4
+        fd2 = (oracle.reweight_all(E, d + h)[0] - 2 * r[0] + oracle.reweight_all(E, d - h)[0]) / h**2
+        assert fd2 == pytest.approx(r[2], rel=2e-4)
+        fdE = -(oracle.reweight_all(E, d + h)[1] - oracle.reweight_all(E, d - h)[1]) / (2 * h)
+        assert fdE == pytest.approx(r[2], rel=1e-6)
+    # at dbeta = 0 the reweighted moments are the population's own
+    r0 = oracle.reweight_all(E, 0.0)
+    assert r0[2] == pytest.approx(E.astype(np.float64).var(), rel=1e-12)
+
+
+def test_overlap_limits_and_derivative():
+    E = _population_energies(n=6000, mean=-2500.0, sd=50.0)
+    a0, da0 = oracle.overlap(E, 0.0)
+    assert a0 == 1.0 and da0 == 0.0
+    prev = 1.0
+    for d in (0.002, 0.005, 0.01, 0.02, 0.05):
+        a, da = oracle.overlap(E, d)
+        assert a < prev  # the overlap falls as the step grows
+        prev = a
+        h = 1e-7
+        fd = (oracle.overlap(E, d + h)[0] - oracle.overlap(E, d - h)[0]) / (2 * h)
+        assert fd == pytest.approx(da, rel=1e-4)
+    # equal energies: every weight is one, the overlap stays one
+    assert oracle.overlap(np.full(100, -64, np.int32), 0.3)[0] == 1.0
+
+
+def test_newton_step_meets_the_target_overlap():
+    E = _population_energies(n=6000, mean=-2500.0, sd=50.0)
+    for target in (0.6, 0.85, 0.95):
+        d = oracle.newton_dbeta(E, target, 1.0)
+        assert d * 2**24 == int(d * 2**24) and d > 0  # a multiple of 2^-24
+        a, da = oracle.overlap(E, d)
+        # rounding down by less than 2^-24 can only raise the overlap
+        assert target <= a <= target + abs(da) * 2**-24 + 1e-9
+    # a step that already meets the target is returned whole
+    assert oracle.newton_dbeta(E, 0.001, 1e-4) == 1e-4
+
+
+def test_adaptive_run_free_energy_matches_exact_enumeration():
+    """Adaptive steps (overlap 0.85) from beta = 0 to 1.6 on 4x4, q = 3: ln Z at
+    the end agrees with exact enumeration, and the last beta is exactly 1.6."""
+    q, L = 3, 4
+    N = L * L
+    g = oracle.density_of_states(q, L)
+    ends = []
+    for seed in range(1, 6):
+        out = oracle.run_adaptive(q, L, 5000, seed, 5, 1.6, target=0.85, dbeta_max=0.2)
+        assert out["betas"][-1] == 1.6
+        assert np.all(np.diff(out["betas"]) > 0)
+        ends.append(out["lnZ"][-1])
+    ex = _lnZ_from_dos(g, N, 1.6)
+    se = np.std(ends, ddof=1) / math.sqrt(len(ends))
+    assert abs(np.mean(ends) - ex) < 5 * se + 2e-3
