@@ -218,10 +218,10 @@ def reweight(E: np.ndarray, dbeta: float, O: np.ndarray | None = None):
 
 
 def reweight_all(E: np.ndarray, dbeta: float, O: np.ndarray | None = None) -> np.ndarray:
-    """[lnQ, <E>_tau, var_tau(E), <O>_tau, cov_tau(O, E), E_ref, S]."""
+    """[lnQ, <E>_tau, var_tau(E), <O>_tau, cov_tau(O, E), E_ref, S, k3_tau(E)]."""
     e = np.ascontiguousarray(E, dtype=np.int32)
     o = np.ascontiguousarray(O, dtype=np.float64) if O is not None else None
-    out = np.zeros(7, dtype=np.float64)
+    out = np.zeros(8, dtype=np.float64)
     lib().orc_reweight(e.size, _p(e), _p(o) if o is not None else None, float(dbeta), _p(out))
     return out
 

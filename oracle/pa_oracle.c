@@ -525,36 +525,41 @@ ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
 /* Reweighting as a function of dbeta (Sec. 2, step 2), for the differentiable */
 /* form:  ln Q(dbeta) = ln( sum_j exp(-dbeta E_j) / R ),                        */
 /*   d ln Q / d dbeta = -<E>_tau,  d^2 ln Q / d dbeta^2 = var_tau(E),           */
+/*   d var_tau(E) / d dbeta = -k3_tau(E) (third central moment),                */
 /*   <O>_tau = sum_j O_j tau_j / R,  d <O>_tau / d dbeta = -cov_tau(O, E),      */
 /* with tau_j = exp(-dbeta E_j) / Q.  Sums run over ascending j, shifted by     */
-/* E_ref as in orc_copy_numbers.  out[0..6] = ln Q, <E>_tau, var_tau(E),         */
-/* <O>_tau, cov_tau(O, E), E_ref, S (the shifted sum).                          */
+/* E_ref as in orc_copy_numbers.  out[0..7] = ln Q, <E>_tau, var_tau(E),         */
+/* <O>_tau, cov_tau(O, E), E_ref, S (the shifted sum), k3_tau(E).               */
 /* ------------------------------------------------------------------------- */
-ORC_API void orc_reweight(int64_t R, const int32_t *E, const double *O, double dbeta, double out[7])
+ORC_API void orc_reweight(int64_t R, const int32_t *E, const double *O, double dbeta, double out[8])
 {
     int32_t E_ref = E[0];
     for (int64_t j = 1; j < R; ++j)
         if (dbeta >= 0.0 ? (E[j] < E_ref) : (E[j] > E_ref)) E_ref = E[j];
-    double S = 0.0, SE = 0.0, SE2 = 0.0, SO = 0.0, SOE = 0.0;
+    /* moments about E_ref (a plain identity) keep var and cov free of cancellation */
+    double S = 0.0, S1 = 0.0, S2 = 0.0, S3 = 0.0, SO = 0.0, SOe = 0.0;
     for (int64_t j = 0; j < R; ++j) {
-        double w = exp(-dbeta * (double)(E[j] - E_ref));
-        double e = (double)E[j];
+        double e = (double)(E[j] - E_ref);
+        double w = exp(-dbeta * e);
         S += w;
-        SE += w * e;
-        SE2 += w * e * e;
+        S1 += w * e;
+        S2 += w * e * e;
+        S3 += w * e * e * e;
         if (O) {
             SO += w * O[j];
-            SOE += w * O[j] * e;
+            SOe += w * O[j] * e;
         }
     }
-    double mE = SE / S;
+    double m1 = S1 / S;
+    double var = S2 / S - m1 * m1;
     out[0] = -dbeta * (double)E_ref + log(S / (double)R);
-    out[1] = mE;
-    out[2] = SE2 / S - mE * mE;
+    out[1] = (double)E_ref + m1;
+    out[2] = var;
     out[3] = O ? SO / S : 0.0;
-    out[4] = O ? SOE / S - (SO / S) * mE : 0.0;
+    out[4] = O ? SOe / S - (SO / S) * m1 : 0.0;
     out[5] = (double)E_ref;
     out[6] = S;
+    out[7] = S3 / S - 3.0 * m1 * (S2 / S) + 2.0 * m1 * m1 * m1;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -567,7 +572,7 @@ ORC_API void orc_reweight(int64_t R, const int32_t *E, const double *O, double d
 /* ------------------------------------------------------------------------- */
 ORC_API void orc_overlap(int64_t R, const int32_t *E, double dbeta, double out[2])
 {
-    double rw[7];
+    double rw[8];
     orc_reweight(R, E, NULL, dbeta, rw);
     double E_ref = rw[5], S = rw[6], mE = rw[1];
     double a = 0.0, da = 0.0;

@@ -419,6 +419,8 @@ def test_second_derivative_of_lnQ_is_the_reweighted_variance():
         assert fd2 == pytest.approx(r[2], rel=2e-4)
         fdE = -(oracle.reweight_all(E, d + h)[1] - oracle.reweight_all(E, d - h)[1]) / (2 * h)
         assert fdE == pytest.approx(r[2], rel=1e-6)
+        fdV = -(oracle.reweight_all(E, d + h)[2] - oracle.reweight_all(E, d - h)[2]) / (2 * h)
+        assert fdV == pytest.approx(r[7], rel=1e-3, abs=1e-3 * r[2] ** 1.5)
     # at dbeta = 0 the reweighted moments are the population's own
     r0 = oracle.reweight_all(E, 0.0)
     assert r0[2] == pytest.approx(E.astype(np.float64).var(), rel=1e-12)
