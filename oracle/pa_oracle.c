@@ -592,11 +592,13 @@ ORC_API void orc_overlap(int64_t R, const int32_t *E, double dbeta, double out[2
 /* reading: the step solves alpha(dbeta) = target on [0, dbeta_max] by Newton
  * iterations safeguarded by bisection: the bracket [lo, hi] starts as [0,
  * dbeta_max]; if alpha(dbeta_max) >= target the step is dbeta_max; otherwise
- * exactly `iters` iterations follow (a Newton step from the bracket midpoint
- * first, then from the last iterate; a step leaving the bracket is replaced by
- * the bracket midpoint), and the bracket shrinks with each evaluation.  The
- * result is rounded down to a multiple of 2^-24 so that runs with a different
- * last-bit rounding of alpha agree, and so that beta + dbeta stays exact. */
+ * at most `iters` iterations follow from the bracket midpoint, stopping once
+ * |alpha - target| <= 1e-12 (a step leaving the bracket is replaced by the
+ * bracket midpoint; the bracket shrinks with each evaluation).  Stopping there,
+ * far above rounding noise, keeps a converged iterate from being thrown back
+ * by a bracket test decided by the last bit.  The result is rounded down to a
+ * multiple of 2^-24 so that runs with a different last-bit rounding of alpha
+ * agree, and so that beta + dbeta stays exact. */
 ORC_API double orc_newton_dbeta(int64_t R, const int32_t *E, double target, double dbeta_max, int iters)
 {
     double ov[2];
@@ -607,6 +609,7 @@ ORC_API double orc_newton_dbeta(int64_t R, const int32_t *E, double target, doub
     for (int it = 0; it < iters; ++it) {
         orc_overlap(R, E, x, ov);
         double f = ov[0] - target;
+        if (fabs(f) <= 1e-12) break;
         if (f > 0.0) lo = x; else hi = x;
         double nx = ov[1] != 0.0 ? x - f / ov[1] : 0.5 * (lo + hi);
         if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
