@@ -176,6 +176,60 @@ pa_status pa_get_ancestors(pa_ctx *ctx, int32_t *host);
 pa_status pa_run(pa_ctx *ctx, const double *betas, int32_t K, int32_t theta, pa_obs *obs_out,
                  const int32_t *hist_steps, int32_t n_hist, int32_t *hist_out, int32_t use_graph);
 
+/* ---- Differentiable reweighting (Sec. 2 step 2) --------------------------
+ * For R energies E (device int32) and a step dbeta (device double, so no host
+ * round trip is needed), with tau_j = exp(-dbeta E_j) / Q:
+ *   out[0] = ln Q = ln( sum_j exp(-dbeta E_j) / R )
+ *   out[1] = <E>_tau         (= -d ln Q / d dbeta)
+ *   out[2] = var_tau(E)      (= -d <E>_tau / d dbeta)
+ *   out[3] = <O>_tau = sum_j O_j tau_j / R   (0 if O is NULL)
+ *   out[4] = cov_tau(O, E)   (= -d <O>_tau / d dbeta)
+ *   out[5] = E_ref (lowest energy for dbeta >= 0, highest otherwise)
+ *   out[6] = sum_j exp(-dbeta (E_j - E_ref))
+ *   out[7] = k3_tau(E), the third central moment (= -d var_tau / d dbeta)
+ * out is a device double[8]; O (device double[R]) may be NULL.  Enqueued on
+ * `stream`; one block, fixed summation order, deterministic.
+ * PA_ERR_INVALID for NULL pointers or R < 1. */
+pa_status pa_reweight_forward(const int32_t *E, const double *O, int32_t R, const double *dbeta, double *out,
+                              void *stream);
+
+/* Backward of one forward output with respect to dbeta: dst[0] = sign * g[0] *
+ * src[idx] (all device pointers), e.g. src = forward out, idx 1, sign -1 gives
+ * d ln Q / d dbeta times the incoming gradient g. */
+pa_status pa_reweight_scale(const double *src, int32_t idx, double sign, const double *g, double *dst, void *stream);
+
+/* Backward of <O>_tau with respect to O: grad_O[j] = g[0] tau_j / R
+ * (device double[R]), from the forward outputs `fwd` of the same E and dbeta. */
+pa_status pa_reweight_grad_O(const int32_t *E, int32_t R, const double *dbeta, const double *fwd, const double *g,
+                             double *grad_O, void *stream);
+
+/* ---- Adaptive temperature step (the paper uses constant steps) ------------
+ * Weight overlap of the populations at beta and beta + dbeta, with mean-one
+ * weights t_j = R exp(-dbeta (E_j - E_ref)) / sum: out[0] = alpha =
+ * (1/R) sum_j min(1, t_j), out[1] = d alpha / d dbeta = (1/R) sum_{t_j < 1}
+ * t_j (<E>_tau - E_j).  Device pointers; out is double[2]. */
+pa_status pa_overlap(const int32_t *E, int32_t R, const double *dbeta, double *out, void *stream);
+
+/* The step dbeta in (0, dbeta_cap] at which the overlap of the context's
+ * current population equals `target`: bisection-safeguarded Newton iterations
+ * (at most `iters`, from the middle of the bracket [0, dbeta_cap], stopping once
+ * |overlap - target| <= 1e-12) on the population's energy histogram, rounded
+ * down to a multiple of 2^-24 (dbeta_cap itself if its overlap already reaches
+ * the target).  Synchronises.  PA_ERR_INVALID for a
+ * target outside (0, 1), a non-positive cap or iters outside 0..200;
+ * PA_ERR_STATE with a resample pending. */
+pa_status pa_next_dbeta(pa_ctx *ctx, double target, double dbeta_cap, int32_t iters, double *dbeta_out);
+
+/* Runs PA from the current inverse temperature to beta_end with adaptive
+ * steps: step i takes dbeta_i = pa_next_dbeta(target, min(dbeta_max, beta_end
+ * - beta), iters), resamples and sweeps theta times at beta_i = beta_{i-1} +
+ * dbeta_i (the last step lands on beta_end exactly), at most max_steps steps.
+ * Writes the number of steps to *K_out, the betas to betas_out[0..K) and the
+ * estimators to obs_out[0..K) (host; either may be NULL).  One host
+ * synchronisation per step (the step size decides the acceptance thresholds). */
+pa_status pa_run_adaptive(pa_ctx *ctx, double beta_end, double target, double dbeta_max, int32_t iters, int32_t theta,
+                          int32_t max_steps, pa_obs *obs_out, double *betas_out, int32_t *K_out);
+
 /* Releases the context and its device memory (synchronises its stream). */
 void pa_destroy(pa_ctx *ctx);
 

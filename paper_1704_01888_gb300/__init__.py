@@ -35,7 +35,8 @@ EXPORTED = (
     "pa_init", "pa_resample", "pa_sweep", "pa_energy", "pa_observables", "pa_population_size",
     "pa_get_spins", "pa_get_ancestors", "pa_run", "pa_destroy", "pa_status_str", "pa_last_cuda_error",
     "pa_set_launch", "pa_kernel_launch_count", "pa_profile", "pa_profile_read", "pa_observables_history",
-    "pa_get_launch", "pa_resample_noalloc",
+    "pa_get_launch", "pa_resample_noalloc", "pa_reweight_forward", "pa_reweight_scale", "pa_reweight_grad_O",
+    "pa_overlap", "pa_next_dbeta", "pa_run_adaptive",
 )
 
 
@@ -101,6 +102,12 @@ def load_library(path: str | None = None):
         "pa_observables_history": ([P, i32, P], st),
         "pa_get_launch": ([P, P, P, P], st),
         "pa_resample_noalloc": ([P, i32, i32, f64, i32, i32, i32, ctypes.c_uint64, P, i32, P, P, P], st),
+        "pa_reweight_forward": ([P, P, i32, P, P, P], st),
+        "pa_reweight_scale": ([P, i32, f64, P, P, P], st),
+        "pa_reweight_grad_O": ([P, i32, P, P, P, P, P], st),
+        "pa_overlap": ([P, i32, P, P, P], st),
+        "pa_next_dbeta": ([P, f64, f64, i32, P], st),
+        "pa_run_adaptive": ([P, f64, f64, f64, i32, i32, i32, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -275,6 +282,27 @@ class Population:
         n = np.zeros(2, dtype=np.int64)
         _check(self.lib.pa_profile_read(self._ctx, _ptr(ms), _ptr(n)), "pa_profile_read")
         return {"sweep": (float(ms[0]), int(n[0])), "resample": (float(ms[1]), int(n[1]))}
+
+    def next_dbeta(self, target: float, dbeta_cap: float, iters: int = 12) -> float:
+        """Newton step holding the weight overlap at `target` (see include/pa.h)."""
+        d = ctypes.c_double()
+        _check(self.lib.pa_next_dbeta(self._ctx, float(target), float(dbeta_cap), int(iters), ctypes.byref(d)),
+               "pa_next_dbeta")
+        return d.value
+
+    def run_adaptive(self, beta_end: float, theta: int, target: float = 0.85, dbeta_max: float = 0.05,
+                     iters: int = 12, max_steps: int = 10000):
+        """PA to beta_end with adaptive steps.  Returns (obs list, betas)."""
+        obs = (Obs * max_steps)()
+        betas = np.zeros(max_steps, dtype=np.float64)
+        K = ctypes.c_int32()
+        _check(self.lib.pa_run_adaptive(self._ctx, float(beta_end), float(target), float(dbeta_max), int(iters),
+                                        int(theta), int(max_steps), ctypes.cast(obs, ctypes.c_void_p), _ptr(betas),
+                                        ctypes.byref(K)), "pa_run_adaptive")
+        self.step += K.value
+        if K.value:
+            self.beta = float(betas[K.value - 1])
+        return [o.as_dict() for o in obs[: K.value]], betas[: K.value].copy()
 
     def run(self, betas, theta: int, hist_steps=(), use_graph: bool = False):
         """Runs betas[1..K] (betas[0] = current beta).  Returns (obs list, hists)."""

@@ -74,6 +74,7 @@ struct pa_ctx {
     long long n_obs = 0;  // estimator records written so far
     uint8_t *stage = nullptr;
     size_t stage_bytes = 0;
+    double *aux = nullptr;  // small device outputs (Newton step)
 
     int step = 0;          // last completed temperature step
     int pending_step = 0;  // step of an enqueued resample awaiting its sweep
@@ -133,7 +134,7 @@ void release(pa_ctx *c)
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     void *ptrs[] = {c->spins[0], c->spins[1], c->anc[0], c->anc[1], c->E, c->Mt, c->hist, c->fam,
                     c->counts, c->local_off, c->blocksum, c->parent, c->wtab, c->acc, c->st, c->obs,
-                    c->stage};
+                    c->stage, c->aux};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -318,7 +319,7 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
         (s = dev_alloc(&c->hist, c->nbins)) || (s = dev_alloc(&c->counts, c->R_cap)) ||
         (s = dev_alloc(&c->local_off, c->R_cap)) || (s = dev_alloc(&c->blocksum, nb)) ||
         (s = dev_alloc(&c->parent, c->R_cap)) || (s = dev_alloc(&c->wtab, c->nbins)) ||
-        (s = dev_alloc(&c->acc, 3)) || (s = dev_alloc(&c->st, 1)))
+        (s = dev_alloc(&c->acc, 3)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
         return fail(s);
     if (g.track_families) {
         if ((s = dev_alloc(&c->anc[0], c->R_cap)) || (s = dev_alloc(&c->anc[1], c->R_cap)) ||
@@ -587,6 +588,67 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
     }
     if (hstore) cudaFree(hstore);
     return s;
+}
+
+pa_status pa_next_dbeta(pa_ctx *c, double target, double dbeta_cap, int32_t iters, double *dbeta_out)
+{
+    if (!c || !dbeta_out || !(target > 0.0 && target < 1.0) || !(dbeta_cap > 0.0) || !std::isfinite(dbeta_cap) ||
+        iters < 0 || iters > 200)
+        return PA_ERR_INVALID;
+    if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
+    PA_CK(pa::launch_newton(c->hist, c->nbins, c->st, target, dbeta_cap, iters, c->aux, c->stream));
+    double h[2];
+    PA_CK(cudaMemcpyAsync(h, c->aux, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    pa_status s = sync_state(c, nullptr);
+    if (s) return s;
+    *dbeta_out = h[0];
+    return PA_OK;
+}
+
+pa_status pa_run_adaptive(pa_ctx *c, double beta_end, double target, double dbeta_max, int32_t iters, int32_t theta,
+                          int32_t max_steps, pa_obs *obs_out, double *betas_out, int32_t *K_out)
+{
+    if (!c || !K_out || theta < 0 || max_steps < 1 || !(beta_end >= 0.0) || !std::isfinite(beta_end) ||
+        !(dbeta_max > 0.0))
+        return PA_ERR_INVALID;
+    if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
+    if (c->obs_cap < max_steps + 1) {
+        PA_CK(cudaStreamSynchronize(c->stream));
+        pa::DevObs *bigger = nullptr;
+        pa_status s = dev_alloc(&bigger, (size_t)max_steps + 1);
+        if (s) return s;
+        PA_CK(cudaMemcpy(bigger, c->obs + ((c->n_obs - 1) % c->obs_cap), sizeof(pa::DevObs), cudaMemcpyDeviceToDevice));
+        cudaFree(c->obs);
+        c->obs = bigger;
+        c->obs_cap = max_steps + 1;
+        c->n_obs = 1;
+    }
+    const long long first_obs = c->n_obs;
+    double beta = c->beta;
+    int K = 0;
+    while (beta < beta_end && K < max_steps) {
+        const double room = beta_end - beta;
+        const double cap = dbeta_max < room ? dbeta_max : room;
+        double dbeta = 0.0;
+        pa_status s = pa_next_dbeta(c, target, cap, iters, &dbeta);
+        if (s) return s;
+        const double nb = (dbeta == room) ? beta_end : beta + dbeta;
+        const int step = c->step + 1;
+        if ((s = enqueue_resample(c, dbeta, step)) || (s = enqueue_sweep(c, nb, theta, step))) return s;
+        K += 1;
+        if (betas_out) betas_out[K - 1] = nb;
+        beta = nb;
+    }
+    pa_status s = sync_state(c, nullptr);
+    if (s) return s;
+    if (obs_out) {
+        for (int i = 0; i < K; ++i) {
+            const pa::DevObs *slot = c->obs + ((first_obs + i) % c->obs_cap);
+            PA_CK(cudaMemcpy(obs_out + i, slot, sizeof(pa_obs), cudaMemcpyDeviceToHost));
+        }
+    }
+    *K_out = K;
+    return PA_OK;
 }
 
 pa_status pa_profile(pa_ctx *c, int32_t enable)

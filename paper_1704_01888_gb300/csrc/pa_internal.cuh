@@ -78,6 +78,10 @@ cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam,
 cudaError_t launch_to_canonical(const uint8_t *spins, uint8_t *out, int L, int64_t count,
                                 cudaStream_t s);
 
+// Launchers (pa_reweight.cu)
+cudaError_t launch_newton(const int32_t *hist, int nbins, const DevState *st, double target, double cap, int iters,
+                          double *out, cudaStream_t s);
+
 int64_t bump_launch_count(int64_t n);
 
 }  // namespace pa

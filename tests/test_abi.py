@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_functions():
     text = open(os.path.join(ROOT, "include", "pa.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(pa_[a-z0-9_]+)\s*\(", text)
+    names = re.findall(r"\b(pa_[A-Za-z0-9_]+)\s*\(", text)
     return sorted(set(names))
 
 
