@@ -66,13 +66,13 @@ def lib():
         L.orc_thresholds.argtypes = [f64, P]
         L.orc_metropolis_decide.argtypes = [ctypes.c_int, ctypes.c_int, P, u32, P]
         L.orc_metropolis_decide.restype = ctypes.c_int
-        L.orc_sweep_replica.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, u32, u32, u64]
-        L.orc_init_random.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, P]
-        L.orc_init_ground.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, P]
-        L.orc_copy_numbers.argtypes = [i64, P, f64, i64, ctypes.c_int, u32, u64, P, P, P]
+        L.orc_sweep_replica.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, u32, u32, u64, u32]
+        L.orc_init_random.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
+        L.orc_init_ground.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
+        L.orc_copy_numbers.argtypes = [i64, P, f64, i64, ctypes.c_int, u32, u64, u32, P, P, P]
         L.orc_copy_numbers.restype = i64
         L.orc_parents.argtypes = [i64, P, P]
-        L.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, ctypes.c_int, ctypes.c_int, P,
+        L.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, ctypes.c_int, ctypes.c_int, P,
                               ctypes.c_int, ctypes.c_int, P, P, P, P, P]
         L.orc_run.restype = i64
         L.orc_obs_size.restype = ctypes.c_int
@@ -84,7 +84,7 @@ def lib():
         L.orc_overlap.argtypes = [i64, P, f64, P]
         L.orc_newton_dbeta.argtypes = [i64, P, f64, f64, ctypes.c_int]
         L.orc_newton_dbeta.restype = f64
-        L.orc_run_adaptive.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, ctypes.c_int, f64, f64, f64,
+        L.orc_run_adaptive.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, ctypes.c_int, f64, f64, f64,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P]
         L.orc_run_adaptive.restype = ctypes.c_int
         assert L.orc_obs_size() == ctypes.sizeof(Obs)
@@ -126,33 +126,34 @@ def metropolis_decide(q, cur, nb, u, thr) -> int:
     return int(lib().orc_metropolis_decide(q, cur, _p(n), int(u), _p(t)))
 
 
-def sweep_replica(q: int, spins: np.ndarray, beta: float, theta: int, step: int, slot: int, seed: int) -> np.ndarray:
+def sweep_replica(q: int, spins: np.ndarray, beta: float, theta: int, step: int, slot: int, seed: int,
+                  stream: int = 0) -> np.ndarray:
     """theta sweeps of one L x L replica; returns a new array."""
     s = np.array(spins, dtype=np.uint8, copy=True, order="C")
     thr = thresholds(beta)
-    lib().orc_sweep_replica(q, s.shape[-1], _p(s), _p(thr), theta, step, slot, seed)
+    lib().orc_sweep_replica(q, s.shape[-1], _p(s), _p(thr), theta, step, slot, seed, stream)
     return s
 
 
-def init_random(q: int, L: int, slot_begin: int, count: int, seed: int) -> np.ndarray:
+def init_random(q: int, L: int, slot_begin: int, count: int, seed: int, stream: int = 0) -> np.ndarray:
     out = np.zeros((count, L, L), dtype=np.uint8)
-    lib().orc_init_random(q, L, slot_begin, count, seed, _p(out))
+    lib().orc_init_random(q, L, slot_begin, count, seed, stream, _p(out))
     return out
 
 
-def init_ground(q: int, L: int, slot_begin: int, count: int, seed: int) -> np.ndarray:
+def init_ground(q: int, L: int, slot_begin: int, count: int, seed: int, stream: int = 0) -> np.ndarray:
     out = np.zeros((count, L, L), dtype=np.uint8)
-    lib().orc_init_ground(q, L, slot_begin, count, seed, _p(out))
+    lib().orc_init_ground(q, L, slot_begin, count, seed, stream, _p(out))
     return out
 
 
-def copy_numbers(E: np.ndarray, dbeta: float, R_target: int, mode: int, step: int, seed: int):
+def copy_numbers(E: np.ndarray, dbeta: float, R_target: int, mode: int, step: int, seed: int, stream: int = 0):
     """Returns (r, lnQ, R_new, rho)."""
     e = np.ascontiguousarray(E, dtype=np.int32)
     r = np.zeros(e.size, dtype=np.int32)
     rho = np.zeros(e.size, dtype=np.float64)
     lnq = ctypes.c_double()
-    Rn = lib().orc_copy_numbers(e.size, _p(e), float(dbeta), R_target, mode, step, seed, _p(r),
+    Rn = lib().orc_copy_numbers(e.size, _p(e), float(dbeta), R_target, mode, step, seed, stream, _p(r),
                                 ctypes.byref(lnq), _p(rho))
     return r, lnq.value, int(Rn), rho
 
@@ -165,7 +166,7 @@ def parents(r: np.ndarray) -> np.ndarray:
 
 
 def run(q, L, R, seed, theta, betas, mode=NEAREST_INT, init_mode=INIT_RANDOM, R_cap=None,
-        want_hist=False, want_state=True):
+        want_hist=False, want_state=True, stream=0):
     """Full PA run over betas[0..K].  Returns a dict of numpy arrays."""
     betas = np.ascontiguousarray(betas, dtype=np.float64)
     K = betas.size - 1
@@ -177,7 +178,7 @@ def run(q, L, R, seed, theta, betas, mode=NEAREST_INT, init_mode=INIT_RANDOM, R_
     spins = np.zeros((R_cap, L, L), dtype=np.uint8) if want_state else None
     E = np.zeros(R_cap, dtype=np.int32) if want_state else None
     anc = np.zeros(R_cap, dtype=np.int32) if want_state else None
-    Rf = lib().orc_run(q, L, R, R_cap, seed, theta, K, _p(betas), mode, init_mode,
+    Rf = lib().orc_run(q, L, R, R_cap, seed, stream, theta, K, _p(betas), mode, init_mode,
                        ctypes.cast(obs, ctypes.c_void_p),
                        _p(hist) if hist is not None else None,
                        _p(spins) if spins is not None else None,
@@ -240,7 +241,7 @@ def newton_dbeta(E: np.ndarray, target: float, dbeta_max: float, iters: int = 12
 
 
 def run_adaptive(q, L, R, seed, theta, beta_end, target=0.85, dbeta_max=0.05, iters=12, max_steps=10000,
-                 mode=NEAREST_INT, R_cap=None):
+                 mode=NEAREST_INT, R_cap=None, stream=0):
     """PA with the Newton step on the weight overlap; returns a dict with the
     per-step estimators, the betas taken and the final population."""
     N = L * L
@@ -250,7 +251,7 @@ def run_adaptive(q, L, R, seed, theta, beta_end, target=0.85, dbeta_max=0.05, it
     betas = np.zeros(max_steps + 1, dtype=np.float64)
     spins = np.zeros((R_cap, L, L), dtype=np.uint8)
     E = np.zeros(R_cap, dtype=np.int32)
-    K = lib().orc_run_adaptive(q, L, R, R_cap, seed, theta, float(beta_end), float(target), float(dbeta_max),
+    K = lib().orc_run_adaptive(q, L, R, R_cap, seed, stream, theta, float(beta_end), float(target), float(dbeta_max),
                                iters, max_steps, mode, ctypes.cast(obs, ctypes.c_void_p), _p(betas), _p(spins), _p(E))
     out = {name: np.array([getattr(o, name) for o in obs[: max(K, 0) + 1]]) for name, _ in Obs._fields_}
     out["K"] = K

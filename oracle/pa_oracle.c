@@ -63,7 +63,8 @@ ORC_API void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uin
 
 /* reading: the counter word c1 carries a 2-bit domain tag in its top bits so
  * that initialisation, sweeps, resampling and ground-state draws never share
- * a counter. */
+ * a counter.  The top byte of c3 carries a stream number (0..255) that lets
+ * several independent runs share one key; slots stay below 2^24. */
 #define ORC_DOM_SWEEP    0x00000000u
 #define ORC_DOM_INIT     0x40000000u
 #define ORC_DOM_RESAMPLE 0x80000000u
@@ -177,7 +178,7 @@ static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
  * Philox call with counter (h >> 2, SWEEP | (2k + colour), step, slot) serves
  * the four sites with the same h >> 2 of that colour, word h & 3 going to h. */
 ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint32_t thr[9], int theta,
-                               uint32_t step, uint32_t slot, uint64_t seed)
+                               uint32_t step, uint32_t slot, uint64_t seed, uint32_t stream)
 {
     for (int k = 0; k < theta; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
@@ -186,7 +187,7 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint32_t thr[9], 
                     if (((x + y) & 1) != colour) continue;
                     uint32_t h = (uint32_t)(y * L + x) >> 1;
                     uint32_t w[4];
-                    orc_draw(seed, h >> 2, ORC_DOM_SWEEP | (uint32_t)(2 * k + colour), step, slot, w);
+                    orc_draw(seed, h >> 2, ORC_DOM_SWEEP | (uint32_t)(2 * k + colour), step, slot | (stream << 24), w);
                     int nb[4];
                     orc_neighbours(L, s, x, y, nb);
                     s[y * L + x] = (uint8_t)orc_metropolis_decide(q, s[y * L + x], nb, w[h & 3], thr);
@@ -203,14 +204,15 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint32_t thr[9], 
 /* beta_0 = 0: every site independently uniform over the q states (Sec. 2,
  * step 1).  Site i = y L + x of slot r takes word (i & 3) of the call with
  * counter (i >> 2, INIT, 0, r). */
-ORC_API void orc_init_random(int q, int L, int64_t slot_begin, int64_t count, uint64_t seed, uint8_t *spins)
+ORC_API void orc_init_random(int q, int L, int64_t slot_begin, int64_t count, uint64_t seed, uint32_t stream,
+                             uint8_t *spins)
 {
     int N = L * L;
     for (int64_t r = 0; r < count; ++r) {
         uint32_t slot = (uint32_t)(slot_begin + r);
         for (int i = 0; i < N; ++i) {
             uint32_t w[4];
-            orc_draw(seed, (uint32_t)i >> 2, ORC_DOM_INIT, 0u, slot, w);
+            orc_draw(seed, (uint32_t)i >> 2, ORC_DOM_INIT, 0u, slot | (stream << 24), w);
             spins[r * N + i] = (uint8_t)orc_scale(w[i & 3], (uint32_t)q);
         }
     }
@@ -218,13 +220,14 @@ ORC_API void orc_init_random(int q, int L, int64_t slot_begin, int64_t count, ui
 
 /* Heating runs: every replica in one of the q ground states, chosen uniformly
  * (Sec. 5, Eq. 6).  Slot r takes word (r & 3) of counter (r >> 2, GROUND, 0, 0). */
-ORC_API void orc_init_ground(int q, int L, int64_t slot_begin, int64_t count, uint64_t seed, uint8_t *spins)
+ORC_API void orc_init_ground(int q, int L, int64_t slot_begin, int64_t count, uint64_t seed, uint32_t stream,
+                             uint8_t *spins)
 {
     int N = L * L;
     for (int64_t r = 0; r < count; ++r) {
         uint32_t slot = (uint32_t)(slot_begin + r);
         uint32_t w[4];
-        orc_draw(seed, slot >> 2, ORC_DOM_GROUND, 0u, 0u, w);
+        orc_draw(seed, slot >> 2, ORC_DOM_GROUND, 0u, stream << 24, w);
         uint8_t alpha = (uint8_t)orc_scale(w[slot & 3], (uint32_t)q);
         for (int i = 0; i < N; ++i) spins[r * N + i] = alpha;
     }
@@ -249,8 +252,8 @@ enum { ORC_NEAREST_INT = 0, ORC_ROUND = 1 };
  * ORC_ROUND instead takes the nearest integer, halves rounded up.
  * rho_out (optional) receives rho_j.  Returns the new population size. */
 ORC_API int64_t orc_copy_numbers(int64_t R_prev, const int32_t *E, double dbeta, int64_t R_target,
-                                 int mode, uint32_t step, uint64_t seed, int32_t *r, double *lnQ,
-                                 double *rho_out)
+                                 int mode, uint32_t step, uint64_t seed, uint32_t stream, int32_t *r,
+                                 double *lnQ, double *rho_out)
 {
     int32_t E_ref = E[0];
     for (int64_t j = 1; j < R_prev; ++j) {
@@ -271,7 +274,7 @@ ORC_API int64_t orc_copy_numbers(int64_t R_prev, const int32_t *E, double dbeta,
             up = frac >= 0.5;
         } else {
             uint32_t u[4];
-            orc_draw(seed, (uint32_t)(j >> 2), ORC_DOM_RESAMPLE, step, 0u, u);
+            orc_draw(seed, (uint32_t)(j >> 2), ORC_DOM_RESAMPLE, step, stream << 24, u);
             up = (double)u[j & 3] < frac * 4294967296.0;
         }
         r[j] = (int32_t)n + up;
@@ -352,7 +355,7 @@ enum { ORC_INIT_RANDOM = 0, ORC_INIT_GROUND = 1 };
  * E_0 = -2N for ground-state starts (Sec. 6, Eqs. 7-8).
  * Returns the final population size, or -1 if a population outgrew R_cap
  * (outputs then hold the last complete step). */
-ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, int theta, int K,
+ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, uint32_t stream, int theta, int K,
                         const double *betas, int mode, int init_mode, orc_obs *obs, int32_t *hist,
                         uint8_t *spins_out, int32_t *E_out, int32_t *anc_out)
 {
@@ -369,9 +372,9 @@ ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, i
     int64_t result = R;
 
     if (init_mode == ORC_INIT_GROUND)
-        orc_init_ground(q, L, 0, R, seed, cur);
+        orc_init_ground(q, L, 0, R, seed, stream, cur);
     else
-        orc_init_random(q, L, 0, R, seed, cur);
+        orc_init_random(q, L, 0, R, seed, stream, cur);
     for (int64_t j = 0; j < R; ++j) {
         E[j] = (int32_t)orc_energy(L, cur + j * N);
         Mt[j] = (int32_t)orc_max_count(q, L, cur + j * N);
@@ -393,7 +396,7 @@ ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, i
     for (int i = 1; i <= K; ++i) {
         double dbeta = betas[i] - betas[i - 1];
         double lnQ;
-        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, r, &lnQ, NULL);
+        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, stream, r, &lnQ, NULL);
         if (Rn > R_cap || Rn <= 0) {
             result = -1;
             break;
@@ -410,7 +413,7 @@ ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, i
         uint32_t thr[9];
         orc_thresholds(betas[i], thr);
         for (int64_t t = 0; t < Rc; ++t) {
-            orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed);
+            orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed, stream);
             E[t] = (int32_t)orc_energy(L, cur + t * N);
             Mt[t] = (int32_t)orc_max_count(q, L, cur + t * N);
         }
@@ -625,7 +628,8 @@ ORC_API double orc_newton_dbeta(int64_t R, const int32_t *E, double target, doub
  * exactly.  Otherwise as orc_run (random start, no histograms).  Writes up to
  * max_steps + 1 estimator records and betas; returns the number of steps K
  * taken (K <= max_steps), or -1 on a capacity overflow. */
-ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, int theta, double beta_end,
+ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, uint32_t stream, int theta,
+                             double beta_end,
                              double target, double dbeta_max, int iters, int max_steps, int mode, orc_obs *obs,
                              double *betas, uint8_t *spins_out, int32_t *E_out)
 {
@@ -637,7 +641,7 @@ ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t se
     int32_t *r = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
     int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)R_cap);
     int64_t Rc = R;
-    orc_init_random(q, L, 0, R, seed, cur);
+    orc_init_random(q, L, 0, R, seed, stream, cur);
     for (int64_t j = 0; j < R; ++j) {
         E[j] = (int32_t)orc_energy(L, cur + j * N);
         Mt[j] = (int32_t)orc_max_count(q, L, cur + j * N);
@@ -656,7 +660,7 @@ ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t se
         double nb = (dbeta == room) ? beta_end : beta + dbeta;
         int i = K + 1;
         double lnQ;
-        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, r, &lnQ, NULL);
+        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, stream, r, &lnQ, NULL);
         if (Rn > R_cap || Rn <= 0) {
             K = -1;
             break;
@@ -668,7 +672,7 @@ ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t se
         uint32_t thr[9];
         orc_thresholds(nb, thr);
         for (int64_t t = 0; t < Rc; ++t) {
-            orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed);
+            orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed, stream);
             E[t] = (int32_t)orc_energy(L, cur + t * N);
             Mt[t] = (int32_t)orc_max_count(q, L, cur + t * N);
         }

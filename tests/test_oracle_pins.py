@@ -469,3 +469,18 @@ def test_adaptive_run_free_energy_matches_exact_enumeration():
     ex = _lnZ_from_dos(g, N, 1.6)
     se = np.std(ends, ddof=1) / math.sqrt(len(ends))
     assert abs(np.mean(ends) - ex) < 5 * se + 2e-3
+
+
+def test_streams_give_independent_runs_under_one_key():
+    """Stream numbers (top byte of the slot counter word) separate runs that
+    share a key; stream 0 is the plain run."""
+    q, L = 10, 8
+    a = oracle.init_random(q, L, 0, 200, 1, stream=0)
+    b = oracle.init_random(q, L, 0, 200, 1, stream=1)
+    assert (a != b).mean() > 0.8
+    betas = np.linspace(0.0, 1.0, 6)
+    r0 = oracle.run(q, L, 300, 1, 2, betas)
+    r0s = oracle.run(q, L, 300, 1, 2, betas, stream=0)
+    r5 = oracle.run(q, L, 300, 1, 2, betas, stream=5)
+    assert np.array_equal(r0["spins"], r0s["spins"])
+    assert not np.array_equal(r0["sumE"], r5["sumE"])
