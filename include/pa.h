@@ -29,9 +29,10 @@
  *   - Every call returns a pa_status.  Nothing aborts the process.  A call that
  *     fails leaves the context at its last complete temperature step.
  *   - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
- *     the 64-bit seed and a counter made of (site pair, sweep/colour, step,
- *     slot) for sweeps, (site/4, init) for initial states and (replica/4,
- *     resample, step) for copy numbers, so results do not depend on launch
+ *     the 64-bit seed and a counter made of (four same-colour sites, sweep and
+ *     colour, step, slot) for sweeps, (site/4, init, slot) for initial states
+ *     and (replica/4, resample, step) for copy numbers, with the stream number
+ *     in the top byte of the last word, so results do not depend on launch
  *     shapes, stream timing or the number of replicas per block.
  */
 #ifndef PA_H
@@ -76,7 +77,9 @@ typedef struct {
     int32_t init_mode;     /* PA_INIT_*                                              */
     double beta0;          /* inverse temperature of the initial population         */
     int32_t track_families;/* 1: keep ancestor ids and family statistics             */
-    int32_t reserved;      /* must be 0                                              */
+    int32_t stream;        /* 0..255: runs with one seed and different streams are
+                              independent (the stream is the top byte of the slot
+                              counter word); 0 for a lone run                        */
 } pa_config;
 
 /* Population estimators of one temperature step (Sec. 2 step 4, Sec. 3 Eq. 4):
@@ -102,7 +105,8 @@ typedef struct pa_ctx pa_ctx;
  * cfg->beta0 (Sec. 2 step 1 or Sec. 5 Eq. 6) with its energies, largest-state
  * occupations, energy histogram and step-0 estimators.
  * Errors: PA_ERR_INVALID for q outside 2..128, odd or out-of-range L, R < 1,
- * R_cap < R, beta0 < 0, an unknown mode, or reserved != 0; PA_ERR_NOMEM or
+ * R_cap < R or R_cap >= 2^24, beta0 < 0, an unknown mode, or a stream outside
+ * 0..255; PA_ERR_NOMEM or
  * PA_ERR_CUDA if allocation or a launch fails (nothing is leaked; *out = NULL). */
 pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 
@@ -229,6 +233,65 @@ pa_status pa_next_dbeta(pa_ctx *ctx, double target, double dbeta_cap, int32_t it
  * synchronisation per step (the step size decides the acceptance thresholds). */
 pa_status pa_run_adaptive(pa_ctx *ctx, double beta_end, double target, double dbeta_max, int32_t iters, int32_t theta,
                           int32_t max_steps, pa_obs *obs_out, double *betas_out, int32_t *K_out);
+
+/* ---- Batches of independent runs ------------------------------------------
+ * M independent PA runs, possibly with different q, L, R, theta and
+ * schedules, advanced together: each temperature step is six launches that
+ * cover every run (weights, copy numbers, parent map, one persistent sweep
+ * kernel over all runs' replica groups, estimators, step counter), so a
+ * captured CUDA graph of one step is replayed for the whole schedule.  All
+ * runs of a batch share one seed and should differ in cfg.stream; run m then
+ * gives exactly what a lone run (pa_init with cfg) gives on the same schedule. */
+typedef struct {
+    pa_config cfg;        /* as for pa_init; every run of a batch has the same seed  */
+    const double *betas;  /* betas[0..K] (host, read during pa_batch_create);
+                             betas[0] must equal cfg.beta0                          */
+    int32_t K;            /* temperature steps, >= 1                                 */
+    int32_t theta;        /* sweeps per step, >= 0                                   */
+} pa_run_desc;
+
+typedef struct pa_batch pa_batch;
+
+/* Allocates every run's buffers, uploads all steps' parameters and enqueues
+ * the initial populations with their step-0 estimators (synchronises).
+ * Errors: PA_ERR_INVALID for M outside 1..1024, any invalid run (as pa_init),
+ * differing seeds, K < 1, theta < 0 or a non-finite or negative beta;
+ * PA_ERR_NOMEM / PA_ERR_CUDA on allocation or launch failures. */
+pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream, pa_batch **out);
+
+/* Picks the sweep kernel's shared-memory budget per block (which sets the
+ * replicas per block of every run) and threads per block by timing the first
+ * temperature step for each candidate from the same initial populations, then
+ * restarts from them.  Results are cached per batch shape for the process.
+ * Only before pa_batch_run (PA_ERR_STATE after). */
+pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *threads_out);
+
+/* Sets the budget (bytes, >= the largest lattice) and threads per block
+ * (multiple of 32, 64..1024) by hand; PA_ERR_INVALID if they do not fit. */
+pa_status pa_batch_set_launch(pa_batch *b, int32_t smem_budget, int32_t threads);
+
+/* Current launch shape (any pointer may be NULL). */
+pa_status pa_batch_get_launch(pa_batch *b, int32_t *smem_budget, int32_t *threads, int32_t *blocks);
+
+/* Runs every run's schedule to its end (runs with fewer steps idle); use_graph
+ * = 1 captures one step as a CUDA graph and launches it max(K) times.
+ * Synchronises; returns PA_ERR_CAPACITY if a run outgrew its capacity.
+ * A batch runs once (PA_ERR_STATE on a second call). */
+pa_status pa_batch_run(pa_batch *b, int32_t use_graph);
+
+/* Estimators of run m at steps 0..K_m (host, K_m + 1 records). */
+pa_status pa_batch_observables(pa_batch *b, int32_t m, pa_obs *out);
+
+/* Replicas [slot_begin, slot_begin + count) of run m's current population, in
+ * the canonical [count][L][L] layout (host; synchronises). */
+pa_status pa_batch_get_spins(pa_batch *b, int32_t m, int64_t slot_begin, int64_t count, uint8_t *host);
+
+/* Current population size of run m (synchronises); returns that run's error
+ * (e.g. PA_ERR_CAPACITY) if it stopped. */
+pa_status pa_batch_population_size(pa_batch *b, int32_t m, int32_t *R_out);
+
+/* Releases the batch (synchronises its stream). */
+void pa_batch_destroy(pa_batch *b);
 
 /* Releases the context and its device memory (synchronises its stream). */
 void pa_destroy(pa_ctx *ctx);

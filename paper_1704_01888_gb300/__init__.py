@@ -36,7 +36,9 @@ EXPORTED = (
     "pa_get_spins", "pa_get_ancestors", "pa_run", "pa_destroy", "pa_status_str", "pa_last_cuda_error",
     "pa_set_launch", "pa_kernel_launch_count", "pa_profile", "pa_profile_read", "pa_observables_history",
     "pa_get_launch", "pa_resample_noalloc", "pa_reweight_forward", "pa_reweight_scale", "pa_reweight_grad_O",
-    "pa_overlap", "pa_next_dbeta", "pa_run_adaptive",
+    "pa_overlap", "pa_next_dbeta", "pa_run_adaptive", "pa_batch_create", "pa_batch_autotune", "pa_batch_set_launch",
+    "pa_batch_get_launch", "pa_batch_run", "pa_batch_observables", "pa_batch_get_spins", "pa_batch_destroy",
+    "pa_batch_population_size",
 )
 
 
@@ -50,8 +52,12 @@ class Config(ctypes.Structure):
     _fields_ = [
         ("q", ctypes.c_int32), ("L", ctypes.c_int32), ("R", ctypes.c_int32), ("R_cap", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("resample_mode", ctypes.c_int32), ("init_mode", ctypes.c_int32),
-        ("beta0", ctypes.c_double), ("track_families", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("beta0", ctypes.c_double), ("track_families", ctypes.c_int32), ("stream", ctypes.c_int32),
     ]
+
+
+class RunDesc(ctypes.Structure):
+    _fields_ = [("cfg", Config), ("betas", ctypes.c_void_p), ("K", ctypes.c_int32), ("theta", ctypes.c_int32)]
 
 
 class Obs(ctypes.Structure):
@@ -108,6 +114,15 @@ def load_library(path: str | None = None):
         "pa_overlap": ([P, i32, P, P, P], st),
         "pa_next_dbeta": ([P, f64, f64, i32, P], st),
         "pa_run_adaptive": ([P, f64, f64, f64, i32, i32, i32, P, P, P], st),
+        "pa_batch_create": ([P, i32, P, ctypes.POINTER(P)], st),
+        "pa_batch_autotune": ([P, P, P], st),
+        "pa_batch_set_launch": ([P, i32, i32], st),
+        "pa_batch_get_launch": ([P, P, P, P], st),
+        "pa_batch_run": ([P, i32], st),
+        "pa_batch_observables": ([P, i32, P], st),
+        "pa_batch_get_spins": ([P, i32, i64, i64, P], st),
+        "pa_batch_destroy": ([P], None),
+        "pa_batch_population_size": ([P, i32, P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -163,6 +178,7 @@ class PAParams:
     init_mode: int = INIT_RANDOM
     beta0: float = 0.0
     track_families: bool = False
+    stream: int = 0
 
 
 class Population:
@@ -173,7 +189,7 @@ class Population:
         self.params = params
         self.lib = load_library()
         cfg = Config(params.q, params.L, params.R, params.R_cap, params.seed, params.resample_mode,
-                     params.init_mode, params.beta0, int(params.track_families), 0)
+                     params.init_mode, params.beta0, int(params.track_families), int(params.stream))
         self._stream = _current_stream() if stream is None else stream
         self._ctx = ctypes.c_void_p()
         _check(self.lib.pa_init(ctypes.byref(cfg), ctypes.c_void_p(self._stream), ctypes.byref(self._ctx)),
@@ -317,3 +333,81 @@ class Population:
         self.step += K
         self.beta = float(betas[-1])
         return [o.as_dict() for o in obs], hist
+
+
+class Batch:
+    """M independent PA runs advanced together (include/pa.h, pa_batch_*).
+    `runs` is a list of (PAParams, betas, theta); all runs share one seed and
+    should differ in PAParams.stream."""
+
+    def __init__(self, runs, stream: int | None = None, autotune: bool = False):
+        self.lib = load_library()
+        self.runs = [(p, np.ascontiguousarray(b, dtype=np.float64), int(t)) for p, b, t in runs]
+        descs = (RunDesc * len(self.runs))()
+        for d, (p, b, t) in zip(descs, self.runs):
+            d.cfg = Config(p.q, p.L, p.R, p.R_cap, p.seed, p.resample_mode, p.init_mode, p.beta0,
+                           int(p.track_families), int(p.stream))
+            d.betas = b.ctypes.data
+            d.K = b.size - 1
+            d.theta = t
+        self._stream = _current_stream() if stream is None else stream
+        self._b = ctypes.c_void_p()
+        _check(self.lib.pa_batch_create(ctypes.cast(descs, ctypes.c_void_p), len(self.runs),
+                                        ctypes.c_void_p(self._stream), ctypes.byref(self._b)), "pa_batch_create")
+        self.tuned = None
+        if autotune:
+            self.tuned = self.autotune()
+
+    def close(self):
+        if self._b:
+            self.lib.pa_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def autotune(self):
+        a, t = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.pa_batch_autotune(self._b, ctypes.byref(a), ctypes.byref(t)), "pa_batch_autotune")
+        return a.value, t.value
+
+    def set_launch(self, smem_budget: int, threads: int):
+        _check(self.lib.pa_batch_set_launch(self._b, smem_budget, threads), "pa_batch_set_launch")
+
+    def launch_shape(self):
+        v = [ctypes.c_int32() for _ in range(3)]
+        _check(self.lib.pa_batch_get_launch(self._b, *[ctypes.byref(x) for x in v]), "pa_batch_get_launch")
+        return tuple(x.value for x in v)
+
+    def run(self, use_graph: bool = True):
+        _check(self.lib.pa_batch_run(self._b, int(use_graph)), "pa_batch_run")
+
+    def observables(self, m: int):
+        K = self.runs[m][1].size - 1
+        recs = (Obs * (K + 1))()
+        _check(self.lib.pa_batch_observables(self._b, m, ctypes.cast(recs, ctypes.c_void_p)), "pa_batch_observables")
+        return [r.as_dict() for r in recs]
+
+    def size(self, m: int) -> int:
+        r = ctypes.c_int32()
+        _check(self.lib.pa_batch_population_size(self._b, m, ctypes.byref(r)), "pa_batch_population_size")
+        return r.value
+
+    def status(self, m: int) -> int:
+        r = ctypes.c_int32()
+        return int(self.lib.pa_batch_population_size(self._b, m, ctypes.byref(r)))
+
+    def spins(self, m: int, begin: int, count: int) -> np.ndarray:
+        L = self.runs[m][0].L
+        out = np.zeros((count, L, L), dtype=np.uint8)
+        _check(self.lib.pa_batch_get_spins(self._b, m, begin, count, _ptr(out)), "pa_batch_get_spins")
+        return out

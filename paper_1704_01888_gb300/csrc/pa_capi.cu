@@ -199,6 +199,7 @@ pa::SweepArgs sweep_args(pa_ctx *c, double beta, int theta, int step, int gather
     a.step = step;
     a.rpb = c->rpb;
     a.gather = gather;
+    a.stream_hi = (uint32_t)c->cfg.stream << 24;
     return a;
 }
 
@@ -231,7 +232,7 @@ pa_status enqueue_resample(pa_ctx *c, double dbeta, int step)
     pa_status s = profile_mark(c, 1, true);
     if (s) return s;
     PA_CK(pa::launch_resample(c->hist, c->nbins, c->E, dbeta, c->cfg.R, c->R_cap, c->cfg.resample_mode, step,
-                              c->k0, c->k1, c->wtab, c->counts, c->local_off, c->blocksum, c->parent,
+                              (uint32_t)c->cfg.stream << 24, c->k0, c->k1, c->wtab, c->counts, c->local_off, c->blocksum, c->parent,
                               c->hist, c->st, c->stream));
     if ((s = profile_mark(c, 1, false))) return s;
     c->pending_step = step;
@@ -281,13 +282,13 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
     *out = nullptr;
     if (!cfg) return PA_ERR_INVALID;
     const pa_config &g = *cfg;
-    if (g.q < 2 || g.q > 128 || g.L < 2 || g.L > 1024 || (g.L & 1) || g.R < 1 || g.reserved != 0)
+    if (g.q < 2 || g.q > 128 || g.L < 2 || g.L > 1024 || (g.L & 1) || g.R < 1 || g.stream < 0 || g.stream > 255)
         return PA_ERR_INVALID;
     if (g.resample_mode != PA_RESAMPLE_NEAREST_INT && g.resample_mode != PA_RESAMPLE_ROUND) return PA_ERR_INVALID;
     if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
     if (!(g.beta0 >= 0.0) || !std::isfinite(g.beta0)) return PA_ERR_INVALID;
     long long R_cap = g.R_cap > 0 ? g.R_cap : (long long)g.R + g.R / 4 + 1024;
-    if (R_cap < g.R || R_cap > 0x7FFFFFFFLL - 1024) return PA_ERR_INVALID;
+    if (R_cap < g.R || R_cap >= (1LL << 24)) return PA_ERR_INVALID;
 
     pa_ctx *c = new (std::nothrow) pa_ctx();
     if (!c) return PA_ERR_NOMEM;
@@ -344,8 +345,8 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 3, c->stream);
     if (e == cudaSuccess && c->fam) e = cudaMemsetAsync(c->fam, 0, sizeof(int32_t) * g.R, c->stream);
     if (e == cudaSuccess)
-        e = pa::launch_init(c->spins[0], c->anc[0], g.q, g.L, g.R, c->k0, c->k1, g.init_mode == PA_INIT_GROUND,
-                            c->stream);
+        e = pa::launch_init(c->spins[0], c->anc[0], g.q, g.L, g.R, c->k0, c->k1, (uint32_t)g.stream << 24,
+                            g.init_mode == PA_INIT_GROUND, c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e));
     if ((s = enqueue_sweep(c, g.beta0, 0, 0))) return fail(s);
     if ((s = sync_state(c, nullptr))) return fail(s);

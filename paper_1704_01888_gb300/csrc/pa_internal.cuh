@@ -59,6 +59,7 @@ struct SweepArgs {
     int32_t q, L, theta, step;
     int32_t rpb;               // replicas per block iteration
     int32_t gather;            // 1: read parents from buf[parity], write buf[parity^1]
+    uint32_t stream_hi;        // stream number << 24 (top byte of the slot counter word)
 };
 
 // Launchers (pa_sweep.cu)
@@ -68,9 +69,9 @@ int sweep_max_blocks_per_sm(int L, int rpb, int threads);
 
 // Launchers (pa_resample.cu)
 cudaError_t launch_init(uint8_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
-                        int ground, cudaStream_t s);
+                        uint32_t stream_hi, int ground, cudaStream_t s);
 cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, double dbeta, int R_target,
-                            int R_cap, int mode, int step, uint32_t k0, uint32_t k1, double *wtab,
+                            int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1, double *wtab,
                             int32_t *counts, int32_t *local_off, int32_t *blocksum, int32_t *parent,
                             int32_t *hist_zero, DevState *st, cudaStream_t s);
 cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,

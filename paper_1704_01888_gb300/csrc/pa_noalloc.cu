@@ -130,7 +130,7 @@ extern "C" pa_status pa_resample_noalloc(const int32_t *E, int32_t R_prev, int32
     k_na_clear<<<(nbins + 1023) / 1024, 1024, 0, s>>>(hist, nbins, st, R_prev);
     k_na_hist<<<(R_prev + 255) / 256, 256, 0, s>>>(E, R_prev, 2 * N, hist, st);
     bump_launch_count(2);
-    cudaError_t e = launch_resample(hist, nbins, E, dbeta, R_target, parent_cap, mode, step, k0, k1, wtab, counts,
+    cudaError_t e = launch_resample(hist, nbins, E, dbeta, R_target, parent_cap, mode, step, 0u, k0, k1, wtab, counts,
                                     local_off, blocksum, parent, hist, st, s);
     if (e != cudaSuccess) return PA_ERR_CUDA;
     k_na_outputs<<<1, 1, 0, s>>>(st, lnQ_out, R_out);

@@ -29,6 +29,7 @@ class Workload:
     hist_bin: int = 1
     hist_steps: tuple = field(default_factory=tuple)
     track_families: bool = False
+    stream: int = 0
 
     @property
     def N(self) -> int:
@@ -81,14 +82,14 @@ C5.hist_steps = (nearest_step(C5, beta_t(20)), nearest_step(C5, beta_t(20)) + 1)
 def batched_runs(M: int = 64, seed: int = 1):
     """M independent runs: q from {5, 6, 8, 10}, L from {16, 32, 48, 64},
     R uniform in [10000, 50000] via SplitMix64, 150 steps to 1.1 beta_t(q),
-    theta = 10, run m seeded with 1 + m."""
+    theta = 10; all runs share the seed and run m has stream m."""
     runs = []
     for m in range(M):
         q = (5, 6, 8, 10)[m % 4]
         L = (16, 32, 48, 64)[(m // 4) % 4]
         R = 10000 + splitmix64(seed * 0x100000000 + m) % 40001
         runs.append(Workload(f"batch{m}", q=q, L=L, R=int(R), K=150, beta_end=1.1 * beta_t(q), theta=10,
-                             seed=1 + m))
+                             seed=seed, stream=m))
     return runs
 
 

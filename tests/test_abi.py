@@ -50,8 +50,8 @@ def test_status_strings_and_validation_without_gpu():
     # invalid configurations are rejected before any CUDA call
     ctx = ctypes.c_void_p()
     for bad in (dict(q=1, L=16, R=10), dict(q=10, L=15, R=10), dict(q=129, L=16, R=10),
-                dict(q=10, L=16, R=0), dict(q=10, L=16, R=10, R_cap=5)):
-        cfg = pa.Config(bad["q"], bad["L"], bad["R"], bad.get("R_cap", 0), 1, 0, 0, 0.0, 0, 0)
+                dict(q=10, L=16, R=0), dict(q=10, L=16, R=10, R_cap=5), dict(q=10, L=16, R=10, stream=256)):
+        cfg = pa.Config(bad["q"], bad["L"], bad["R"], bad.get("R_cap", 0), 1, 0, 0, 0.0, 0, bad.get("stream", 0))
         assert lib.pa_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == pa.PA_ERR_INVALID
         assert not ctx.value
     assert lib.pa_kernel_launch_count() == 0

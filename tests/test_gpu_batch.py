@@ -1,0 +1,107 @@
+"""Batches of independent runs: run m of a batch is bit-identical to a lone
+run with the same configuration (seed and stream), with or without graph
+capture and for any launch shape, and agrees with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1704_01888_gb300 as pa
+from paper_1704_01888_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1704_01888_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+def _mixed_runs():
+    """Mixed q, L (the site body for L = 6, run-time L = 24, 40), R, K, theta."""
+    spec = [(5, 16, 700, 6, 3), (10, 8, 400, 9, 2), (8, 6, 300, 5, 2), (6, 32, 500, 4, 3),
+            (10, 24, 350, 7, 2), (3, 40, 200, 3, 1), (20, 16, 900, 8, 0), (2, 64, 150, 2, 2)]
+    runs = []
+    for m, (q, L, R, K, theta) in enumerate(spec):
+        p = pa.PAParams(q=q, L=L, R=R, seed=9, stream=m)
+        betas = np.array([1.4 * i / K for i in range(K + 1)])
+        runs.append((p, betas, theta))
+    return runs
+
+
+def _lone(p, betas, theta):
+    with pa.Population(p) as pop:
+        obs0 = pop.observables()
+        obs, _ = pop.run(betas, theta)
+        return [obs0] + obs, pop.spins()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_runs_equal_lone_runs(graph):
+    runs = _mixed_runs()
+    with pa.Batch(runs) as b:
+        b.run(use_graph=graph)
+        got = [(b.observables(m), b.spins(m, 0, b.observables(m)[-1]["R"])) for m in range(len(runs))]
+    for m, (p, betas, theta) in enumerate(runs):
+        obs, spins = _lone(p, betas, theta)
+        bobs, bspins = got[m]
+        assert [o["sumE"] for o in bobs] == [o["sumE"] for o in obs], m
+        assert [o["lnZ"] for o in bobs] == [o["lnZ"] for o in obs], m
+        assert [o["R"] for o in bobs] == [o["R"] for o in obs], m
+        assert np.array_equal(bspins, spins), m
+
+
+def test_batch_launch_shapes_and_autotune_do_not_change_results():
+    runs = _mixed_runs()[:5]
+    results = []
+    for shape in (None, (16384, 256), (131072, 1024), "tune"):
+        with pa.Batch(runs) as b:
+            if shape == "tune":
+                b.autotune()
+            elif shape:
+                b.set_launch(*shape)
+            b.run(use_graph=True)
+            results.append([b.spins(m, 0, 50) for m in range(len(runs))] +
+                           [[o["sumE"] for o in b.observables(m)] for m in range(len(runs))])
+    for r in results[1:]:
+        for a, c in zip(results[0], r):
+            assert np.array_equal(np.asarray(a), np.asarray(c))
+
+
+def test_batch_runs_match_oracle():
+    runs = _mixed_runs()
+    with pa.Batch(runs) as b:
+        b.run(use_graph=True)
+        for m in (0, 2, 4):
+            p, betas, theta = runs[m]
+            ref = oracle.run(p.q, p.L, p.R, p.seed, theta, betas, stream=p.stream)
+            obs = b.observables(m)
+            assert [o["sumE"] for o in obs] == list(ref["sumE"])
+            assert [o["R"] for o in obs] == list(ref["R"])
+            assert np.allclose([o["lnZ"] for o in obs], ref["lnZ"], rtol=1e-10, atol=0)
+            assert np.array_equal(b.spins(m, 0, ref["R_final"]), ref["spins"])
+
+
+def test_batched_configuration_first_steps_against_oracle():
+    """The 64-run batched configuration (q in {5,6,8,10}, L in {16,32,48,64},
+    R in [1e4, 5e4], theta = 10) for its first 3 steps: the L = 16 and L = 32
+    runs of q = 5 against the oracle, every run against its lone run."""
+    all_runs = wl.batched_runs()
+    runs = []
+    for w in all_runs:
+        p = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed, stream=w.stream)
+        runs.append((p, w.betas()[:4], w.theta))
+    with pa.Batch(runs, autotune=True) as b:
+        b.run(use_graph=True)
+        for m in (0, 5):  # (q, L) = (5, 16) and (6, 32)
+            p, betas, theta = runs[m]
+            ref = oracle.run(p.q, p.L, p.R, p.seed, theta, betas, stream=p.stream, want_state=False)
+            obs = b.observables(m)
+            assert [o["sumE"] for o in obs] == list(ref["sumE"]), m
+            assert [o["sumMt"] for o in obs] == list(ref["sumMt"]), m
+        for m in range(0, 64, 9):
+            p, betas, theta = runs[m]
+            lone, _ = _lone(p, betas, theta)
+            assert [o["sumE"] for o in b.observables(m)] == [o["sumE"] for o in lone], m

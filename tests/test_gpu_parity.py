@@ -138,6 +138,19 @@ def test_edge_cases_bit_exact(q, L, R, theta, K, extra):
     _compare(g, o)
 
 
+@pytest.mark.parametrize("q,L,R,betas", [
+    (3, 40, 200, [0.0, 0.467, 0.933, 1.4]),   # steps large enough that exp overflows off E_ref
+    (2, 64, 150, [0.0, 0.7, 1.4]),
+    (4, 16, 300, [2.5, 1.2, 0.0]),           # heating with large negative steps
+])
+def test_large_temperature_steps(q, L, R, betas):
+    b = np.array(betas)
+    init = pa.INIT_GROUND if b[0] > 0 else pa.INIT_RANDOM
+    g = _gpu_run(q, L, R, 21, 2, b, init=init)
+    o = _oracle_run(q, L, R, 21, 2, b, init=1 if init == pa.INIT_GROUND else 0)
+    _compare(g, o)
+
+
 def test_heating_from_ground_state_with_families():
     q, L, R, K = 6, 16, 600, 15
     b = np.array([3.0 - 3.0 * i / K for i in range(K + 1)])
