@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--R", type=int, default=0, help="override the population size (profiling runs)")
     ap.add_argument("--launch", default="", help="replicas_per_block,threads_per_block for the sweep kernel")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, adaptive and strong first-order measurements")
     return ap.parse_args()
 
 
@@ -134,6 +136,11 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def _sweep_sources() -> bytes:
+    csrc = os.path.join(ROOT, "paper_1704_01888_gb300", "csrc")
+    return b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("pa_sweep.cu", "pa_kernels.cuh", "pa_internal.cuh"))
+
+
 def _sweep_traffic_per_replica():
     """DRAM bytes per replica per sweep launch from the committed ncu summary,
     valid only while the sweep kernel sources are unchanged."""
@@ -146,8 +153,7 @@ def _sweep_traffic_per_replica():
             rec[key.strip()] = val.strip()
     except OSError:
         return None
-    csrc = os.path.join(ROOT, "paper_1704_01888_gb300", "csrc")
-    src = open(os.path.join(csrc, "pa_sweep.cu"), "rb").read() + open(os.path.join(csrc, "pa_internal.cuh"), "rb").read()
+    src = _sweep_sources()
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return float(rec["dram_bytes_per_replica"])
@@ -305,6 +311,12 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu:
         cpu = _cpu_baseline(w)
 
+    extras = {}
+    if world == 1 and not args.no_extras and not args.R:
+        extras["batched"] = _batched(pa)
+        extras["strong_first_order"] = _strong_first_order(pa)
+        extras["adaptive"] = _adaptive(pa)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -324,6 +336,7 @@ def run_ours(args):
         "final": {"beta": final_obs["beta"], "lnZ": final_obs["lnZ"], "meanE_per_site": final_obs["meanE"] / w.N,
                   "R": final_obs["R"]},
     }
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -368,6 +381,104 @@ def _e2e(pa, w, params, betas, W, K, rank, world, launch):
     return {"value": attempts / (dt * 1e9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
             "note": "population generated on the device from the seed; per step beta and dbeta travel as "
                     "kernel arguments; per step the host reads ln Q, R_i, the estimators and the histogram"}
+
+
+def _batched(pa):
+    """64 independent runs (q in {5,6,8,10}, L in {16,32,48,64}, R in [1e4, 5e4],
+    150 steps, theta = 10): one persistent launch per kernel and a graph per
+    temperature step, against the same runs launched one after another."""
+    import torch
+
+    ws = wl.batched_runs()
+    runs = [(pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed, stream=w.stream), w.betas(), w.theta) for w in ws]
+    attempts = sum(w.R * w.N * w.theta * w.K for w in ws)  # expected; exact counts below
+    steps = sum(w.K for w in ws)
+    b = pa.Batch(runs)
+    tuned = b.autotune()
+    launches0 = pa.kernel_launch_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(use_graph=True)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    launches_batch = pa.kernel_launch_count() - launches0
+    exact = sum(sum(o["R"] for o in b.observables(m)[1:]) * ws[m].N * ws[m].theta for m in range(len(ws)))
+    last_b = [b.observables(m)[-1]["sumE"] for m in range(len(ws))]
+    b.close()
+    t_plain, last_p = 0.0, []
+    for p, betas, theta in runs:
+        with pa.Population(p) as pop:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            obs, _ = pop.run(betas, theta)
+            torch.cuda.synchronize()
+            t_plain += time.perf_counter() - t0
+            last_p.append(obs[-1]["sumE"])
+    return {"workload": "batch of 64 runs, q 5-10, L 16-64, R 1e4-5e4, 150 steps, theta 10",
+            "pa_steps_per_s": steps / t_batch, "attempts_per_ns": exact / t_batch / 1e9,
+            "plain_pa_steps_per_s": steps / t_plain, "plain_attempts_per_ns": exact / t_plain / 1e9,
+            "speedup_vs_plain": t_plain / t_batch, "graph": True, "launches": launches_batch,
+            "autotuned": {"smem_budget": tuned[0], "threads": tuned[1]},
+            "identical_to_plain": last_b == last_p, "expected_attempts": attempts}
+
+
+def _strong_first_order(pa, warm=2, timed=6):
+    """q = 20, L = 256, R = 1e5, theta = 20, families tracked: a few steps."""
+    import torch
+
+    w = wl.C5
+    b = w.betas()
+    with pa.Population(pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed, track_families=True)) as pop:
+        for i in range(1, warm + 1):
+            pop.resample(b[i] - b[i - 1], i)
+            pop.sweep(b[i], w.theta, i)
+        torch.cuda.synchronize()
+        pop.profile(True)
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        for i in range(warm + 1, warm + timed + 1):
+            pop.resample(b[i] - b[i - 1], i)
+            pop.sweep(b[i], w.theta, i)
+        stop.record()
+        stop.synchronize()
+        ms = start.elapsed_time(stop)
+        h = pop.history(timed)
+        att = sum(x["R"] for x in h) * w.N * w.theta
+        return {"workload": w.name, "steps": f"{warm + 1}..{warm + timed} of {w.K}", "attempts_per_ns": att / ms / 1e6,
+                "ms_per_step": ms / timed, "launch": list(pop.launch_shape()), "S_f": h[-1]["S_f"],
+                "n_families": h[-1]["n_families"]}
+
+
+def _adaptive(pa, R=20000, seeds=4):
+    """q = 8, L = 128 to 1.1 beta_t: adaptive steps (overlap 0.85) against
+    constant steps with the same number of steps, ln Z / N spread over seeds
+    (R reduced from 2e5 to keep the measurement short)."""
+    import torch
+
+    w = wl.C4
+    res = {"adaptive": [], "constant": []}
+    for seed in range(1, seeds + 1):
+        with pa.Population(pa.PAParams(q=w.q, L=w.L, R=R, seed=seed)) as pop:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            obs, betas = pop.run_adaptive(w.beta_end, w.theta, target=0.85, dbeta_max=0.05)
+            torch.cuda.synchronize()
+            res["adaptive"].append((obs[-1]["lnZ"] / w.N, len(betas), time.perf_counter() - t0))
+        K = len(betas)
+        bc = np.array([w.beta_end * i / K for i in range(K + 1)])
+        with pa.Population(pa.PAParams(q=w.q, L=w.L, R=R, seed=seed)) as pop:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            obs, _ = pop.run(bc, w.theta)
+            torch.cuda.synchronize()
+            res["constant"].append((obs[-1]["lnZ"] / w.N, K, time.perf_counter() - t0))
+    out = {"workload": f"q=8 L=128 R={R} (reduced from 200000), beta 0 -> {w.beta_end:.4f}, theta=10, overlap 0.85",
+           "seeds": seeds}
+    for k, v in res.items():
+        a = np.array(v)
+        out[k] = {"lnZ_per_site_mean": float(a[:, 0].mean()), "lnZ_per_site_std": float(a[:, 0].std(ddof=1)),
+                  "steps": [int(x) for x in a[:, 1]], "pa_steps_per_s": float(a[:, 1].sum() / a[:, 2].sum())}
+    return out
 
 
 def main():

@@ -231,11 +231,9 @@ struct pa_batch {
 
 namespace {
 
-thread_local std::string t_batch_error;
-
 pa_status bfail(cudaError_t e)
 {
-    t_batch_error = cudaGetErrorString(e);
+    pa::record_cuda_error(cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PA_ERR_NOMEM : PA_ERR_CUDA;
 }
 
@@ -281,7 +279,9 @@ pa_status apply_launch(pa_batch *b, int budget, int threads)
     int dev = 0, optin = 0;
     PB_CK(cudaGetDevice(&dev));
     PB_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const int static_smem = 9 * 4 + (pa::kMaxRuns + 1) * 4 + 64;
+    cudaFuncAttributes fa;
+    PB_CK(cudaFuncGetAttributes(&fa, pa::k_batch_sweep));
+    const int static_smem = (int)fa.sharedSizeBytes;
     if (budget < 1024 || threads < 64 || threads > 1024 || threads % 32) return PA_ERR_INVALID;
     if (budget + static_smem > optin) return PA_ERR_INVALID;
     for (int m = 0; m < b->M; ++m) {

@@ -26,11 +26,15 @@ static std::atomic<long long> g_launches{0};
 
 int64_t bump_launch_count(int64_t n) { return g_launches.fetch_add(n) + n; }
 
+static thread_local std::string t_cuda_error;
+
+void record_cuda_error(const char *msg) { t_cuda_error = msg; }
+
 }  // namespace pa
 
 namespace {
 
-thread_local std::string t_cuda_error;
+using pa::t_cuda_error;
 
 pa_status cuda_fail(cudaError_t e)
 {

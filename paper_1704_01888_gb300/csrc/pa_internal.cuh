@@ -85,6 +85,9 @@ cudaError_t launch_newton(const int32_t *hist, int nbins, const DevState *st, do
 
 int64_t bump_launch_count(int64_t n);
 
+// Records the message returned by pa_last_cuda_error() on this thread.
+void record_cuda_error(const char *msg);
+
 }  // namespace pa
 
 namespace pa {

@@ -95,6 +95,25 @@ struct Vec<4> {
     }
 };
 
+// Block-wide sum of ints; every thread receives it.  All threads must call.
+__device__ __forceinline__ int block_sum_int(int v)
+{
+    __shared__ int s_red[33];
+    v = __reduce_add_sync(0xFFFFFFFFu, v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0;
+        x = __reduce_add_sync(0xFFFFFFFFu, x);
+        if (lane == 0) s_red[32] = x;
+    }
+    __syncthreads();
+    const int r = s_red[32];
+    __syncthreads();
+    return r;
+}
+
 // ===========================================================================
 // One group of resident replicas
 // ===========================================================================
@@ -235,27 +254,31 @@ __device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 
         }
     }
 
-    // measurements: one warp per replica
-    for (int r = warp; r < nrep; r += nwarps) {
+    // measurements: one warp per replica, or the whole block per replica when
+    // the block holds fewer replicas than warps
+    const bool cooperative = 2 * nrep <= nwarps;
+    const int mstep = cooperative ? (int)blockDim.x : 32;
+    const int mlane = cooperative ? tid : lane;
+    for (int r = cooperative ? 0 : warp; r < nrep; r += cooperative ? 1 : nwarps) {
         const uint32_t *rep = sw + r * WPR;
         int agree = 0;
-        for (int w = lane; w < WPC; w += 32) {
+        for (int w = mlane; w < WPC; w += mstep) {
             const int y = w / L8;
             const int t = w - y * L8;
             const Neighbours nb = load_neighbours(rep + WPC, L, L8, y, t, y & 1);
             const uint32_t d = count_differ(rep[w], nb.up, nb.down, nb.same, nb.shifted);
             agree += 16 - (int)((d * 0x01010101u) >> 24);
         }
-        agree = __reduce_add_sync(0xFFFFFFFFu, agree);
+        agree = cooperative ? block_sum_int(agree) : __reduce_add_sync(0xFFFFFFFFu, agree);
         int best = 0;
         for (int s = 0; s < G.q; ++s) {
             const uint32_t S4 = (uint32_t)s * 0x01010101u;
             int cnt = 0;
-            for (int w = lane; w < WPR; w += 32) cnt += 4 - __popc(differ_bits(rep[w], S4));
-            cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+            for (int w = mlane; w < WPR; w += mstep) cnt += 4 - __popc(differ_bits(rep[w], S4));
+            cnt = cooperative ? block_sum_int(cnt) : __reduce_add_sync(0xFFFFFFFFu, cnt);
             best = max(best, cnt);
         }
-        if (lane == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
+        if (mlane == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
     }
     group_families(G);
     __syncthreads();
