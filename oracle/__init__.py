@@ -21,6 +21,8 @@ _LIB = os.path.join(_HERE, "libpa_oracle.so")
 
 NEAREST_INT = 0
 ROUND = 1
+POISSON = 2
+OFF = 3
 INIT_RANDOM = 0
 INIT_GROUND = 1
 

@@ -236,7 +236,37 @@ ORC_API void orc_init_ground(int q, int L, int64_t slot_begin, int64_t count, ui
 /* ------------------------------------------------------------------------- */
 /* Resampling (Sec. 2, step 2).                                                */
 /* ------------------------------------------------------------------------- */
-enum { ORC_NEAREST_INT = 0, ORC_ROUND = 1 };
+enum { ORC_NEAREST_INT = 0, ORC_ROUND = 1, ORC_POISSON = 2, ORC_OFF = 3 };
+
+/* A Poisson draw with mean rho for replica j (Sec. 2, Eq. 1), by inversion of
+ * the cumulative distribution, the mean split into pieces of at most 64 (a
+ * sum of independent Poisson variables is Poisson with the summed mean, and
+ * exp(-64) is far from underflow).  The k-th uniform, (U_k + 1/2) / 2^32, is
+ * word k & 3 of counter (j, RESAMPLE | (1 + k / 4), step, stream << 24). */
+static int32_t orc_poisson(double rho, int64_t j, uint32_t step, uint64_t seed, uint32_t stream)
+{
+    int32_t r = 0;
+    double remaining = rho;
+    uint32_t k = 0;
+    uint32_t w[4] = {0, 0, 0, 0};
+    while (remaining > 0.0) {
+        double mu = remaining < 64.0 ? remaining : 64.0;
+        remaining = remaining - mu;
+        if ((k & 3) == 0) orc_draw(seed, (uint32_t)j, ORC_DOM_RESAMPLE | (1u + (k >> 2)), step, stream << 24, w);
+        double u = ((double)w[k & 3] + 0.5) / 4294967296.0;
+        k += 1;
+        double p = exp(-mu);
+        double F = p;
+        int32_t n = 0;
+        while (u > F && n < 1000) {
+            n += 1;
+            p = p * mu / (double)n;
+            F = F + p;
+        }
+        r += n;
+    }
+    return r;
+}
 
 /* Computes Q_i and the copy numbers r_j for the R_prev replicas with energies
  * E[j], from beta_{i-1} to beta_i = beta_{i-1} + dbeta.
@@ -249,7 +279,9 @@ enum { ORC_NEAREST_INT = 0, ORC_ROUND = 1 };
  * reading: "nearest-integer" copy numbers draw r_j from the two integers
  * nearest to rho_j with the mean kept exact: r_j = floor(rho_j) + [u_j <
  * frac(rho_j) 2^32], u_j = word (j & 3) of counter (j >> 2, RESAMPLE, step, 0).
- * ORC_ROUND instead takes the nearest integer, halves rounded up.
+ * ORC_ROUND instead takes the nearest integer, halves rounded up;
+ * ORC_POISSON draws r_j ~ Pois(rho_j), the paper's Eq. 1; ORC_OFF keeps every
+ * replica once (the resampling-off comparison of Sec. 5, Fig. 2 right).
  * rho_out (optional) receives rho_j.  Returns the new population size. */
 ORC_API int64_t orc_copy_numbers(int64_t R_prev, const int32_t *E, double dbeta, int64_t R_target,
                                  int mode, uint32_t step, uint64_t seed, uint32_t stream, int32_t *r,
@@ -270,6 +302,16 @@ ORC_API int64_t orc_copy_numbers(int64_t R_prev, const int32_t *E, double dbeta,
         double n = floor(rho);
         double frac = rho - n;
         int32_t up;
+        if (mode == ORC_POISSON) {
+            r[j] = orc_poisson(rho, j, step, seed, stream);
+            total += r[j];
+            continue;
+        }
+        if (mode == ORC_OFF) {
+            r[j] = 1;
+            total += 1;
+            continue;
+        }
         if (mode == ORC_ROUND) {
             up = frac >= 0.5;
         } else {

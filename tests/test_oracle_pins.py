@@ -484,3 +484,37 @@ def test_streams_give_independent_runs_under_one_key():
     r5 = oracle.run(q, L, 300, 1, 2, betas, stream=5)
     assert np.array_equal(r0["spins"], r0s["spins"])
     assert not np.array_equal(r0["sumE"], r5["sumE"])
+
+
+def test_poisson_copy_numbers_follow_eq_1():
+    """r_j ~ Pois(rho_j) (Sec. 2, Eq. 1): over many steps the counts of one
+    replica have the Poisson mean and variance, and the total is Poisson(R)
+    on average; a mean above the 64 piece size is handled."""
+    rng = np.random.default_rng(9)
+    R = 50
+    E = rng.integers(-60, -40, size=R).astype(np.int32)
+    draws, tot = [], []
+    for step in range(1, 4001):
+        r, _, Rn, rho = oracle.copy_numbers(E, 0.08, R, oracle.POISSON, step, 2)
+        draws.append(r)
+        tot.append(Rn)
+    d = np.array(draws)
+    mean, var = d.mean(axis=0), d.var(axis=0)
+    se = np.sqrt(rho / 4000)
+    assert np.all(np.abs(mean - rho) < 6 * se + 1e-9)
+    big = np.argmax(rho)
+    assert var[big] == pytest.approx(rho[big], rel=0.15)
+    assert abs(np.mean(tot) - R) < 6 * math.sqrt(R / 4000)
+    # one replica holding the whole population (mean R > 64)
+    Ebig = np.array([-100] + [-10] * 9, np.int32)
+    vals = [oracle.copy_numbers(Ebig, 1.0, 300, oracle.POISSON, s, 3)[0][0] for s in range(1, 1501)]
+    assert abs(np.mean(vals) - 300) < 6 * math.sqrt(300 / 1500)
+    assert np.var(vals) == pytest.approx(300, rel=0.15)
+
+
+def test_resampling_off_keeps_every_replica():
+    E = np.arange(-50, -10, dtype=np.int32)
+    r, lnQ, Rn, _ = oracle.copy_numbers(E, 0.3, 40, oracle.OFF, 1, 1)
+    assert np.all(r == 1) and Rn == 40
+    out = oracle.run(6, 8, 300, 1, 2, np.linspace(0, 1.5, 11), mode=oracle.OFF)
+    assert np.all(out["R"] == 300) and np.all(out["n_families"] == 300)  # no family is lost
