@@ -57,11 +57,14 @@ typedef enum {
 } pa_status;
 
 /* Copy-number rule for the resampling step (Sec. 2, step 2).  The paper draws
- * r_j from a Poisson law with mean (R/R_{i-1}) tau_i(E_j) (Eq. 1).  NEAREST_INT
- * takes one of the two integers nearest to that mean, floor(rho_j) + 1 with
- * probability frac(rho_j), so the mean is kept and the spread is minimal;
- * ROUND takes the nearest integer outright (halves up). */
-enum { PA_RESAMPLE_NEAREST_INT = 0, PA_RESAMPLE_ROUND = 1 };
+ * r_j from a Poisson law with mean rho_j = (R/R_{i-1}) tau_i(E_j) (Eq. 1):
+ * POISSON (inversion of the distribution, the mean split into pieces of at
+ * most 64).  NEAREST_INT takes one of the two integers nearest to rho_j,
+ * floor(rho_j) + 1 with probability frac(rho_j), so the mean is kept and the
+ * spread is minimal; ROUND takes the nearest integer outright (halves up);
+ * OFF keeps every replica once (the resampling-off comparison of Sec. 5,
+ * Fig. 2 right; ln Q is still computed). */
+enum { PA_RESAMPLE_NEAREST_INT = 0, PA_RESAMPLE_ROUND = 1, PA_RESAMPLE_POISSON = 2, PA_RESAMPLE_OFF = 3 };
 
 /* Initial population (Sec. 2 step 1; Sec. 5 Eq. 6). */
 enum { PA_INIT_RANDOM = 0, /* beta_0 = 0: independent uniform spins, ln Z_0 = N ln q        */
@@ -292,6 +295,21 @@ pa_status pa_batch_population_size(pa_batch *b, int32_t m, int32_t *R_out);
 
 /* Releases the batch (synchronises its stream). */
 void pa_batch_destroy(pa_batch *b);
+
+/* Checkpoint of the current population (Sec. 2: the PA state between
+ * temperature steps): configuration, step, inverse temperature, ln Z, spins,
+ * energies, occupations, energy histogram, family ids and the latest
+ * estimators, with a checksum.  The random numbers are counter-based, so a
+ * run resumed with pa_load continues bit for bit as the uninterrupted run.
+ * Synchronises.  PA_ERR_STATE with a resample pending or a failed context;
+ * PA_ERR_INVALID if the file cannot be written.  Files are read back on
+ * machines of the same byte order. */
+pa_status pa_save(pa_ctx *ctx, const char *path);
+
+/* Creates a context from a checkpoint written by pa_save (synchronises).
+ * PA_ERR_INVALID for a missing, truncated or corrupted file (bad header,
+ * sizes or checksum: checked before any device work); otherwise as pa_init. */
+pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out);
 
 /* Releases the context and its device memory (synchronises its stream). */
 void pa_destroy(pa_ctx *ctx);

@@ -27,6 +27,8 @@ LIB_PATH = os.path.join(_HERE, "libpa_gb300.so")
  PA_ERR_TOO_LARGE) = range(8)
 RESAMPLE_NEAREST_INT = 0
 RESAMPLE_ROUND = 1
+RESAMPLE_POISSON = 2
+RESAMPLE_OFF = 3
 INIT_RANDOM = 0
 INIT_GROUND = 1
 
@@ -38,7 +40,7 @@ EXPORTED = (
     "pa_get_launch", "pa_resample_noalloc", "pa_reweight_forward", "pa_reweight_scale", "pa_reweight_grad_O",
     "pa_overlap", "pa_next_dbeta", "pa_run_adaptive", "pa_batch_create", "pa_batch_autotune", "pa_batch_set_launch",
     "pa_batch_get_launch", "pa_batch_run", "pa_batch_observables", "pa_batch_get_spins", "pa_batch_destroy",
-    "pa_batch_population_size",
+    "pa_batch_population_size", "pa_save", "pa_load",
 )
 
 
@@ -123,6 +125,8 @@ def load_library(path: str | None = None):
         "pa_batch_get_spins": ([P, i32, i64, i64, P], st),
         "pa_batch_destroy": ([P], None),
         "pa_batch_population_size": ([P, i32, P], st),
+        "pa_save": ([P, ctypes.c_char_p], st),
+        "pa_load": ([ctypes.c_char_p, P, ctypes.POINTER(P)], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -185,12 +189,18 @@ class Population:
     """One PA run on the GPU: a population of R_i replicas of the L x L Potts
     lattice at the current inverse temperature (Sec. 2)."""
 
-    def __init__(self, params: PAParams, stream: int | None = None):
+    def __init__(self, params: PAParams, stream: int | None = None, _ctx=None, _step=0, _beta=None):
         self.params = params
         self.lib = load_library()
+        self._stream = _current_stream() if stream is None else stream
+        if _ctx is not None:
+            self._ctx = _ctx
+            self.N = params.L * params.L
+            self.step = _step
+            self.beta = _beta
+            return
         cfg = Config(params.q, params.L, params.R, params.R_cap, params.seed, params.resample_mode,
                      params.init_mode, params.beta0, int(params.track_families), int(params.stream))
-        self._stream = _current_stream() if stream is None else stream
         self._ctx = ctypes.c_void_p()
         _check(self.lib.pa_init(ctypes.byref(cfg), ctypes.c_void_p(self._stream), ctypes.byref(self._ctx)),
                "pa_init")
@@ -246,6 +256,29 @@ class Population:
         _check(self.lib.pa_observables(self._ctx, ctypes.byref(obs), _ptr(hist) if with_hist else None,
                                        hist.size if with_hist else 0), "pa_observables")
         return (obs.as_dict(), hist) if with_hist else obs.as_dict()
+
+    def save(self, path: str):
+        """Checkpoint (include/pa.h, pa_save)."""
+        _check(self.lib.pa_save(self._ctx, os.fsencode(path)), "pa_save")
+
+    @classmethod
+    def load(cls, path: str, stream: int | None = None) -> "Population":
+        """Resume from a checkpoint written by save()."""
+        lib = load_library()
+        s = _current_stream() if stream is None else stream
+        ctx = ctypes.c_void_p()
+        _check(lib.pa_load(os.fsencode(path), ctypes.c_void_p(s), ctypes.byref(ctx)), "pa_load")
+        obs = Obs()
+        _check(lib.pa_observables(ctx, ctypes.byref(obs), None, 0), "pa_observables")
+        # the configuration travels in the file; rebuild the parameters from it
+        with open(path, "rb") as f:
+            head = f.read(16 + ctypes.sizeof(Config) + 8 + 8)
+        cfg = Config.from_buffer_copy(head[16:16 + ctypes.sizeof(Config)])
+        step = int.from_bytes(head[16 + ctypes.sizeof(Config):20 + ctypes.sizeof(Config)], "little", signed=True)
+        p = PAParams(q=cfg.q, L=cfg.L, R=cfg.R, seed=cfg.seed, R_cap=cfg.R_cap, resample_mode=cfg.resample_mode,
+                     init_mode=cfg.init_mode, beta0=cfg.beta0, track_families=bool(cfg.track_families),
+                     stream=cfg.stream)
+        return cls(p, stream=s, _ctx=ctx, _step=step, _beta=obs.beta)
 
     def history(self, count: int) -> list:
         """Estimators of the last `count` completed steps, oldest first."""

@@ -386,7 +386,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         if (g.q < 2 || g.q > 128 || g.L < 2 || g.L > 1024 || (g.L & 1) || g.R < 1 || g.stream < 0 ||
             g.stream > 255 || g.seed != seed || runs[m].K < 1 || runs[m].theta < 0 || !runs[m].betas)
             return PA_ERR_INVALID;
-        if (g.resample_mode != PA_RESAMPLE_NEAREST_INT && g.resample_mode != PA_RESAMPLE_ROUND) return PA_ERR_INVALID;
+        if (g.resample_mode < PA_RESAMPLE_NEAREST_INT || g.resample_mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
         if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
         if (!(g.beta0 >= 0.0) || runs[m].betas[0] != g.beta0) return PA_ERR_INVALID;
         for (int i = 0; i <= runs[m].K; ++i)

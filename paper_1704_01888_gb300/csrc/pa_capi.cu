@@ -12,6 +12,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -280,15 +281,18 @@ const char *pa_last_cuda_error(void) { return t_cuda_error.c_str(); }
 
 int64_t pa_kernel_launch_count(void) { return pa::g_launches.load(); }
 
-pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
+}  // extern "C"
+
+namespace {
+
+// Validates a configuration, allocates a context and its device buffers and
+// picks the sweep launch shape; no kernel runs.
+pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
 {
-    if (!out) return PA_ERR_INVALID;
     *out = nullptr;
-    if (!cfg) return PA_ERR_INVALID;
-    const pa_config &g = *cfg;
     if (g.q < 2 || g.q > 128 || g.L < 2 || g.L > 1024 || (g.L & 1) || g.R < 1 || g.stream < 0 || g.stream > 255)
         return PA_ERR_INVALID;
-    if (g.resample_mode != PA_RESAMPLE_NEAREST_INT && g.resample_mode != PA_RESAMPLE_ROUND) return PA_ERR_INVALID;
+    if (g.resample_mode < PA_RESAMPLE_NEAREST_INT || g.resample_mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
     if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
     if (!(g.beta0 >= 0.0) || !std::isfinite(g.beta0)) return PA_ERR_INVALID;
     long long R_cap = g.R_cap > 0 ? g.R_cap : (long long)g.R + g.R / 4 + 1024;
@@ -335,16 +339,60 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
     if ((s = dev_alloc(&c->obs, c->obs_cap))) return fail(s);
     c->stage_bytes = spin_bytes < (64u << 20) ? spin_bytes : (64u << 20);
     if ((s = dev_alloc(&c->stage, c->stage_bytes))) return fail(s);
-
     if ((s = choose_launch(c, 0, 0))) return fail(s);
+    *out = c;
+    return PA_OK;
+}
 
+// Checkpoint file: a fixed header, the population's arrays, and an FNV-1a
+// checksum of everything before it.
+constexpr char kMagic[8] = {'P', 'A', 'G', 'B', '3', '0', '0', '\x01'};
+constexpr uint32_t kVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    pa_config cfg;
+    int32_t step, pop;
+    double beta, lnZ;
+    pa_obs last;
+    uint64_t payload_bytes;
+};
+
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h)
+{
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
+{
+    if (!out) return PA_ERR_INVALID;
+    *out = nullptr;
+    if (!cfg) return PA_ERR_INVALID;
+    const pa_config &g = *cfg;
+    pa_ctx *c = nullptr;
+    pa_status s = ctx_create(g, cuda_stream, &c);
+    if (s) return s;
+    auto fail = [&](pa_status e) {
+        release(c);
+        delete c;
+        return e;
+    };
     pa::DevState h{};
     h.pop = g.R;
     if (g.init_mode == PA_INIT_GROUND)
         h.lnZ = std::log((double)g.q) - g.beta0 * (double)(-2 * c->N);
     else
         h.lnZ = (double)c->N * std::log((double)g.q);
-    e = cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->hist, 0, sizeof(int32_t) * c->nbins, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 3, c->stream);
     if (e == cudaSuccess && c->fam) e = cudaMemsetAsync(c->fam, 0, sizeof(int32_t) * g.R, c->stream);
@@ -354,6 +402,110 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
     if (e != cudaSuccess) return fail(cuda_fail(e));
     if ((s = enqueue_sweep(c, g.beta0, 0, 0))) return fail(s);
     if ((s = sync_state(c, nullptr))) return fail(s);
+    *out = c;
+    return PA_OK;
+}
+
+pa_status pa_save(pa_ctx *c, const char *path)
+{
+    if (!c || !path) return PA_ERR_INVALID;
+    if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
+    pa::DevState st;
+    pa_status s = sync_state(c, &st);
+    if (s) return s;
+    const size_t pop = (size_t)st.pop, N = (size_t)c->N;
+    const bool fam = c->cfg.track_families != 0;
+    std::vector<unsigned char> payload(pop * N + 4 * (2 * pop + (size_t)c->nbins + (fam ? pop : 0)));
+    unsigned char *p = payload.data();
+    PA_CK(cudaMemcpy(p, c->spins[st.parity], pop * N, cudaMemcpyDeviceToHost));
+    p += pop * N;
+    PA_CK(cudaMemcpy(p, c->E, 4 * pop, cudaMemcpyDeviceToHost));
+    p += 4 * pop;
+    PA_CK(cudaMemcpy(p, c->Mt, 4 * pop, cudaMemcpyDeviceToHost));
+    p += 4 * pop;
+    PA_CK(cudaMemcpy(p, c->hist, 4 * (size_t)c->nbins, cudaMemcpyDeviceToHost));
+    p += 4 * (size_t)c->nbins;
+    if (fam) PA_CK(cudaMemcpy(p, c->anc[st.parity], 4 * pop, cudaMemcpyDeviceToHost));
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = kVersion;
+    h.header_bytes = sizeof(CkptHeader);
+    h.cfg = c->cfg;
+    h.step = c->step;
+    h.pop = st.pop;
+    h.beta = c->beta;
+    h.lnZ = st.lnZ;
+    PA_CK(cudaMemcpy(&h.last, c->obs + ((c->n_obs - 1) % c->obs_cap), sizeof(pa_obs), cudaMemcpyDeviceToHost));
+    h.payload_bytes = payload.size();
+    uint64_t sum = fnv1a(reinterpret_cast<const unsigned char *>(&h), sizeof(h), 1469598103934665603ull);
+    sum = fnv1a(payload.data(), payload.size(), sum);
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return PA_ERR_INVALID;
+    const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+                    std::fwrite(payload.data(), 1, payload.size(), f) == payload.size() &&
+                    std::fwrite(&sum, sizeof(sum), 1, f) == 1;
+    const bool closed = std::fclose(f) == 0;
+    return ok && closed ? PA_OK : PA_ERR_INVALID;
+}
+
+pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out)
+{
+    if (!out) return PA_ERR_INVALID;
+    *out = nullptr;
+    if (!path) return PA_ERR_INVALID;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return PA_ERR_INVALID;
+    CkptHeader h;
+    std::vector<unsigned char> payload;
+    uint64_t sum = 0;
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kMagic, 8) == 0 &&
+              h.version == kVersion && h.header_bytes == sizeof(CkptHeader) && h.payload_bytes < (1ull << 40);
+    if (ok) {
+        payload.resize(h.payload_bytes);
+        ok = std::fread(payload.data(), 1, payload.size(), f) == payload.size() &&
+             std::fread(&sum, sizeof(sum), 1, f) == 1;
+    }
+    std::fclose(f);
+    if (!ok) return PA_ERR_INVALID;
+    uint64_t check = fnv1a(reinterpret_cast<const unsigned char *>(&h), sizeof(h), 1469598103934665603ull);
+    check = fnv1a(payload.data(), payload.size(), check);
+    if (check != sum) return PA_ERR_INVALID;
+    const size_t N = (size_t)h.cfg.L * h.cfg.L, pop = (size_t)h.pop;
+    const bool fam = h.cfg.track_families != 0;
+    const size_t nbins = 2 * N + 1;
+    if (h.pop < 1 || h.pop > h.cfg.R_cap || h.step < 0 ||
+        payload.size() != pop * N + 4 * (2 * pop + nbins + (fam ? pop : 0)))
+        return PA_ERR_INVALID;
+    pa_ctx *c = nullptr;
+    pa_status s = ctx_create(h.cfg, cuda_stream, &c);
+    if (s) return s;
+    auto fail = [&](pa_status e) {
+        release(c);
+        delete c;
+        return e;
+    };
+    const unsigned char *p = payload.data();
+    cudaError_t e = cudaMemcpy(c->spins[0], p, pop * N, cudaMemcpyHostToDevice);
+    p += pop * N;
+    if (e == cudaSuccess) e = cudaMemcpy(c->E, p, 4 * pop, cudaMemcpyHostToDevice);
+    p += 4 * pop;
+    if (e == cudaSuccess) e = cudaMemcpy(c->Mt, p, 4 * pop, cudaMemcpyHostToDevice);
+    p += 4 * pop;
+    if (e == cudaSuccess) e = cudaMemcpy(c->hist, p, 4 * nbins, cudaMemcpyHostToDevice);
+    p += 4 * nbins;
+    if (e == cudaSuccess && fam) e = cudaMemcpy(c->anc[0], p, 4 * pop, cudaMemcpyHostToDevice);
+    pa::DevState st{};
+    st.pop = h.pop;
+    st.lnZ = h.lnZ;
+    if (e == cudaSuccess) e = cudaMemcpy(c->st, &st, sizeof(st), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->acc, 0, sizeof(unsigned long long) * 3);
+    if (e == cudaSuccess && c->fam) e = cudaMemset(c->fam, 0, sizeof(int32_t) * h.cfg.R);
+    if (e == cudaSuccess) e = cudaMemcpy(c->obs, &h.last, sizeof(pa_obs), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    c->n_obs = 1;
+    c->step = h.step;
+    c->beta = h.beta;
     *out = c;
     return PA_OK;
 }

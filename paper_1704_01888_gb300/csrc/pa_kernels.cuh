@@ -225,10 +225,14 @@ __device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 
                     const uint32_t hi = p ? (j == S - 1 ? edge : H.v[j < S - 1 ? j + 1 : 0]) : H.v[j];
                     const uint32_t shifted = __funnelshift_r(lo, hi, sh);
                     const uint32_t Wj = W.v[j];
-                    // one word per site: (high, low) of u (q-1) = (proposal offset, acceptance uniform)
+                    // one word per site: (high, low) of the 64-bit product u (q-1) are the
+                    // proposal offset and the acceptance uniform
                     const uint4 ru = philox10_rk(make_uint4(quad0 + j, ctr1, (uint32_t)G.step, slot), rk0, rk1);
-                    const uint32_t m = __umulhi(ru.x, qm1) | (__umulhi(ru.y, qm1) << 8) |
-                                       (__umulhi(ru.z, qm1) << 16) | (__umulhi(ru.w, qm1) << 24);
+                    const uint64_t px = (uint64_t)ru.x * qm1, py = (uint64_t)ru.y * qm1;
+                    const uint64_t pz = (uint64_t)ru.z * qm1, pw = (uint64_t)ru.w * qm1;
+                    const uint32_t m = __byte_perm(__byte_perm((uint32_t)(px >> 32), (uint32_t)(py >> 32), 0x0040),
+                                                   __byte_perm((uint32_t)(pz >> 32), (uint32_t)(pw >> 32), 0x0040),
+                                                   0x5410);
                     // proposals s' = s + 1 + m, reduced mod q bytewise
                     uint32_t P = Wj + m + 0x01010101u;
                     const uint32_t ge = (P + (0x80u - qb) * 0x01010101u) & 0x80808080u;
@@ -242,10 +246,10 @@ __device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 
                     const uint32_t T2 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4442));
                     const uint32_t T3 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4443));
                     uint32_t sel = 0x3210u;
-                    sel += (ru.x * qm1 < T0) ? 0x4u : 0u;
-                    sel += (ru.y * qm1 < T1) ? 0x40u : 0u;
-                    sel += (ru.z * qm1 < T2) ? 0x400u : 0u;
-                    sel += (ru.w * qm1 < T3) ? 0x4000u : 0u;
+                    sel += ((uint32_t)px < T0) ? 0x4u : 0u;
+                    sel += ((uint32_t)py < T1) ? 0x40u : 0u;
+                    sel += ((uint32_t)pz < T2) ? 0x400u : 0u;
+                    sel += ((uint32_t)pw < T3) ? 0x4000u : 0u;
                     NW.v[j] = __byte_perm(Wj, P, sel);
                 }
                 NW.store(own + row + t0);
@@ -256,29 +260,50 @@ __device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 
 
     // measurements: one warp per replica, or the whole block per replica when
     // the block holds fewer replicas than warps
-    const bool cooperative = 2 * nrep <= nwarps;
-    const int mstep = cooperative ? (int)blockDim.x : 32;
-    const int mlane = cooperative ? tid : lane;
-    for (int r = cooperative ? 0 : warp; r < nrep; r += cooperative ? 1 : nwarps) {
-        const uint32_t *rep = sw + r * WPR;
-        int agree = 0;
-        for (int w = mlane; w < WPC; w += mstep) {
-            const int y = w / L8;
-            const int t = w - y * L8;
-            const Neighbours nb = load_neighbours(rep + WPC, L, L8, y, t, y & 1);
-            const uint32_t d = count_differ(rep[w], nb.up, nb.down, nb.same, nb.shifted);
-            agree += 16 - (int)((d * 0x01010101u) >> 24);
+    if (2 * nrep > nwarps) {
+        for (int r = warp; r < nrep; r += nwarps) {
+            const uint32_t *rep = sw + r * WPR;
+            int agree = 0;
+            for (int w = lane; w < WPC; w += 32) {
+                const int y = w / L8;
+                const int t = w - y * L8;
+                const Neighbours nb = load_neighbours(rep + WPC, L, L8, y, t, y & 1);
+                const uint32_t d = count_differ(rep[w], nb.up, nb.down, nb.same, nb.shifted);
+                agree += 16 - (int)((d * 0x01010101u) >> 24);
+            }
+            agree = __reduce_add_sync(0xFFFFFFFFu, agree);
+            int best = 0;
+            for (int s = 0; s < G.q; ++s) {
+                const uint32_t S4 = (uint32_t)s * 0x01010101u;
+                int cnt = 0;
+                for (int w = lane; w < WPR; w += 32) cnt += 4 - __popc(differ_bits(rep[w], S4));
+                cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+                best = max(best, cnt);
+            }
+            if (lane == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
         }
-        agree = cooperative ? block_sum_int(agree) : __reduce_add_sync(0xFFFFFFFFu, agree);
-        int best = 0;
-        for (int s = 0; s < G.q; ++s) {
-            const uint32_t S4 = (uint32_t)s * 0x01010101u;
-            int cnt = 0;
-            for (int w = mlane; w < WPR; w += mstep) cnt += 4 - __popc(differ_bits(rep[w], S4));
-            cnt = cooperative ? block_sum_int(cnt) : __reduce_add_sync(0xFFFFFFFFu, cnt);
-            best = max(best, cnt);
+    } else {
+        for (int r = 0; r < nrep; ++r) {
+            const uint32_t *rep = sw + r * WPR;
+            int agree = 0;
+            for (int w = tid; w < WPC; w += blockDim.x) {
+                const int y = w / L8;
+                const int t = w - y * L8;
+                const Neighbours nb = load_neighbours(rep + WPC, L, L8, y, t, y & 1);
+                const uint32_t d = count_differ(rep[w], nb.up, nb.down, nb.same, nb.shifted);
+                agree += 16 - (int)((d * 0x01010101u) >> 24);
+            }
+            agree = block_sum_int(agree);
+            int best = 0;
+            for (int s = 0; s < G.q; ++s) {
+                const uint32_t S4 = (uint32_t)s * 0x01010101u;
+                int cnt = 0;
+                for (int w = tid; w < WPR; w += blockDim.x) cnt += 4 - __popc(differ_bits(rep[w], S4));
+                cnt = block_sum_int(cnt);
+                best = max(best, cnt);
+            }
+            if (tid == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
         }
-        if (mlane == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
     }
     group_families(G);
     __syncthreads();
@@ -556,6 +581,36 @@ __device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, dou
     }
 }
 
+// A Poisson draw with mean rho for replica j (Sec. 2, Eq. 1): inversion of
+// the cumulative distribution with the mean split into pieces of at most 64;
+// the k-th uniform (U_k + 1/2) / 2^32 is word k & 3 of counter
+// (j, RESAMPLE | (1 + k / 4), step, stream).
+__device__ __forceinline__ int poisson_draw(double rho, int j, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1)
+{
+    int r = 0;
+    double remaining = rho;
+    uint32_t k = 0;
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    while (remaining > 0.0) {
+        const double mu = remaining < 64.0 ? remaining : 64.0;
+        remaining = __dsub_rn(remaining, mu);
+        if ((k & 3) == 0)
+            w = philox10(make_uint4((uint32_t)j, DOM_RESAMPLE | (1u + (k >> 2)), (uint32_t)step, stream_hi), k0, k1);
+        const double u = __ddiv_rn(__dadd_rn((double)pick_word(w, k & 3), 0.5), 4294967296.0);
+        k += 1;
+        double p = exp(-mu);
+        double F = p;
+        int n = 0;
+        while (u > F && n < 1000) {
+            n += 1;
+            p = __ddiv_rn(__dmul_rn(p, mu), (double)n);
+            F = __dadd_rn(F, p);
+        }
+        r += n;
+    }
+    return r;
+}
+
 // One block of 1024 old replicas (chunk): copy numbers and their block scan.
 __device__ __forceinline__ void counts_body(int chunk, const int32_t *E, int twoN, int R_target, int mode, int step,
                                             uint32_t stream_hi, uint32_t k0, uint32_t k1, const double *wtab,
@@ -572,14 +627,20 @@ __device__ __forceinline__ void counts_body(int chunk, const int32_t *E, int two
         const double rho = __ddiv_rn(__dmul_rn((double)R_target, w), st->S);
         const double n = floor(rho);
         const double frac = __dsub_rn(rho, n);
-        int up;
-        if (mode == 1) {
-            up = frac >= 0.5;
+        if (mode == 2) {
+            r = poisson_draw(rho, j, step, stream_hi, k0, k1);
+        } else if (mode == 3) {
+            r = 1;
         } else {
-            const uint4 u = philox10(make_uint4((uint32_t)j >> 2, DOM_RESAMPLE, (uint32_t)step, stream_hi), k0, k1);
-            up = (double)pick_word(u, j & 3) < __dmul_rn(frac, 4294967296.0);
+            int up;
+            if (mode == 1) {
+                up = frac >= 0.5;
+            } else {
+                const uint4 u = philox10(make_uint4((uint32_t)j >> 2, DOM_RESAMPLE, (uint32_t)step, stream_hi), k0, k1);
+                up = (double)pick_word(u, j & 3) < __dmul_rn(frac, 4294967296.0);
+            }
+            r = (int)n + up;
         }
-        r = (int)n + up;
         counts[j] = r;
     }
     int total;

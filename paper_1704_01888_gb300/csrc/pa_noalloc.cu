@@ -110,7 +110,7 @@ extern "C" pa_status pa_resample_noalloc(const int32_t *E, int32_t R_prev, int32
     using namespace pa;
     if (!E || !parent || !lnQ_out || !R_out) return PA_ERR_INVALID;
     if (L < 2 || (L & 1) || R_prev < 1 || R_target < 1 || parent_cap < R_prev) return PA_ERR_INVALID;
-    if (mode != PA_RESAMPLE_NEAREST_INT && mode != PA_RESAMPLE_ROUND) return PA_ERR_INVALID;
+    if (mode < PA_RESAMPLE_NEAREST_INT || mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
     if (!(dbeta == dbeta) || dbeta > 1e300 || dbeta < -1e300) return PA_ERR_INVALID;
     if (L > kMaxL || R_prev > kMaxReplicas || parent_cap > kMaxReplicas) return PA_ERR_TOO_LARGE;
 

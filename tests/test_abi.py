@@ -55,3 +55,18 @@ def test_status_strings_and_validation_without_gpu():
         assert lib.pa_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == pa.PA_ERR_INVALID
         assert not ctx.value
     assert lib.pa_kernel_launch_count() == 0
+
+
+def test_checkpoint_loader_rejects_bad_files_before_device_work(tmp_path):
+    """pa_load validates header, sizes and checksum on the host first."""
+    import paper_1704_01888_gb300 as pa
+
+    _library()
+    lib = pa.load_library()
+    ctx = ctypes.c_void_p()
+    missing = str(tmp_path / "none.ckpt").encode()
+    assert lib.pa_load(missing, None, ctypes.byref(ctx)) == pa.PA_ERR_INVALID
+    junk = tmp_path / "junk.ckpt"
+    junk.write_bytes(b"PAGB300\x01" + bytes(400))
+    assert lib.pa_load(str(junk).encode(), None, ctypes.byref(ctx)) == pa.PA_ERR_INVALID
+    assert not ctx.value

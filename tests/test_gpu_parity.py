@@ -130,6 +130,8 @@ def test_step_api_graph_and_launch_shapes_agree():
     (10, 16, 1, 3, 10, {}),             # one replica
     (6, 16, 500, 0, 8, {}),             # resampling only
     (8, 16, 400, 3, 10, {"mode": pa.RESAMPLE_ROUND}),
+    (8, 16, 400, 3, 10, {"mode": pa.RESAMPLE_POISSON}),  # the paper's Eq. 1
+    (10, 16, 300, 2, 8, {"mode": pa.RESAMPLE_OFF}),
 ])
 def test_edge_cases_bit_exact(q, L, R, theta, K, extra):
     b = np.array([1.5 * i / K for i in range(K + 1)])
@@ -142,12 +144,14 @@ def test_edge_cases_bit_exact(q, L, R, theta, K, extra):
     (3, 40, 200, [0.0, 0.467, 0.933, 1.4]),   # steps large enough that exp overflows off E_ref
     (2, 64, 150, [0.0, 0.7, 1.4]),
     (4, 16, 300, [2.5, 1.2, 0.0]),           # heating with large negative steps
+    (5, 16, 100, [0.0, 1.0, 2.0]),           # Poisson with means far above 64
 ])
 def test_large_temperature_steps(q, L, R, betas):
     b = np.array(betas)
     init = pa.INIT_GROUND if b[0] > 0 else pa.INIT_RANDOM
-    g = _gpu_run(q, L, R, 21, 2, b, init=init)
-    o = _oracle_run(q, L, R, 21, 2, b, init=1 if init == pa.INIT_GROUND else 0)
+    mode = pa.RESAMPLE_POISSON if q == 5 else pa.RESAMPLE_NEAREST_INT
+    g = _gpu_run(q, L, R, 21, 2, b, init=init, mode=mode)
+    o = _oracle_run(q, L, R, 21, 2, b, init=1 if init == pa.INIT_GROUND else 0, mode=mode)
     _compare(g, o)
 
 
@@ -260,3 +264,31 @@ def test_plain_at_scale_launch_shape_reduced_population():
     g = _gpu_run(w.q, w.L, R, w.seed, w.theta, b, launch=(16, 512))
     o = _oracle_run(w.q, w.L, R, w.seed, w.theta, b)
     _compare(g, o)
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    """Save after 6 steps, resume from the file, run 6 more: identical to the
+    uninterrupted 12-step run (counter-based random numbers); a corrupted
+    file is refused."""
+    q, L, R = 10, 16, 800
+    b = np.array([1.2 * i / 12 for i in range(13)])
+    p = pa.PAParams(q=q, L=L, R=R, seed=17, track_families=True)
+    path = str(tmp_path / "pa.ckpt")
+    with pa.Population(p) as pop:
+        pop.run(b[:7], 4)
+        pop.save(path)
+        obs_ref, _ = pop.run(b[6:], 4)
+        spins_ref, anc_ref = pop.spins(), pop.ancestors()
+    with pa.Population.load(path) as pop2:
+        assert pop2.step == 6 and pop2.beta == b[6]
+        obs, _ = pop2.run(b[6:], 4)
+        assert [o["lnZ"] for o in obs] == [o["lnZ"] for o in obs_ref]
+        assert [o["S_f"] for o in obs] == [o["S_f"] for o in obs_ref]
+        assert np.array_equal(pop2.spins(), spins_ref) and np.array_equal(pop2.ancestors(), anc_ref)
+    raw = bytearray(open(path, "rb").read())
+    raw[len(raw) // 2] ^= 0x40
+    bad = str(tmp_path / "bad.ckpt")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(pa.PAError) as e:
+        pa.Population.load(bad)
+    assert e.value.status == pa.PA_ERR_INVALID
