@@ -46,6 +46,24 @@ PA_OBS_BYTES = 104
 DEVSTATE_BYTES = 48
 
 
+def reduce_over_ranks(elapsed, attempts, device):
+    """Whole-job figures of independent per-rank populations: the slowest
+    rank's time (max) and the attempts of all ranks (sum)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    a = torch.tensor([float(attempts)], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(a.item())
+
+
+def rank_seed(base_seed, rank):
+    """Each rank runs its own population: seed + rank."""
+    return base_seed + rank
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,7 +251,7 @@ def run_ours(args):
     W, K = args.warmup, args.steps
     betas = _betas(w, W + K)
     launch = tuple(int(x) for x in args.launch.split(",")) if args.launch else None
-    params = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed + rank, track_families=w.track_families)
+    params = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=rank_seed(w.seed, rank), track_families=w.track_families)
     stream = torch.cuda.current_stream()
 
     pop = pa.Population(params)
@@ -269,13 +287,7 @@ def run_ours(args):
     pop.close()
 
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        a = torch.tensor([attempts], dtype=torch.float64, device="cuda")
-        dist.all_reduce(a, op=dist.ReduceOp.SUM)
-        elapsed_ms, total_attempts = float(t.item()), float(a.item())
+        elapsed_ms, total_attempts = reduce_over_ranks(elapsed_ms, attempts, "cuda")
     else:
         total_attempts = float(attempts)
 
@@ -370,13 +382,7 @@ def _e2e(pa, w, params, betas, W, K, rank, world, launch):
     dt = time.perf_counter() - t0
     pop.close()
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        a = torch.tensor([attempts], dtype=torch.float64, device="cuda")
-        dist.all_reduce(a, op=dist.ReduceOp.SUM)
-        dt, attempts = float(t.item()), float(a.item())
+        dt, attempts = reduce_over_ranks(dt, attempts, "cuda")
     d2h = DEVSTATE_BYTES + DEVSTATE_BYTES + PA_OBS_BYTES + 4 * (2 * w.N + 1)
     return {"value": attempts / (dt * 1e9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
             "note": "population generated on the device from the seed; per step beta and dbeta travel as "

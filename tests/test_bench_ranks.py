@@ -1,0 +1,50 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks reduce their
+timings (max) and attempts (sum) as the GPU ranks do over NCCL, and every
+rank runs its own population seed."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    elapsed = 10.0 + 5.0 * rank
+    attempts = 1000 * (rank + 1)
+    t, a = bench.reduce_over_ranks(elapsed, attempts, "cpu")
+    out.put((rank, t, a, bench.rank_seed(1, rank)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_reduce_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [15.0, 15.0]
+    assert [r[2] for r in res] == [3000.0, 3000.0]
+    assert [r[3] for r in res] == [1, 2]
