@@ -70,7 +70,10 @@ def _args():
     ap.add_argument("--steps", type=int, default=197)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"],
+                    help="c3 runs the batch of 64 runs alone (its first --steps steps)")
+    ap.add_argument("--batch-launch", default="", help="smem_budget,threads for the batched sweep kernel (c3)")
+    ap.add_argument("--no-graph", action="store_true", help="c3 without graph capture")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--R", type=int, default=0, help="override the population size (profiling runs)")
@@ -81,7 +84,7 @@ def _args():
 
 
 def _workload(name, R=0):
-    w = {"c1": wl.C1, "c2": wl.C2, "c5": wl.C5}[name]
+    w = {"c1": wl.C1, "c2": wl.C2, "c5": wl.C5, "c3": wl.C2}[name]
     return wl.scaled(w, R=R, name=f"{w.name}-R{R}") if R else w
 
 
@@ -487,10 +490,44 @@ def _adaptive(pa, R=20000, seeds=4):
     return out
 
 
+def run_batch_only(args):
+    """The batched configuration on its own: the first --steps temperature
+    steps of all 64 runs, one JSON line (PA steps/s and attempts/ns)."""
+    import torch
+
+    import paper_1704_01888_gb300 as pa
+    from paper_1704_01888_gb300 import build as pabuild
+
+    torch.cuda.set_device(0)
+    pabuild.build()
+    ws = wl.batched_runs()
+    K = max(1, min(args.steps, 150))
+    runs = [(pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed, stream=w.stream), w.betas()[:K + 1], w.theta) for w in ws]
+    b = pa.Batch(runs)
+    if args.batch_launch:
+        b.set_launch(*[int(x) for x in args.batch_launch.split(",")])
+    else:
+        b.autotune()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(use_graph=not args.no_graph)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    att = sum(sum(o["R"] for o in b.observables(m)[1:]) * ws[m].N * ws[m].theta for m in range(len(ws)))
+    shape = b.launch_shape()
+    b.close()
+    print(json.dumps({"metric": METRIC, "value": att / dt / 1e9, "unit": UNIT, "n_gpus": 1, "steps": K,
+                      "pa_steps_per_s": len(ws) * K / dt, "config": {"workload": "batch of 64 runs", "launch": shape,
+                                                                     "graph": not args.no_graph}}))
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c3":
+        return run_batch_only(args)
     return run_ours(args)
 
 

@@ -149,6 +149,11 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
     const int L = c->cfg.L;
     const int N = c->N;
     const bool words = (L % 8) == 0;
+    // work items per replica and half sweep: row segments of S words (S = 4,
+    // 2 or 1 as the row length L/8 allows) or single sites
+    const int L8 = L / 8;
+    const int S = !words ? 1 : (L8 % 4 == 0 ? 4 : (L8 % 2 == 0 ? 2 : 1));
+    const long long units = words ? (long long)L * (L8 / S) : N / 2;
     int rpb = rpb_req;
     if (rpb <= 0) {
         int rpb_mem = (int)(65536 / (size_t)N);
@@ -156,11 +161,14 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
         int rpb_fill = c->cfg.R / (4 * c->sms);
         if (rpb_fill < 1) rpb_fill = 1;
         rpb = rpb_mem < rpb_fill ? rpb_mem : rpb_fill;
+        // at least one warp of work items per block
+        const int rpb_warp = (int)((32 + units - 1) / units);
+        if (rpb < rpb_warp) rpb = rpb_warp < rpb_mem ? rpb_warp : rpb_mem;
     }
     if ((size_t)rpb * N > 200 * 1024) return PA_ERR_INVALID;
     int threads = threads_req;
     if (threads <= 0) {
-        const long long work = (long long)rpb * (words ? N / 8 : N / 2);
+        const long long work = (long long)rpb * units;
         threads = (int)((work + 31) / 32 * 32);
         if (threads > 512) threads = 512;
         if (threads < 32) threads = 32;
