@@ -162,6 +162,22 @@ def _sweep_sources() -> bytes:
     return b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("pa_sweep.cu", "pa_kernels.cuh", "pa_internal.cuh"))
 
 
+def _sweep_issue_active():
+    """smsp__issue_active of the sweep kernel from the committed ncu summary
+    (fraction of the SM issue rate), valid only while the sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", "k_sweep_rows_q10-L64-R32768.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    if _sweep_traffic_per_replica() is None:
+        return None
+    for line in text.splitlines():
+        if line.startswith("| smsp__issue_active"):
+            return float(line.split("|")[2].strip().split()[0]) / 100.0
+    return None
+
+
 def _sweep_traffic_per_replica():
     """DRAM bytes per replica per sweep launch from the committed ncu summary,
     valid only while the sweep kernel sources are unchanged."""
@@ -315,6 +331,9 @@ def run_ours(args):
                 "kernel": "k_sweep_rows", "ops_per_attempt": OPS_PER_ATTEMPT,
                 "kernel_ms_avg": sweep_avg_s * 1e3, "kernel_share": sweep_ms / elapsed_ms,
                 "peak_basis": f"{sms} SMs x {LANES_PER_SM_PER_CLK} lanes x {f_max / 1e6:.0f} MHz (max SM clock)"}
+    issue = _sweep_issue_active()
+    if issue is not None:
+        roofline["issue_active_ncu"] = issue
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (sms * LANES_PER_SM_PER_CLK * clocks["sm_mhz"] * 1e6 / 1e12)
 

@@ -222,22 +222,27 @@ def _init_energies(args):
     return np.array([orc.energy(x) for x in s], dtype=np.int32)
 
 
-def test_plain_at_scale_step_one_sampled():
-    w = wl.C2
+@pytest.mark.parametrize("w", [wl.C2, wl.C4, wl.C5], ids=["q10-L64-R1e5", "q8-L128-R2e5", "q20-L256-R1e5"])
+def test_full_size_step_one_sampled(w):
+    """Full population, first temperature step: every initial energy, ln Q and
+    the new size against the oracle, and sampled slots recomputed one by one
+    from their parents' initial states (theta sweeps at beta_1)."""
     b = w.betas()
-    p = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed)
+    p = pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed, track_families=w.track_families)
     rng = np.random.default_rng(2024)
+    n_sample = 24 if w.L <= 64 else 8
     with pa.Population(p) as pop:
         E0 = pop.energies()
         lnq, R1 = pop.resample(b[1] - b[0], 1, sync=True)
         pop.sweep(b[1], w.theta, 1)
         E1 = pop.energies()
         assert E1.size == R1
-        sample = np.unique(np.concatenate([rng.integers(0, R1, 48), [0, R1 - 1]]))
+        sample = np.unique(np.concatenate([rng.integers(0, R1, n_sample), [0, R1 - 1]]))
         spins = {int(s): pop.spins(int(s), 1)[0] for s in sample}
         o1, h1 = pop.observables(with_hist=True)
 
-    chunks = [(w.q, w.L, k, min(6250, w.R - k), w.seed) for k in range(0, w.R, 6250)]
+    per = 6250 if w.L <= 64 else 2000
+    chunks = [(w.q, w.L, k, min(per, w.R - k), w.seed) for k in range(0, w.R, per)]
     with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as poolp:
         E0_ref = np.concatenate(poolp.map(_init_energies, chunks))
     assert np.array_equal(E0, E0_ref)
@@ -253,6 +258,8 @@ def test_plain_at_scale_step_one_sampled():
     # properties that hold at any size
     assert h1.sum() == R1 and np.array_equal(np.bincount(E1 + 2 * w.N, minlength=2 * w.N + 1), h1)
     assert o1["sumE"] == int(E1.astype(np.int64).sum())
+    if w.track_families:
+        assert o1["n_families"] == int(np.count_nonzero(r))
 
 
 def test_plain_at_scale_launch_shape_reduced_population():
