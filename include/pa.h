@@ -52,8 +52,9 @@ typedef enum {
     PA_ERR_TIMEOUT = 4,  /* a bounded device wait gave up                      */
     PA_ERR_STATE = 5,    /* calls in the wrong order, or a failed context      */
     PA_ERR_NOMEM = 6,    /* device or host allocation failed                   */
-    PA_ERR_TOO_LARGE = 7 /* a size exceeds the fixed working memory of
-                            pa_resample_noalloc                              */
+    PA_ERR_TOO_LARGE = 7 /* a lattice larger than one block's shared memory
+                            holds (L*L > 204800), or a size beyond the fixed
+                            working memory of pa_resample_noalloc            */
 } pa_status;
 
 /* Copy-number rule for the resampling step (Sec. 2, step 2).  The paper draws
@@ -109,7 +110,8 @@ typedef struct pa_ctx pa_ctx;
  * occupations, energy histogram and step-0 estimators.
  * Errors: PA_ERR_INVALID for q outside 2..128, odd or out-of-range L, R < 1,
  * R_cap < R or R_cap >= 2^24, beta0 < 0, an unknown mode, or a stream outside
- * 0..255; PA_ERR_NOMEM or
+ * 0..255; PA_ERR_TOO_LARGE for L*L > 204800 (L <= 452: a sweep block keeps
+ * whole lattices in shared memory); PA_ERR_NOMEM or
  * PA_ERR_CUDA if allocation or a launch fails (nothing is leaked; *out = NULL). */
 pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 
@@ -259,6 +261,7 @@ typedef struct pa_batch pa_batch;
  * the initial populations with their step-0 estimators (synchronises).
  * Errors: PA_ERR_INVALID for M outside 1..1024, any invalid run (as pa_init),
  * differing seeds, K < 1, theta < 0 or a non-finite or negative beta;
+ * PA_ERR_TOO_LARGE for a run with L*L > 204800 (as pa_init);
  * PA_ERR_NOMEM / PA_ERR_CUDA on allocation or launch failures. */
 pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream, pa_batch **out);
 

@@ -389,6 +389,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         if (g.resample_mode < PA_RESAMPLE_NEAREST_INT || g.resample_mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
         if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
         if (!(g.beta0 >= 0.0) || runs[m].betas[0] != g.beta0) return PA_ERR_INVALID;
+        if ((long long)g.L * g.L > pa::kMaxLatticeBytes) return PA_ERR_TOO_LARGE;
         for (int i = 0; i <= runs[m].K; ++i)
             if (!std::isfinite(runs[m].betas[i]) || !(runs[m].betas[i] >= 0.0)) return PA_ERR_INVALID;
     }

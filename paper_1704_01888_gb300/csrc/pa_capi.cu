@@ -165,7 +165,7 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
         const int rpb_warp = (int)((32 + units - 1) / units);
         if (rpb < rpb_warp) rpb = rpb_warp < rpb_mem ? rpb_warp : rpb_mem;
     }
-    if ((size_t)rpb * N > 200 * 1024) return PA_ERR_INVALID;
+    if ((size_t)rpb * N > (size_t)pa::kMaxLatticeBytes) return rpb == 1 ? PA_ERR_TOO_LARGE : PA_ERR_INVALID;
     int threads = threads_req;
     if (threads <= 0) {
         const long long work = (long long)rpb * units;
@@ -280,7 +280,7 @@ const char *pa_status_str(pa_status s)
     case PA_ERR_TIMEOUT: return "device wait timed out";
     case PA_ERR_STATE: return "call out of order or context failed";
     case PA_ERR_NOMEM: return "out of memory";
-    case PA_ERR_TOO_LARGE: return "size exceeds the fixed working memory of the no-allocation entry point";
+    case PA_ERR_TOO_LARGE: return "size exceeds shared memory (lattice) or fixed working memory (no-allocation call)";
     }
     return "unknown status";
 }
@@ -303,6 +303,7 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
     if (g.resample_mode < PA_RESAMPLE_NEAREST_INT || g.resample_mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
     if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
     if (!(g.beta0 >= 0.0) || !std::isfinite(g.beta0)) return PA_ERR_INVALID;
+    if ((long long)g.L * g.L > pa::kMaxLatticeBytes) return PA_ERR_TOO_LARGE;
     long long R_cap = g.R_cap > 0 ? g.R_cap : (long long)g.R + g.R / 4 + 1024;
     if (R_cap < g.R || R_cap >= (1LL << 24)) return PA_ERR_INVALID;
 

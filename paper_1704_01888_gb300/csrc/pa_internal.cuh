@@ -23,6 +23,10 @@ constexpr uint32_t DOM_INIT = 0x40000000u;
 constexpr uint32_t DOM_RESAMPLE = 0x80000000u;
 constexpr uint32_t DOM_GROUND = 0xC0000000u;
 
+// Largest lattice (bytes, one per site) a sweep block keeps in shared memory,
+// leaving room for the threshold table and block reductions within 227 KB.
+constexpr int kMaxLatticeBytes = 200 * 1024;
+
 // Device-resident run state.  Kernels read and update it so that a whole
 // schedule can be enqueued (or captured in a graph) with no host round trip.
 struct DevState {
