@@ -65,9 +65,15 @@ def lib():
         L.orc_energy.restype = i64
         L.orc_max_count.argtypes = [ctypes.c_int, ctypes.c_int, P]
         L.orc_max_count.restype = i64
+        L.orc_state_bits.argtypes = [ctypes.c_int]
+        L.orc_state_bits.restype = ctypes.c_int
         L.orc_thresholds.argtypes = [f64, P]
-        L.orc_metropolis_decide.argtypes = [ctypes.c_int, ctypes.c_int, P, u32, P]
+        L.orc_propose.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32]
+        L.orc_propose.restype = ctypes.c_int
+        L.orc_metropolis_decide.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, u32, u32, P]
         L.orc_metropolis_decide.restype = ctypes.c_int
+        L.orc_below_value.argtypes = [u32, u64]
+        L.orc_below_value.restype = ctypes.c_int
         L.orc_sweep_replica.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, u32, u32, u64, u32]
         L.orc_init_random.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
         L.orc_init_ground.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
@@ -116,16 +122,30 @@ def max_count(q: int, spins: np.ndarray) -> int:
     return int(lib().orc_max_count(q, s.shape[-1], _p(s)))
 
 
+def state_bits(q: int) -> int:
+    return int(lib().orc_state_bits(q))
+
+
 def thresholds(beta: float) -> np.ndarray:
-    t = np.zeros(9, dtype=np.uint32)
+    """T[d] = floor(exp(-beta d) 2^32) for d = 1..4 (T[0] = 2^32)."""
+    t = np.zeros(5, dtype=np.uint64)
     lib().orc_thresholds(float(beta), _p(t))
     return t
 
 
-def metropolis_decide(q, cur, nb, u, thr) -> int:
+def propose(q: int, cur: int, sigma: int, u: int) -> int:
+    return int(lib().orc_propose(q, cur, sigma, int(u)))
+
+
+def below_value(v: int, T: int) -> bool:
+    """The sweep's most-significant-bit-first comparison v < T."""
+    return bool(lib().orc_below_value(int(v), int(T)))
+
+
+def metropolis_decide(q, cur, nb, sigma, u, v, T) -> int:
     n = np.ascontiguousarray(nb, dtype=np.int32)
-    t = np.ascontiguousarray(thr, dtype=np.uint32)
-    return int(lib().orc_metropolis_decide(q, cur, _p(n), int(u), _p(t)))
+    t = np.ascontiguousarray(T, dtype=np.uint64)
+    return int(lib().orc_metropolis_decide(q, cur, _p(n), int(sigma), int(u), int(v), _p(t)))
 
 
 def sweep_replica(q: int, spins: np.ndarray, beta: float, theta: int, step: int, slot: int, seed: int,

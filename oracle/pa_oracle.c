@@ -121,45 +121,99 @@ ORC_API int64_t orc_max_count(int q, int L, const uint8_t *s)
 
 /* ------------------------------------------------------------------------- */
 /* Metropolis single-spin-flip update (Sec. 2 step 3, Sec. 3).                */
-/* reading: one 32-bit random word u per attempt.  With k = q - 1, the 64-bit */
-/* product u k splits into a high word, the proposal offset m = floor(u k /   */
-/* 2^32), uniform over 0..q-2, and a low word v = u k mod 2^32, the position  */
-/* of u inside its proposal bin, which serves as the acceptance uniform:      */
-/*   s' = (s + 1 + m) mod q,  accepted iff v < T[dE],                         */
-/* where dE = E(s') - E(s) is an integer in [-4, 4] and                       */
-/* T[d] = min(2^32 - 1, floor(min(1, exp(-beta d)) 2^32)).  Given m, v runs   */
-/* over every (q-1)-th value of [0, 2^32), so the acceptance probability is   */
-/* T / 2^32 to within (q-1) / 2^32.                                           */
+/*                                                                             */
+/* reading (proposal): B = ceil(log2 q) bits hold a state.  An attempt draws  */
+/* a direction bit sigma and a (B-1)-bit number u; with d = 1 + u (so         */
+/* 1 <= d <= 2^(B-1) <= q - 1) the proposed state is s' = (s + d) mod q for   */
+/* sigma = 0 and (s - d) mod q for sigma = 1.  s' never equals s, every other */
+/* state is reachable, and the move s -> s' has the same probability as the   */
+/* move s' -> s (+d under one direction is -d under the other), so the        */
+/* Metropolis rule below satisfies detailed balance exactly.  For q - 1 a     */
+/* power of two the proposal is uniform over the q - 1 other states.          */
+/*                                                                             */
+/* reading (acceptance): with dE = E(s') - E(s), an integer in [-4, 4], the   */
+/* move is accepted if dE <= 0 and otherwise iff v < T[dE], v a uniform       */
+/* 32-bit number and T[d] = floor(exp(-beta d) 2^32).                          */
 /* ------------------------------------------------------------------------- */
-ORC_API void orc_thresholds(double beta, uint32_t thr[9])
+
+/* Bits per state: the smallest B with 2^B >= q. */
+ORC_API int orc_state_bits(int q)
 {
-    for (int d = -4; d <= 4; ++d) {
-        double a = exp(-beta * (double)d);
-        if (a >= 1.0)
-            thr[d + 4] = 0xFFFFFFFFu;
-        else
-            thr[d + 4] = (uint32_t)(a * 4294967296.0);
-    }
+    int B = 0;
+    while ((1 << B) < q) ++B;
+    return B;
 }
 
-/* One attempt on a site in state `cur` whose four neighbours are nb[0..3],
- * driven by the random word u.  Returns the state after the attempt. */
-ORC_API int orc_metropolis_decide(int q, int cur, const int nb[4], uint32_t u, const uint32_t thr[9])
+/* T[d] = floor(exp(-beta d) 2^32) for d = 1..4 (T[0] = 2^32, unused). */
+ORC_API void orc_thresholds(double beta, uint64_t T[5])
 {
-    uint64_t prod = (uint64_t)u * (uint64_t)(q - 1);
-    int m = (int)(prod >> 32);
-    uint32_t v = (uint32_t)prod;
-    int prop = (cur + 1 + m) % q;
+    T[0] = 4294967296ull;
+    for (int d = 1; d <= 4; ++d) T[d] = (uint64_t)(exp(-beta * (double)d) * 4294967296.0);
+}
+
+/* The proposal: s' = (s + d) mod q for sigma = 0, (s - d) mod q for sigma = 1,
+ * d = 1 + u. */
+ORC_API int orc_propose(int q, int cur, int sigma, uint32_t u)
+{
+    int d = 1 + (int)u;
+    return sigma ? ((cur - d) % q + q) % q : (cur + d) % q;
+}
+
+/* E = -(number of satisfied bonds): moving a site from `cur` to `prop` with
+ * neighbours nb[0..3] changes E by n(cur) - n(prop), n(a) the number of
+ * neighbours in state a. */
+ORC_API int orc_delta_energy(int cur, int prop, const int nb[4])
+{
     int n_cur = 0, n_prop = 0;
     for (int k = 0; k < 4; ++k) {
         if (nb[k] == cur) n_cur += 1;
         if (nb[k] == prop) n_prop += 1;
     }
-    /* E = -(number of satisfied bonds): moving cur -> prop changes E by
-     * n_cur - n_prop. */
-    int dE = n_cur - n_prop;
-    if (v < thr[dE + 4]) return prop;
-    return cur;
+    return n_cur - n_prop;
+}
+
+/* v < T for a 32-bit v whose bits are supplied most significant first by
+ * bit(ctx, j), j = 0..31 (bit j has weight 2^(31-j)): the first bit in which v
+ * and T differ decides, and v = T is not below.  Reading bits only until that
+ * point is how an unsigned comparison works; it lets the sweep draw no more
+ * random words than the decision needs. */
+typedef int (*orc_bit_fn)(void *ctx, int j);
+
+static int orc_below(orc_bit_fn bit, void *ctx, uint64_t T)
+{
+    if (T >= 4294967296ull) return 1;
+    for (int j = 0; j < 32; ++j) {
+        int vb = bit(ctx, j);
+        int tb = (int)(T >> (31 - j)) & 1;
+        if (vb != tb) return vb < tb;
+    }
+    return 0;
+}
+
+static int orc_value_bit(void *ctx, int j) { return (int)(*(const uint32_t *)ctx >> (31 - j)) & 1; }
+
+/* orc_below on a given value (exported so that the tests can compare it with
+ * the integer comparison). */
+ORC_API int orc_below_value(uint32_t v, uint64_t T)
+{
+    return orc_below(orc_value_bit, &v, T);
+}
+
+/* The Metropolis acceptance: always for dE <= 0, else iff v < T[dE]. */
+ORC_API int orc_accept(int dE, uint32_t v, const uint64_t T[5])
+{
+    if (dE <= 0) return 1;
+    return (uint64_t)v < T[dE];
+}
+
+/* One attempt on a site in state `cur` whose four neighbours are nb[0..3],
+ * with direction bit sigma, offset bits u and acceptance number v.  Returns
+ * the state after the attempt. */
+ORC_API int orc_metropolis_decide(int q, int cur, const int nb[4], int sigma, uint32_t u, uint32_t v,
+                                  const uint64_t T[5])
+{
+    int prop = orc_propose(q, cur, sigma, u);
+    return orc_accept(orc_delta_energy(cur, prop, nb), v, T) ? prop : cur;
 }
 
 static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
@@ -170,27 +224,90 @@ static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
     nb[3] = s[((y + 1) % L) * L + x];
 }
 
-/* theta checkerboard sweeps of one replica at the thresholds `thr`.
+/* reading (random numbers of a sweep): the sites of colour c ((x + y) mod 2)
+ * in row y, with column index m = x >> 1, are grouped 32 columns to a "site
+ * word": word t = m >> 5 of the row, bit b = m & 31, word index
+ * w = y ceil(L / 64) + t.  In sweep k, colour c, temperature step `step`, the
+ * word draws a stream Z_0, Z_1, ... of 32-bit numbers, Z_{4n+i} being word i
+ * of the Philox call with counter (w, SWEEP | ((2k + c) << 8) | n, step,
+ * slot | stream << 24), and the site at bit b takes bit b of each:
+ *   sigma = bit of Z_0,  u = sum_{i=1}^{B-1} bit(Z_i) 2^(i-1),
+ *   v = sum_{j=0}^{31} bit(Z_{P+j}) 2^(31-j),  P = B rounded up to a power of 2.
+ * The stream of one word is drawn once per half sweep (lazily, on first use). */
+struct orc_word_stream {
+    uint64_t seed;
+    uint32_t w, c1base, step, c3;
+    int have;             /* number of Philox calls drawn so far */
+    uint32_t Z[48];
+};
+
+static uint32_t orc_stream_word(struct orc_word_stream *st, int i)
+{
+    while (st->have <= i / 4) {
+        orc_draw(st->seed, st->w, st->c1base | (uint32_t)st->have, st->step, st->c3, st->Z + 4 * st->have);
+        st->have += 1;
+    }
+    return st->Z[i];
+}
+
+/* Bit j (weight 2^(31-j)) of the acceptance number v of the site at bit b. */
+struct orc_v_source {
+    struct orc_word_stream *st;
+    int first, b;  /* v's bit j is bit b of Z_{first + j} */
+};
+
+static int orc_v_bit(void *ctx, int j)
+{
+    struct orc_v_source *src = (struct orc_v_source *)ctx;
+    return (int)(orc_stream_word(src->st, src->first + j) >> src->b) & 1;
+}
+
+/* theta checkerboard sweeps of one replica at the thresholds T.
  * reading: one sweep updates the colour-0 sites ((x+y) even) and then the
- * colour-1 sites.  With L even no two sites of one colour are neighbours, so
- * this in-place row-major order equals a simultaneous update of each colour.
- * Random words: site (x, y) has sublattice index h = (y L + x) >> 1; the
- * Philox call with counter (h >> 2, SWEEP | (2k + colour), step, slot) serves
- * the four sites with the same h >> 2 of that colour, word h & 3 going to h. */
-ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint32_t thr[9], int theta,
+ * colour-1 sites, each colour row by row and, within a row, by increasing x.
+ * With L even no two sites of one colour are neighbours, so this in-place
+ * order equals a simultaneous update of each colour.  (For odd L the order is
+ * still a product of single-site Metropolis steps, each of which keeps the
+ * Boltzmann distribution stationary.) */
+ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], int theta,
                                uint32_t step, uint32_t slot, uint64_t seed, uint32_t stream)
 {
+    int B = orc_state_bits(q);
+    int P = 1;
+    while (P < B) P *= 2;
+    int words_per_row = (L + 63) / 64;
     for (int k = 0; k < theta; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
             for (int y = 0; y < L; ++y) {
-                for (int x = 0; x < L; ++x) {
-                    if (((x + y) & 1) != colour) continue;
-                    uint32_t h = (uint32_t)(y * L + x) >> 1;
-                    uint32_t w[4];
-                    orc_draw(seed, h >> 2, ORC_DOM_SWEEP | (uint32_t)(2 * k + colour), step, slot | (stream << 24), w);
-                    int nb[4];
-                    orc_neighbours(L, s, x, y, nb);
-                    s[y * L + x] = (uint8_t)orc_metropolis_decide(q, s[y * L + x], nb, w[h & 3], thr);
+                int x0 = (colour + y) & 1;  /* first column of this colour in row y */
+                for (int t = 0; t < words_per_row; ++t) {
+                    struct orc_word_stream st;
+                    st.seed = seed;
+                    st.w = (uint32_t)(y * words_per_row + t);
+                    st.c1base = ORC_DOM_SWEEP | ((uint32_t)(2 * k + colour) << 8);
+                    st.step = step;
+                    st.c3 = slot | (stream << 24);
+                    st.have = 0;
+                    for (int b = 0; b < 32; ++b) {
+                        int x = 2 * (32 * t + b) + x0;
+                        if (x >= L) break;
+                        int sigma = (int)(orc_stream_word(&st, 0) >> b) & 1;
+                        uint32_t u = 0;
+                        for (int i = 1; i < B; ++i) u |= ((orc_stream_word(&st, i) >> b) & 1u) << (i - 1);
+                        int nb[4];
+                        orc_neighbours(L, s, x, y, nb);
+                        int cur = s[y * L + x];
+                        int prop = orc_propose(q, cur, sigma, u);
+                        int dE = orc_delta_energy(cur, prop, nb);
+                        /* the Metropolis acceptance of orc_accept, with v read
+                         * bit by bit and only when the move raises the energy */
+                        int accept = 1;
+                        if (dE > 0) {
+                            struct orc_v_source src = {&st, P, b};
+                            accept = orc_below(orc_v_bit, &src, T[dE]);
+                        }
+                        if (accept) s[y * L + x] = (uint8_t)prop;
+                    }
                 }
             }
         }
@@ -452,7 +569,7 @@ ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, u
         int32_t *ta = anc; anc = anc2; anc2 = ta;
         Rc = Rn;
 
-        uint32_t thr[9];
+        uint64_t thr[5];
         orc_thresholds(betas[i], thr);
         for (int64_t t = 0; t < Rc; ++t) {
             orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed, stream);
@@ -510,30 +627,23 @@ ORC_API int orc_density_of_states(int q, int L, uint64_t *g)
 
 /* Exact transition matrix of one Metropolis attempt at `site` (= y L + x) of an
  * L x L lattice, over all q^N configurations (index = sum_i s_i q^i).  The
- * probabilities are read off orc_metropolis_decide itself: the random word u
- * is split into the proposal bins {u : floor(u (q-1) / 2^32) = m}, located by
- * bisection, and inside each bin (where acceptance holds for a prefix of u)
- * the first rejecting u is located by bisection, so a mistake in the update
- * rule shows up in the matrix.  P is (q^N)^2 row-major, P[a][b] = Prob(a -> b).
- * Returns -1 if q^N > 4096. */
-static uint64_t orc_first_u_in_bin(int q, int m)
-{
-    uint64_t lo = 0, hi = 4294967296ull;
-    while (lo < hi) {
-        uint64_t mid = (lo + hi) / 2;
-        if (((uint64_t)mid * (uint64_t)(q - 1) >> 32) >= (uint64_t)m) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-}
-
+ * probabilities are read off orc_metropolis_decide itself: each of the 2^B
+ * equally likely (sigma, u) pairs is tried, and for each the acceptance
+ * probability is the length of the set of v in [0, 2^32) that move the site,
+ * found by bisection for its first rejecting v (the accepting v form a prefix),
+ * so a mistake in the update rule shows up in the matrix.  P is (q^N)^2
+ * row-major, P[a][b] = Prob(a -> b).  Returns -1 if q^N > 4096. */
 ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
 {
     int N = L * L;
     int64_t n = 1;
     for (int i = 0; i < N; ++i) n *= q;
     if (n > 4096) return -1;
-    uint32_t thr[9];
+    uint64_t thr[5];
     orc_thresholds(beta, thr);
+    int B = orc_state_bits(q);
+    int n_u = 1 << (B > 0 ? B - 1 : 0);
+    double w = 1.0 / (2.0 * (double)n_u);
     memset(P, 0, sizeof(double) * (size_t)(n * n));
     int x = site % L, y = site / L;
     int64_t place = 1;
@@ -545,22 +655,24 @@ ORC_API int orc_site_matrix(int q, int L, int site, double beta, double *P)
         int nb[4];
         orc_neighbours(L, s, x, y, nb);
         int cur = s[site];
-        for (int m = 0; m < q - 1; ++m) {
-            uint64_t first = orc_first_u_in_bin(q, m);
-            uint64_t end = orc_first_u_in_bin(q, m + 1);
-            /* smallest u in [first, end) whose attempt is rejected */
-            uint64_t lo = first, hi = end;
-            while (lo < hi) {
-                uint64_t mid = (lo + hi) / 2;
-                if (orc_metropolis_decide(q, cur, nb, (uint32_t)mid, thr) == cur) hi = mid; else lo = mid + 1;
+        for (int sigma = 0; sigma < 2; ++sigma) {
+            for (int u = 0; u < n_u; ++u) {
+                /* smallest v in [0, 2^32] whose attempt leaves the site unchanged */
+                uint64_t lo = 0, hi = 4294967296ull;
+                while (lo < hi) {
+                    uint64_t mid = (lo + hi) / 2;
+                    if (orc_metropolis_decide(q, cur, nb, sigma, (uint32_t)u, (uint32_t)mid, thr) == cur)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                double p_acc = (double)lo / 4294967296.0;
+                int prop = cur;
+                if (lo > 0) prop = orc_metropolis_decide(q, cur, nb, sigma, (uint32_t)u, 0u, thr);
+                int64_t b = a + (int64_t)(prop - cur) * place;
+                P[a * n + b] += w * p_acc;
+                P[a * n + a] += w * (1.0 - p_acc);
             }
-            double p_acc = (double)(lo - first) / 4294967296.0;
-            double p_rej = (double)(end - lo) / 4294967296.0;
-            int prop = cur;
-            if (lo > first) prop = orc_metropolis_decide(q, cur, nb, (uint32_t)first, thr);
-            int64_t b = a + (int64_t)(prop - cur) * place;
-            P[a * n + b] += p_acc;
-            P[a * n + a] += p_rej;
         }
     }
     return 0;
@@ -711,7 +823,7 @@ ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t se
         for (int64_t t = 0; t < Rn; ++t) memcpy(nxt + t * N, cur + (int64_t)parent[t] * N, (size_t)N);
         uint8_t *tmp = cur; cur = nxt; nxt = tmp;
         Rc = Rn;
-        uint32_t thr[9];
+        uint64_t thr[5];
         orc_thresholds(nb, thr);
         for (int64_t t = 0; t < Rc; ++t) {
             orc_sweep_replica(q, L, cur + t * N, thr, theta, (uint32_t)i, (uint32_t)t, seed, stream);

@@ -163,7 +163,7 @@ def test_energy_and_max_count_small_cases():
 # --------------------------------------------------------------------------
 # Metropolis update: exact detailed balance (Sec. 2 step 3)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("q", [2, 3, 4])
+@pytest.mark.parametrize("q", [2, 3, 4, 6])
 @pytest.mark.parametrize("beta", [0.4, 1.3])
 def test_site_kernels_satisfy_detailed_balance(q, beta):
     L = 2
@@ -181,8 +181,8 @@ def test_site_kernels_satisfy_detailed_balance(q, beta):
         P = oracle.site_matrix(q, L, site, beta)
         assert np.allclose(P.sum(axis=1), 1.0, atol=1e-14)
         flow = pi[:, None] * P
-        # the 32-bit quantisation of proposals, thresholds and acceptance words
-        # bounds the asymmetry by about (q - 1) 2^-32 relative to pi
+        # the proposal is exactly symmetric; the 32-bit thresholds bound the
+        # remaining asymmetry by about 2^-32 relative to pi
         assert np.max(np.abs(flow - flow.T)) <= 1e-8 * pi.max()
         sweep = sweep @ P
     assert np.max(np.abs(pi @ sweep - pi)) < 1e-8
@@ -193,48 +193,60 @@ def test_site_kernels_satisfy_detailed_balance(q, beta):
 def test_thresholds_are_quantised_boltzmann_factors():
     for beta in (0.0, 0.37, 1.426, 3.0):
         t = oracle.thresholds(beta)
-        for d in range(-4, 5):
-            if d <= 0:
-                assert t[d + 4] == 0xFFFFFFFF
-            else:
-                exact = math.exp(-beta * d) * 2**32
-                assert t[d + 4] == min(2**32 - 1, math.floor(exact))
+        assert int(t[0]) == 2**32
+        for d in range(1, 5):
+            exact = math.exp(-beta * d) * 2**32
+            assert int(t[d]) == math.floor(exact)
 
 
-def test_proposal_never_repeats_current_state():
-    """At beta = 0 every move is accepted (T = 2^32 - 1 > v except for the
-    single low word 2^32 - 1): the proposal is always another state, and the
-    q - 1 others are reached from bins of equal width."""
-    thr = oracle.thresholds(0.0)
-    rng = np.random.default_rng(3)
-    for q in (2, 3, 10, 20):
-        seen = np.zeros(q, int)
-        for _ in range(400):
-            cur = int(rng.integers(q))
-            u = int(rng.integers(2**32))
-            new = oracle.metropolis_decide(q, cur, [cur, cur, cur, cur], u, thr)
-            assert new != cur and 0 <= new < q
-            seen[(new - cur - 1) % q] += 1
-        assert seen[: q - 1].min() > 0 and seen[q - 1] == 0
+@pytest.mark.parametrize("q", [2, 3, 4, 5, 6, 9, 10, 17, 20, 33, 128])
+def test_proposal_is_symmetric_and_reaches_every_other_state(q):
+    """Over the 2^B equally likely (sigma, u), the offset s' - s mod q never
+    vanishes, covers 1..q-1, and has the same probability as its inverse
+    (detailed balance needs no more); for q - 1 a power of two it is uniform."""
+    B = oracle.state_bits(q)
+    assert 2 ** (B - 1) < q <= 2**B
+    for cur in sorted({0, q // 2, q - 1}):
+        count = np.zeros(q, int)
+        for sigma in (0, 1):
+            for u in range(2 ** (B - 1) if B > 0 else 1):
+                new = oracle.propose(q, cur, sigma, u)
+                assert 0 <= new < q and new != cur
+                count[(new - cur) % q] += 1
+        assert count[0] == 0 and count[1:].min() > 0
+        assert all(count[k] == count[q - k] for k in range(1, q))
+        if (q - 1) & (q - 2) == 0:
+            assert count[1:].min() == count[1:].max()
 
 
-def test_acceptance_uses_position_inside_proposal_bin():
-    """Inside one proposal bin, acceptance holds exactly for the words whose
-    low product word is below the threshold: a prefix of the bin of length
-    about T / (q - 1)."""
+def test_bitwise_comparison_equals_integer_comparison():
+    rng = np.random.default_rng(11)
+    vs = [0, 1, 2**31 - 1, 2**31, 2**32 - 2, 2**32 - 1] + [int(x) for x in rng.integers(0, 2**32, 300)]
+    Ts = [0, 1, 2**31, 2**32 - 1, 2**32] + [int(x) for x in rng.integers(0, 2**32, 60)]
+    for v in vs:
+        for T in Ts + [v, v + 1, max(v - 1, 0)]:
+            assert oracle.below_value(v, T) == (v < T), (v, T)
+
+
+def test_acceptance_is_a_threshold_on_v():
+    """Moves that do not raise the energy are always taken; a move raising it
+    by dE is taken exactly for v < T[dE] (a prefix of the 2^32 values)."""
     q = 10
-    beta = 1.3
-    thr = oracle.thresholds(beta)
-    nb = [0, 0, 0, 0]  # a site in state 0 with all neighbours 0: any move costs dE = 4
-    for m in (0, 4, 8):
-        first = -(-(m << 32) // (q - 1))
-        end = -(-((m + 1) << 32) // (q - 1))
-        acc = [oracle.metropolis_decide(q, 0, nb, u, thr) != 0 for u in (first, first + 1, end - 1)]
-        assert acc == [True, True, False]
-        # the first rejected word: v = u (q - 1) mod 2^32 reaches T[4]
-        k = -(-(int(thr[8]) + (m << 32)) // (q - 1))
-        assert oracle.metropolis_decide(q, 0, nb, k - 1, thr) != 0
-        assert oracle.metropolis_decide(q, 0, nb, k, thr) == 0
+    for beta in (0.3, 1.3):
+        T = oracle.thresholds(beta)
+        # a site in state 0: neighbours with k zeros and 4 - k in state 5
+        for k in range(5):
+            nb = [0] * k + [5] * (4 - k)
+            for sigma, u in ((0, 4), (1, 3), (0, 0)):
+                prop = oracle.propose(q, 0, sigma, u)
+                dE = k - sum(1 for x in nb if x == prop)
+                if dE <= 0:
+                    assert oracle.metropolis_decide(q, 0, nb, sigma, u, 2**32 - 1, T) == prop
+                    continue
+                t = int(T[dE])
+                assert oracle.metropolis_decide(q, 0, nb, sigma, u, t - 1, T) == prop
+                assert oracle.metropolis_decide(q, 0, nb, sigma, u, t, T) == 0
+                assert oracle.metropolis_decide(q, 0, nb, sigma, u, 0, T) == prop
 
 
 # --------------------------------------------------------------------------
