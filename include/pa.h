@@ -52,8 +52,8 @@ typedef enum {
     PA_ERR_TIMEOUT = 4,  /* a bounded device wait gave up                      */
     PA_ERR_STATE = 5,    /* calls in the wrong order, or a failed context      */
     PA_ERR_NOMEM = 6,    /* device or host allocation failed                   */
-    PA_ERR_TOO_LARGE = 7 /* a lattice larger than one block's shared memory
-                            holds (L*L > 204800), or a size beyond the fixed
+    PA_ERR_TOO_LARGE = 7 /* a replica larger than one block's shared memory
+                            holds (see pa_init), or a size beyond the fixed
                             working memory of pa_resample_noalloc            */
 } pa_status;
 
@@ -110,8 +110,10 @@ typedef struct pa_ctx pa_ctx;
  * occupations, energy histogram and step-0 estimators.
  * Errors: PA_ERR_INVALID for q outside 2..128, odd or out-of-range L, R < 1,
  * R_cap < R or R_cap >= 2^24, beta0 < 0, an unknown mode, or a stream outside
- * 0..255; PA_ERR_TOO_LARGE for L*L > 204800 (L <= 452: a sweep block keeps
- * whole lattices in shared memory); PA_ERR_NOMEM or
+ * 0..255; PA_ERR_TOO_LARGE when a replica's bit planes exceed 204800 bytes
+ * (a sweep block keeps whole lattices in shared memory; a replica takes
+ * 2 L ceil(L/64) P 4 bytes, P = ceil(log2 q) rounded up to 1, 2, 4 or 8, so
+ * L <= 640 for q <= 16 and L <= 448 for q <= 128); PA_ERR_NOMEM or
  * PA_ERR_CUDA if allocation or a launch fails (nothing is leaked; *out = NULL). */
 pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 
@@ -134,12 +136,14 @@ pa_status pa_resample(pa_ctx *ctx, double dbeta, int32_t step, double *lnQ_out, 
  * replica gather and followed by the per-replica energies, largest-state
  * occupations, the energy histogram and the step's estimators.  One sweep
  * updates the colour (x+y) even sites, then the odd ones; each attempt
- * proposes one of the q-1 other states uniformly and accepts it with
- * probability min(1, exp(-beta dE)) quantised to 32 bits.
+ * proposes s' = s + d or s - d (mod q) with a random direction and
+ * d = 1 + u, u uniform on B - 1 bits (B = ceil(log2 q); a symmetric proposal
+ * over the q-1 other states, uniform when q-1 is a power of two), and accepts
+ * it with probability min(1, exp(-beta dE)) quantised to 32 bits.
  * `step` must equal the step of the pending resample (or 0 for extra sweeps
- * at step 0 before any resample).  theta >= 0.
- * Errors: PA_ERR_INVALID for theta < 0 or beta < 0; PA_ERR_STATE for a step
- * mismatch or a failed context. */
+ * at step 0 before any resample).  0 <= theta <= 2^21.
+ * Errors: PA_ERR_INVALID for theta outside 0..2^21 or beta < 0;
+ * PA_ERR_STATE for a step mismatch or a failed context. */
 pa_status pa_sweep(pa_ctx *ctx, double beta, int32_t theta, int32_t step);
 
 /* Per-replica energies E_j of the current population, int32, in slot order.
@@ -261,7 +265,7 @@ typedef struct pa_batch pa_batch;
  * the initial populations with their step-0 estimators (synchronises).
  * Errors: PA_ERR_INVALID for M outside 1..1024, any invalid run (as pa_init),
  * differing seeds, K < 1, theta < 0 or a non-finite or negative beta;
- * PA_ERR_TOO_LARGE for a run with L*L > 204800 (as pa_init);
+ * PA_ERR_TOO_LARGE for a run whose replica is too large (as pa_init);
  * PA_ERR_NOMEM / PA_ERR_CUDA on allocation or launch failures. */
 pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream, pa_batch **out);
 

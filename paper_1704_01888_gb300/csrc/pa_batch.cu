@@ -29,7 +29,7 @@ constexpr int kB = 1024;
 constexpr int kMaxRuns = 1024;
 
 struct RunDev {
-    uint8_t *buf[2];
+    uint32_t *buf[2];
     int32_t *anc[2];
     int32_t *parent, *E, *Mt, *hist, *fam, *counts, *local_off, *blocksum;
     double *wtab;
@@ -38,11 +38,11 @@ struct RunDev {
     DevObs *obs;  // K + 1 records
     int32_t q, L, N, nbins, R0, R_cap, mode, rpb, chunk0, nchunks, K, ground;
     uint32_t stream_hi;
-    long long quad0;  // first quad of this run in the flattened init index
+    long long item0;  // first site word of this run in the flattened init index
 };
 
 struct StepDev {  // one per (step, run)
-    uint32_t thr[9];
+    Thresholds thr;
     double beta, dbeta;
     int32_t theta, active;
 };
@@ -52,7 +52,7 @@ struct BatchArgs {
     const StepDev *steps;  // (K_max + 1) x M
     const int32_t *step_counter;
     int32_t M, total_chunks;
-    long long total_quads;
+    long long total_items;
     uint32_t k0, k1;
     uint32_t rk0[10], rk1[10];
     int32_t gather;  // 0 for the measurement at step 0
@@ -70,15 +70,31 @@ __device__ __forceinline__ int run_of_chunk(const RunDev *runs, int M, int chunk
 
 __global__ void k_batch_init(const BatchArgs b)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.total_quads;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.total_items;
          i += (long long)gridDim.x * blockDim.x) {
         int lo = 0, hi = b.M - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
-            if (b.runs[mid].quad0 <= i) lo = mid; else hi = mid - 1;
+            if (b.runs[mid].item0 <= i) lo = mid; else hi = mid - 1;
         }
         const RunDev &r = b.runs[lo];
-        dev::init_quad(r.buf[0], r.anc[0], r.q, r.L, i - r.quad0, b.k0, b.k1, r.stream_hi, r.ground);
+        dev::init_item(r.buf[0], r.anc[0], r.q, r.L, i - r.item0, b.k0, b.k1, r.stream_hi, r.ground);
+    }
+}
+
+// The sweep body for a run's bits per state and row geometry.
+template <int MODE>
+__device__ __forceinline__ void batch_body(int B, const dev::Group &G, int L, uint32_t *sw, const uint4 *s_tab,
+                                           const BatchArgs &b, long long &sE, long long &sE2, long long &sM)
+{
+    switch (B) {
+    case 1: dev::sweep_group_bits<1, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 2: dev::sweep_group_bits<2, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 3: dev::sweep_group_bits<3, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 4: dev::sweep_group_bits<4, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 5: dev::sweep_group_bits<5, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 6: dev::sweep_group_bits<6, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
+    default: dev::sweep_group_bits<7, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
     }
 }
 
@@ -120,7 +136,7 @@ __global__ void __launch_bounds__(kB) k_batch_scatter(const BatchArgs b)
 __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
 {
     extern __shared__ uint4 smem4[];
-    __shared__ uint32_t s_thr[9];
+    __shared__ uint4 s_tab[33];
     __shared__ int s_prefix[kMaxRuns + 1];
     const int i = *b.step_counter;
     if (threadIdx.x == 0) {
@@ -168,25 +184,16 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
         G.stream_hi = r.stream_hi;
         G.gather = b.gather != 0;
         G.write_back = b.gather || sp.theta > 0;
-        if (threadIdx.x < 9) s_thr[threadIdx.x] = sp.thr[threadIdx.x];
+        dev::build_threshold_table(s_tab, sp.thr);
         long long sE = 0, sE2 = 0, sM = 0;
-        switch (r.L) {
-        case 16: dev::sweep_group_rows<16, 2>(G, 16, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM); break;
-        case 32: dev::sweep_group_rows<32, 4>(G, 32, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM); break;
-        case 48: dev::sweep_group_rows<48, 2>(G, 48, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM); break;
-        case 64: dev::sweep_group_rows<64, 4>(G, 64, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM); break;
-        case 128: dev::sweep_group_rows<128, 4>(G, 128, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM); break;
-        case 256: dev::sweep_group_rows<256, 4>(G, 256, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM); break;
-        default:
-            if (r.L % 8 != 0)
-                dev::sweep_group_sites(G, r.L, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM);
-            else if ((r.L / 8) % 4 == 0)
-                dev::sweep_group_rows<0, 4>(G, r.L, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM);
-            else if ((r.L / 8) % 2 == 0)
-                dev::sweep_group_rows<0, 2>(G, r.L, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM);
-            else
-                dev::sweep_group_rows<0, 1>(G, r.L, smem4, s_thr, b.rk0, b.rk1, sE, sE2, sM);
-        }
+        uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);
+        const int B = state_bits(r.q);
+        if (r.L == 64)
+            batch_body<0>(B, G, 64, sw, s_tab, b, sE, sE2, sM);
+        else if (r.L % 64 == 0)
+            batch_body<1>(B, G, r.L, sw, s_tab, b, sE, sE2, sM);
+        else
+            batch_body<2>(B, G, r.L, sw, s_tab, b, sE, sE2, sM);
         if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(r.acc, sE, sE2, sM);
     }
 }
@@ -222,6 +229,8 @@ struct pa_batch {
     std::vector<pa::RunDev> runs_h;
     pa::RunDev *runs_d = nullptr;
     pa::StepDev *steps_d = nullptr;
+    uint8_t *stage = nullptr;  // canonical-layout staging for pa_batch_get_spins
+    size_t stage_bytes = 0;
     int32_t *counter_d = nullptr;
     std::vector<void *> allocs;
     pa::BatchArgs args{};
@@ -242,14 +251,6 @@ pa_status bfail(cudaError_t e)
         cudaError_t pb_e_ = (expr);                        \
         if (pb_e_ != cudaSuccess) return bfail(pb_e_);     \
     } while (0)
-
-void thresholds(double beta, uint32_t thr[9])
-{
-    for (int d = -4; d <= 4; ++d) {
-        const double a = std::exp(-beta * (double)d);
-        thr[d + 4] = a >= 1.0 ? 0xFFFFFFFFu : (uint32_t)(a * 4294967296.0);
-    }
-}
 
 template <typename T>
 pa_status balloc(pa_batch *b, T **p, size_t count)
@@ -285,8 +286,7 @@ pa_status apply_launch(pa_batch *b, int budget, int threads)
     if (budget < 1024 || threads < 64 || threads > 1024 || threads % 32) return PA_ERR_INVALID;
     if (budget + static_smem > optin) return PA_ERR_INVALID;
     for (int m = 0; m < b->M; ++m) {
-        const size_t N = (size_t)b->cfg[m].L * b->cfg[m].L;
-        const size_t padded = (N + 15) & ~(size_t)15;
+        const size_t padded = pa::replica_bytes(b->cfg[m].q, b->cfg[m].L);
         if (padded > (size_t)budget) return PA_ERR_INVALID;
         int r = (int)(budget / padded);
         if (r > b->cfg[m].R) r = b->cfg[m].R;
@@ -322,7 +322,7 @@ pa_status enqueue_start(pa_batch *b)
         if (r.fam) PB_CK(cudaMemsetAsync(r.fam, 0, sizeof(int32_t) * r.R0, b->stream));
         PB_CK(cudaStreamSynchronize(b->stream));  // h lives on this stack frame
     }
-    long long threads_total = (b->args.total_quads + 255) / 256;
+    long long threads_total = (b->args.total_items + 255) / 256;
     int grid = (int)std::min<long long>(threads_total, 65535LL * 16);
     pa::k_batch_init<<<grid, 256, 0, b->stream>>>(b->args);
     pa::BatchArgs a0 = b->args;
@@ -384,7 +384,8 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
     for (int m = 0; m < M; ++m) {
         const pa_config &g = runs[m].cfg;
         if (g.q < 2 || g.q > 128 || g.L < 2 || g.L > 1024 || (g.L & 1) || g.R < 1 || g.stream < 0 ||
-            g.stream > 255 || g.seed != seed || runs[m].K < 1 || runs[m].theta < 0 || !runs[m].betas)
+            g.stream > 255 || g.seed != seed || runs[m].K < 1 || runs[m].theta < 0 ||
+            runs[m].theta > pa::kMaxTheta || !runs[m].betas)
             return PA_ERR_INVALID;
         if (g.resample_mode < PA_RESAMPLE_NEAREST_INT || g.resample_mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
         if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
@@ -416,7 +417,8 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
 
     pa_status s = PA_OK;
     int chunk0 = 0;
-    long long quad0 = 0;
+    size_t stage_bytes = 0;
+    long long item0 = 0;
     for (int m = 0; m < M; ++m) {
         const pa_run_desc &d = runs[m];
         pa_config g = d.cfg;
@@ -444,9 +446,10 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         r.nchunks = nc;
         chunk0 += nc;
         b->nchunks[m] = nc;
-        r.quad0 = quad0;
-        quad0 += (long long)g.R * (r.N / 4);
-        const size_t spin_bytes = (size_t)r.R_cap * r.N;
+        r.item0 = item0;
+        item0 += (long long)g.R * (2 * g.L * pa::row_words(g.L));
+        const size_t spin_bytes = (size_t)r.R_cap * pa::replica_bytes(g.q, g.L);
+        stage_bytes = std::max(stage_bytes, std::min((size_t)r.R_cap * r.N, (size_t)64 << 20));
         if ((s = balloc(b, &r.buf[0], spin_bytes)) || (s = balloc(b, &r.buf[1], spin_bytes)) ||
             (s = balloc(b, &r.E, r.R_cap)) || (s = balloc(b, &r.Mt, r.R_cap)) || (s = balloc(b, &r.hist, r.nbins)) ||
             (s = balloc(b, &r.counts, r.R_cap)) || (s = balloc(b, &r.local_off, r.R_cap)) ||
@@ -472,7 +475,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
             sp.beta = beta;
             sp.dbeta = i > 0 ? beta - runs[m].betas[i - 1] : 0.0;
             sp.theta = i > 0 ? b->theta[m] : 0;
-            thresholds(beta, sp.thr);
+            sp.thr = pa::acceptance_thresholds(beta);
         }
     }
     if ((s = balloc(b, &b->runs_d, M)) || (s = balloc(b, &b->steps_d, steps.size())) ||
@@ -487,7 +490,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
     a.step_counter = b->counter_d;
     a.M = M;
     a.total_chunks = chunk0;
-    a.total_quads = quad0;
+    a.total_items = item0;
     a.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
     a.k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
@@ -496,10 +499,9 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
     }
     a.gather = 1;
     int budget = 65536;
-    for (int m = 0; m < M; ++m) {
-        const int N = b->runs_h[m].N;
-        if (((N + 15) & ~15) > budget) budget = (N + 15) & ~15;
-    }
+    for (int m = 0; m < M; ++m) budget = std::max(budget, (int)pa::replica_bytes(b->cfg[m].q, b->cfg[m].L));
+    if ((s = balloc(b, &b->stage, stage_bytes))) return fail(s);
+    b->stage_bytes = stage_bytes;
     if ((s = apply_launch(b, budget, 512))) return fail(s);
     if ((s = enqueue_start(b))) return fail(s);
     e = cudaStreamSynchronize(b->stream);
@@ -575,11 +577,16 @@ pa_status pa_batch_get_spins(pa_batch *b, int32_t m, int64_t slot_begin, int64_t
     PB_CK(cudaMemcpy(&h, r.st, sizeof(h), cudaMemcpyDeviceToHost));
     if (slot_begin + count > h.pop) return PA_ERR_INVALID;
     if (count == 0) return PA_OK;
-    // the unused buffer of the pair serves as staging for the canonical layout
-    uint8_t *stage = r.buf[h.parity ^ 1];
-    PB_CK(pa::launch_to_canonical(r.buf[h.parity] + (size_t)slot_begin * r.N, stage, r.L, count, b->stream));
-    PB_CK(cudaMemcpyAsync(host, stage, (size_t)count * r.N, cudaMemcpyDeviceToHost, b->stream));
-    PB_CK(cudaStreamSynchronize(b->stream));
+    const size_t RW = (size_t)pa::replica_words(r.q, r.L);
+    const int64_t per = (int64_t)(b->stage_bytes / (size_t)r.N);
+    for (int64_t done = 0; done < count; done += per) {
+        const int64_t n = count - done < per ? count - done : per;
+        PB_CK(pa::launch_to_canonical(r.buf[h.parity] + (size_t)(slot_begin + done) * RW, b->stage, r.q, r.L, n,
+                                      b->stream));
+        PB_CK(cudaMemcpyAsync(host + (size_t)done * r.N, b->stage, (size_t)n * r.N, cudaMemcpyDeviceToHost,
+                              b->stream));
+        PB_CK(cudaStreamSynchronize(b->stream));
+    }
     return PA_OK;
 }
 

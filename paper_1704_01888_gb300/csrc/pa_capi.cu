@@ -7,7 +7,7 @@
 // parity, pending normaliser, ln Z, error flag) lives in device memory, so a
 // whole temperature schedule can be enqueued or captured as one CUDA graph
 // without host round trips.  The host computes only the per-beta acceptance
-// thresholds (nine 32-bit integers, passed as kernel arguments), using the C
+// thresholds (four 32-bit integers, passed as kernel arguments), using the C
 // library's exp so that they are reproducible bit for bit on the host.
 #include <atomic>
 #include <cmath>
@@ -31,6 +31,21 @@ static thread_local std::string t_cuda_error;
 
 void record_cuda_error(const char *msg) { t_cuda_error = msg; }
 
+Thresholds acceptance_thresholds(double beta)
+{
+    Thresholds th{};
+    for (int d = 1; d <= 4; ++d) {
+        const uint64_t T = (uint64_t)(std::exp(-beta * (double)d) * 4294967296.0);
+        if (T >= 4294967296ull) {
+            th.full |= 1u << (d - 1);
+            th.T[d - 1] = 0u;
+        } else {
+            th.T[d - 1] = (uint32_t)T;
+        }
+    }
+    return th;
+}
+
 }  // namespace pa
 
 namespace {
@@ -49,15 +64,6 @@ pa_status cuda_fail(cudaError_t e)
         if (pa_e_ != cudaSuccess) return cuda_fail(pa_e_); \
     } while (0)
 
-// Acceptance thresholds T[dE + 4] = min(2^32 - 1, floor(min(1, exp(-beta dE)) 2^32)).
-void thresholds(double beta, uint32_t thr[9])
-{
-    for (int d = -4; d <= 4; ++d) {
-        const double a = std::exp(-beta * (double)d);
-        thr[d + 4] = a >= 1.0 ? 0xFFFFFFFFu : (uint32_t)(a * 4294967296.0);
-    }
-}
-
 }  // namespace
 
 struct pa_ctx {
@@ -67,7 +73,7 @@ struct pa_ctx {
     uint32_t k0 = 0, k1 = 0;
     int sms = 0;
 
-    uint8_t *spins[2] = {nullptr, nullptr};
+    uint32_t *spins[2] = {nullptr, nullptr};  // multi-spin-coded populations
     int32_t *anc[2] = {nullptr, nullptr};
     int32_t *E = nullptr, *Mt = nullptr, *hist = nullptr, *fam = nullptr;
     int32_t *counts = nullptr, *local_off = nullptr, *blocksum = nullptr, *parent = nullptr;
@@ -147,16 +153,12 @@ void release(pa_ctx *c)
 pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
 {
     const int L = c->cfg.L;
-    const int N = c->N;
-    const bool words = (L % 8) == 0;
-    // work items per replica and half sweep: row segments of S words (S = 4,
-    // 2 or 1 as the row length L/8 allows) or single sites
-    const int L8 = L / 8;
-    const int S = !words ? 1 : (L8 % 4 == 0 ? 4 : (L8 % 2 == 0 ? 2 : 1));
-    const long long units = words ? (long long)L * (L8 / S) : N / 2;
+    const size_t RB = pa::replica_bytes(c->cfg.q, L);
+    // work items per replica and half sweep: the site words of one colour
+    const long long units = (long long)L * pa::row_words(L);
     int rpb = rpb_req;
     if (rpb <= 0) {
-        int rpb_mem = (int)(65536 / (size_t)N);
+        int rpb_mem = (int)(65536 / RB);
         if (rpb_mem < 1) rpb_mem = 1;
         int rpb_fill = c->cfg.R / (4 * c->sms);
         if (rpb_fill < 1) rpb_fill = 1;
@@ -165,7 +167,7 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
         const int rpb_warp = (int)((32 + units - 1) / units);
         if (rpb < rpb_warp) rpb = rpb_warp < rpb_mem ? rpb_warp : rpb_mem;
     }
-    if ((size_t)rpb * N > (size_t)pa::kMaxLatticeBytes) return rpb == 1 ? PA_ERR_TOO_LARGE : PA_ERR_INVALID;
+    if ((size_t)rpb * RB > (size_t)pa::kMaxLatticeBytes) return rpb == 1 ? PA_ERR_TOO_LARGE : PA_ERR_INVALID;
     int threads = threads_req;
     if (threads <= 0) {
         const long long work = (long long)rpb * units;
@@ -174,7 +176,7 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
         if (threads < 32) threads = 32;
     }
     if (threads % 32 != 0 || threads > 1024) return PA_ERR_INVALID;
-    const int per_sm = pa::sweep_max_blocks_per_sm(L, rpb, threads);
+    const int per_sm = pa::sweep_max_blocks_per_sm(c->cfg.q, L, rpb, threads);
     if (per_sm <= 0) return PA_ERR_INVALID;
     const long long groups = ((long long)c->R_cap + rpb - 1) / rpb;
     long long grid = (long long)per_sm * c->sms;
@@ -199,7 +201,7 @@ pa::SweepArgs sweep_args(pa_ctx *c, double beta, int theta, int step, int gather
     a.acc = c->acc;
     a.fam = c->cfg.track_families ? c->fam : nullptr;
     a.st = c->st;
-    thresholds(beta, a.thr);
+    a.thr = pa::acceptance_thresholds(beta);
     a.k0 = c->k0;
     a.k1 = c->k1;
     for (int r = 0; r < 10; ++r) {
@@ -303,7 +305,7 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
     if (g.resample_mode < PA_RESAMPLE_NEAREST_INT || g.resample_mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
     if (g.init_mode != PA_INIT_RANDOM && g.init_mode != PA_INIT_GROUND) return PA_ERR_INVALID;
     if (!(g.beta0 >= 0.0) || !std::isfinite(g.beta0)) return PA_ERR_INVALID;
-    if ((long long)g.L * g.L > pa::kMaxLatticeBytes) return PA_ERR_TOO_LARGE;
+    if (pa::replica_bytes(g.q, g.L) > (size_t)pa::kMaxLatticeBytes) return PA_ERR_TOO_LARGE;
     long long R_cap = g.R_cap > 0 ? g.R_cap : (long long)g.R + g.R / 4 + 1024;
     if (R_cap < g.R || R_cap >= (1LL << 24)) return PA_ERR_INVALID;
 
@@ -330,7 +332,7 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(cuda_fail(e));
 
-    const size_t spin_bytes = (size_t)c->R_cap * c->N;
+    const size_t spin_bytes = (size_t)c->R_cap * pa::replica_bytes(g.q, g.L);
     const int nb = (c->R_cap + 1023) / 1024;
     if ((s = dev_alloc(&c->spins[0], spin_bytes)) || (s = dev_alloc(&c->spins[1], spin_bytes)) ||
         (s = dev_alloc(&c->E, c->R_cap)) || (s = dev_alloc(&c->Mt, c->R_cap)) ||
@@ -346,7 +348,9 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
     }
     c->obs_cap = 1024;
     if ((s = dev_alloc(&c->obs, c->obs_cap))) return fail(s);
-    c->stage_bytes = spin_bytes < (64u << 20) ? spin_bytes : (64u << 20);
+    // staging for the canonical layout of pa_get_spins (at least one replica)
+    const size_t canon_bytes = (size_t)c->R_cap * c->N;
+    c->stage_bytes = canon_bytes < (64u << 20) ? canon_bytes : (64u << 20);
     if ((s = dev_alloc(&c->stage, c->stage_bytes))) return fail(s);
     if ((s = choose_launch(c, 0, 0))) return fail(s);
     *out = c;
@@ -356,7 +360,7 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
 // Checkpoint file: a fixed header, the population's arrays, and an FNV-1a
 // checksum of everything before it.
 constexpr char kMagic[8] = {'P', 'A', 'G', 'B', '3', '0', '0', '\x01'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;  // 2: multi-spin-coded spin arrays
 
 struct CkptHeader {
     char magic[8];
@@ -422,12 +426,12 @@ pa_status pa_save(pa_ctx *c, const char *path)
     pa::DevState st;
     pa_status s = sync_state(c, &st);
     if (s) return s;
-    const size_t pop = (size_t)st.pop, N = (size_t)c->N;
+    const size_t pop = (size_t)st.pop, RB = pa::replica_bytes(c->cfg.q, c->cfg.L);
     const bool fam = c->cfg.track_families != 0;
-    std::vector<unsigned char> payload(pop * N + 4 * (2 * pop + (size_t)c->nbins + (fam ? pop : 0)));
+    std::vector<unsigned char> payload(pop * RB + 4 * (2 * pop + (size_t)c->nbins + (fam ? pop : 0)));
     unsigned char *p = payload.data();
-    PA_CK(cudaMemcpy(p, c->spins[st.parity], pop * N, cudaMemcpyDeviceToHost));
-    p += pop * N;
+    PA_CK(cudaMemcpy(p, c->spins[st.parity], pop * RB, cudaMemcpyDeviceToHost));
+    p += pop * RB;
     PA_CK(cudaMemcpy(p, c->E, 4 * pop, cudaMemcpyDeviceToHost));
     p += 4 * pop;
     PA_CK(cudaMemcpy(p, c->Mt, 4 * pop, cudaMemcpyDeviceToHost));
@@ -480,11 +484,13 @@ pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out)
     uint64_t check = fnv1a(reinterpret_cast<const unsigned char *>(&h), sizeof(h), 1469598103934665603ull);
     check = fnv1a(payload.data(), payload.size(), check);
     if (check != sum) return PA_ERR_INVALID;
+    if (h.cfg.q < 2 || h.cfg.q > 128 || h.cfg.L < 2 || h.cfg.L > 1024) return PA_ERR_INVALID;
     const size_t N = (size_t)h.cfg.L * h.cfg.L, pop = (size_t)h.pop;
+    const size_t RB = pa::replica_bytes(h.cfg.q, h.cfg.L);
     const bool fam = h.cfg.track_families != 0;
     const size_t nbins = 2 * N + 1;
     if (h.pop < 1 || h.pop > h.cfg.R_cap || h.step < 0 ||
-        payload.size() != pop * N + 4 * (2 * pop + nbins + (fam ? pop : 0)))
+        payload.size() != pop * RB + 4 * (2 * pop + nbins + (fam ? pop : 0)))
         return PA_ERR_INVALID;
     pa_ctx *c = nullptr;
     pa_status s = ctx_create(h.cfg, cuda_stream, &c);
@@ -495,8 +501,8 @@ pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out)
         return e;
     };
     const unsigned char *p = payload.data();
-    cudaError_t e = cudaMemcpy(c->spins[0], p, pop * N, cudaMemcpyHostToDevice);
-    p += pop * N;
+    cudaError_t e = cudaMemcpy(c->spins[0], p, pop * RB, cudaMemcpyHostToDevice);
+    p += pop * RB;
     if (e == cudaSuccess) e = cudaMemcpy(c->E, p, 4 * pop, cudaMemcpyHostToDevice);
     p += 4 * pop;
     if (e == cudaSuccess) e = cudaMemcpy(c->Mt, p, 4 * pop, cudaMemcpyHostToDevice);
@@ -573,7 +579,7 @@ pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, in
 pa_status pa_sweep(pa_ctx *c, double beta, int32_t theta, int32_t step)
 {
     if (!c) return PA_ERR_INVALID;
-    if (theta < 0 || !(beta >= 0.0) || !std::isfinite(beta)) return PA_ERR_INVALID;
+    if (theta < 0 || theta > pa::kMaxTheta || !(beta >= 0.0) || !std::isfinite(beta)) return PA_ERR_INVALID;
     if (c->failed) return PA_ERR_STATE;
     if (c->pending_step != 0 ? step != c->pending_step : step != c->step) return PA_ERR_STATE;
     return enqueue_sweep(c, beta, theta, step);
@@ -644,8 +650,9 @@ pa_status pa_get_spins(pa_ctx *c, int64_t slot_begin, int64_t count, uint8_t *ho
     const int64_t per = (int64_t)(c->stage_bytes / c->N);
     for (int64_t done = 0; done < count; done += per) {
         const int64_t n = count - done < per ? count - done : per;
-        PA_CK(pa::launch_to_canonical(c->spins[h.parity] + (size_t)(slot_begin + done) * c->N, c->stage, c->cfg.L, n,
-                                      c->stream));
+        const size_t RW = (size_t)pa::replica_words(c->cfg.q, c->cfg.L);
+        PA_CK(pa::launch_to_canonical(c->spins[h.parity] + (size_t)(slot_begin + done) * RW, c->stage, c->cfg.q,
+                                      c->cfg.L, n, c->stream));
         PA_CK(cudaMemcpyAsync(host + (size_t)done * c->N, c->stage, (size_t)n * c->N, cudaMemcpyDeviceToHost,
                               c->stream));
         PA_CK(cudaStreamSynchronize(c->stream));
@@ -668,7 +675,7 @@ pa_status pa_get_ancestors(pa_ctx *c, int32_t *host)
 pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_obs *obs_out,
                  const int32_t *hist_steps, int32_t n_hist, int32_t *hist_out, int32_t use_graph)
 {
-    if (!c || !betas || K < 1 || theta < 0 || n_hist < 0 || (n_hist > 0 && (!hist_steps || !hist_out)))
+    if (!c || !betas || K < 1 || theta < 0 || theta > pa::kMaxTheta || n_hist < 0 || (n_hist > 0 && (!hist_steps || !hist_out)))
         return PA_ERR_INVALID;
     if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
     for (int i = 0; i <= K; ++i)
@@ -774,7 +781,7 @@ pa_status pa_next_dbeta(pa_ctx *c, double target, double dbeta_cap, int32_t iter
 pa_status pa_run_adaptive(pa_ctx *c, double beta_end, double target, double dbeta_max, int32_t iters, int32_t theta,
                           int32_t max_steps, pa_obs *obs_out, double *betas_out, int32_t *K_out)
 {
-    if (!c || !K_out || theta < 0 || max_steps < 1 || !(beta_end >= 0.0) || !std::isfinite(beta_end) ||
+    if (!c || !K_out || theta < 0 || theta > pa::kMaxTheta || max_steps < 1 || !(beta_end >= 0.0) || !std::isfinite(beta_end) ||
         !(dbeta_max > 0.0))
         return PA_ERR_INVALID;
     if (c->failed || c->pending_step != 0) return PA_ERR_STATE;

@@ -1,15 +1,18 @@
 // pa_internal.cuh -- device helpers and host<->device structures shared by the
 // translation units of the GB300 population-annealing library.
 //
-// Device layout of one replica (N = L*L bytes, one byte per spin):
-//   byte (c * N/2 + y * L/2 + m) holds site (x, y) with colour c = (x + y) & 1
-//   and x = 2m + ((y + c) & 1).
-// Each colour's sites of one row are contiguous, so the four neighbours of
-// four consecutive same-colour sites are four aligned or byte-shifted 32-bit
-// words of the other colour (left/right in the same row, up/down in the rows
-// above and below).  Replicas are stored back to back: replica s starts at
-// byte s*N of its buffer.  The canonical [y][x] layout exists only at the API
-// boundary (pa_get_spins).
+// Device layout of one replica (multi-spin coding).  A state 0..q-1 takes
+// B = ceil(log2 q) bits; the sites of colour c = (x + y) & 1 in row y, with
+// column index m = x >> 1, are packed 32 columns to a word: word t = m >> 5 of
+// the row, bit b = m & 31.  Each such site word is stored as BP 32-bit planes
+// (BP = B rounded up to 1, 2, 4 or 8; plane p holds bit p of the states):
+//   word index ((c * L + y) * WPR + t) * BP + p,   WPR = ceil(L / 64).
+// Bits of columns >= L/2 and planes >= B are always zero.  One replica takes
+// RW = 2 L WPR BP words; replica s starts at word s * RW of its buffer.  The
+// four neighbours of a site word are the words of the other colour in rows
+// y-1, y+1 and y and that row word shifted by one bit, so one 32-bit logic
+// instruction serves 32 sites.  The canonical [y][x] byte layout exists only at
+// the API boundary (pa_get_spins).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -23,9 +26,28 @@ constexpr uint32_t DOM_INIT = 0x40000000u;
 constexpr uint32_t DOM_RESAMPLE = 0x80000000u;
 constexpr uint32_t DOM_GROUND = 0xC0000000u;
 
-// Largest lattice (bytes, one per site) a sweep block keeps in shared memory,
-// leaving room for the threshold table and block reductions within 227 KB.
+// Sweeps per temperature step: 2k + colour must fit below the domain tag of
+// the counter word in which it is shifted left by 8.
+constexpr int kMaxTheta = 1 << 21;
+
+// Largest replica (bytes of its bit planes) a sweep block keeps in shared
+// memory, leaving room for the threshold table and reductions within 227 KB.
 constexpr int kMaxLatticeBytes = 200 * 1024;
+
+// Bits per state, planes stored per site word, words per row of one colour,
+// words per replica (see the layout above).
+__host__ __device__ constexpr int state_bits(int q) { return q <= 2 ? 1 : q <= 4 ? 2 : q <= 8 ? 3 : q <= 16 ? 4 : q <= 32 ? 5 : q <= 64 ? 6 : 7; }
+__host__ __device__ constexpr int plane_stride(int B) { return B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8; }
+__host__ __device__ constexpr int row_words(int L) { return (L + 63) / 64; }
+__host__ __device__ constexpr int replica_words(int q, int L) { return 2 * L * row_words(L) * plane_stride(state_bits(q)); }
+inline size_t replica_bytes(int q, int L) { return (size_t)replica_words(q, L) * 4; }
+
+// Acceptance thresholds T[d] = floor(exp(-beta d) 2^32), d = 1..4, as the low 32
+// bits plus a flag for T[d] = 2^32 (beta = 0), computed on the host with libm.
+struct Thresholds {
+    uint32_t T[4];
+    uint32_t full;  // bit d-1 set where T[d] = 2^32
+};
 
 // Device-resident run state.  Kernels read and update it so that a whole
 // schedule can be enqueued (or captured in a graph) with no host round trip.
@@ -48,7 +70,7 @@ struct DevObs {
 };
 
 struct SweepArgs {
-    uint8_t *buf[2];           // spin double buffer
+    uint32_t *buf[2];          // spin double buffer (layout above)
     int32_t *anc[2];           // ancestor double buffer (null: no families)
     const int32_t *parent;     // parent map of the pending resample (null: in place)
     int32_t *E;                // per-replica energies
@@ -57,7 +79,7 @@ struct SweepArgs {
     unsigned long long *acc;   // [3] running sums of E, E^2, Mt (two's complement)
     int32_t *fam;              // family counts (null: no families)
     DevState *st;
-    uint32_t thr[9];           // acceptance thresholds T[dE + 4]
+    Thresholds thr;            // acceptance thresholds
     uint32_t k0, k1;           // Philox key (seed low / high word)
     uint32_t rk0[10], rk1[10]; // Philox round keys k + r * (Weyl constant), r = 0..9
     int32_t q, L, theta, step;
@@ -68,11 +90,11 @@ struct SweepArgs {
 
 // Launchers (pa_sweep.cu)
 cudaError_t launch_sweep(const SweepArgs &a, int threads, int grid, cudaStream_t s);
-size_t sweep_smem_bytes(int L, int rpb);
-int sweep_max_blocks_per_sm(int L, int rpb, int threads);
+size_t sweep_smem_bytes(int q, int L, int rpb);
+int sweep_max_blocks_per_sm(int q, int L, int rpb, int threads);
 
 // Launchers (pa_resample.cu)
-cudaError_t launch_init(uint8_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
+cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
                         uint32_t stream_hi, int ground, cudaStream_t s);
 cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, double dbeta, int R_target,
                             int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1, double *wtab,
@@ -80,8 +102,11 @@ cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, do
                             int32_t *hist_zero, DevState *st, cudaStream_t s);
 cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,
                             double beta, int q, int N, int gathered, int resampled, cudaStream_t s);
-cudaError_t launch_to_canonical(const uint8_t *spins, uint8_t *out, int L, int64_t count,
+cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count,
                                 cudaStream_t s);
+
+// Host: the thresholds of inverse temperature beta.
+Thresholds acceptance_thresholds(double beta);
 
 // Launchers (pa_reweight.cu)
 cudaError_t launch_newton(const int32_t *hist, int nbins, const DevState *st, double target, double cap, int iters,

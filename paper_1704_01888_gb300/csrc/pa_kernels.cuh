@@ -7,6 +7,8 @@
 // (the gather of Sec. 2 step 2 fused into the load), runs theta
 // checkerboard Metropolis sweeps (Sec. 2 step 3) and measures each replica's
 // energy (Eq. 3), largest-state occupation (Eq. 5) and the energy histogram.
+// Spins are multi-spin coded (layout in pa_internal.cuh): every logic
+// instruction of the update acts on the 32 sites of one site word.
 // Resampling bodies (Sec. 2 step 2, Eq. 2): weights and ln Q, copy numbers and
 // their scan, parent map; estimators (Sec. 2 step 4, Eqs. 4-5).
 #pragma once
@@ -18,82 +20,95 @@ namespace pa {
 namespace dev {
 
 // ===========================================================================
-// SWAR helpers (four spins per 32-bit word, all values < 128)
+// Bit-plane helpers
 // ===========================================================================
 
-// Bit 7 of each byte is set where the bytes of a and b differ.
-__device__ __forceinline__ uint32_t differ_bits(uint32_t a, uint32_t b)
+// BP consecutive words (the planes of one site word) with one vector access.
+template <int BP>
+__device__ __forceinline__ void load_planes(uint32_t (&v)[BP], const uint32_t *src)
 {
-    return ((a ^ b) + 0x7F7F7F7Fu) & 0x80808080u;
-}
-
-// Per byte: how many of the four neighbour words differ from a (0..4).
-__device__ __forceinline__ uint32_t count_differ(uint32_t a, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3)
-{
-    return (differ_bits(a, n0) >> 7) + (differ_bits(a, n1) >> 7) + (differ_bits(a, n2) >> 7) +
-           (differ_bits(a, n3) >> 7);
-}
-
-struct Neighbours {
-    uint32_t up, down, same, shifted;
-};
-
-// Neighbour words of word t in row y of a colour whose row offset is p =
-// (y + colour) & 1.  `oth` is the other colour's sublattice of the replica.
-__device__ __forceinline__ Neighbours load_neighbours(const uint32_t *oth, int L, int L8, int y, int t, int p)
-{
-    Neighbours nb;
-    const int yu = (y == 0) ? L - 1 : y - 1;
-    const int yd = (y == L - 1) ? 0 : y + 1;
-    const int row = y * L8;
-    nb.up = oth[yu * L8 + t];
-    nb.down = oth[yd * L8 + t];
-    nb.same = oth[row + t];
-    if (p == 0) {
-        const int tl = (t == 0) ? L8 - 1 : t - 1;
-        nb.shifted = __funnelshift_l(oth[row + tl], nb.same, 8);  // bytes m-1
+    if constexpr (BP == 1) {
+        v[0] = src[0];
+    } else if constexpr (BP == 2) {
+        const uint2 a = *reinterpret_cast<const uint2 *>(src);
+        v[0] = a.x;
+        v[1] = a.y;
     } else {
-        const int tr = (t == L8 - 1) ? 0 : t + 1;
-        nb.shifted = __funnelshift_r(nb.same, oth[row + tr], 8);  // bytes m+1
+#pragma unroll
+        for (int h = 0; h < BP / 4; ++h) {
+            const uint4 a = reinterpret_cast<const uint4 *>(src)[h];
+            v[4 * h + 0] = a.x;
+            v[4 * h + 1] = a.y;
+            v[4 * h + 2] = a.z;
+            v[4 * h + 3] = a.w;
+        }
     }
-    return nb;
 }
 
-template <int S>
-struct Vec;
-template <>
-struct Vec<1> {
-    uint32_t v[1];
-    __device__ __forceinline__ void load(const uint32_t *p) { v[0] = p[0]; }
-    __device__ __forceinline__ void store(uint32_t *p) const { p[0] = v[0]; }
-};
-template <>
-struct Vec<2> {
-    uint32_t v[2];
-    __device__ __forceinline__ void load(const uint32_t *p)
-    {
-        const uint2 x = *reinterpret_cast<const uint2 *>(p);
-        v[0] = x.x;
-        v[1] = x.y;
+template <int BP>
+__device__ __forceinline__ void store_planes(uint32_t *dst, const uint32_t (&v)[BP])
+{
+    if constexpr (BP == 1) {
+        dst[0] = v[0];
+    } else if constexpr (BP == 2) {
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int h = 0; h < BP / 4; ++h)
+            reinterpret_cast<uint4 *>(dst)[h] = make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
     }
-    __device__ __forceinline__ void store(uint32_t *p) const { *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]); }
-};
-template <>
-struct Vec<4> {
-    uint32_t v[4];
-    __device__ __forceinline__ void load(const uint32_t *p)
-    {
-        const uint4 x = *reinterpret_cast<const uint4 *>(p);
-        v[0] = x.x;
-        v[1] = x.y;
-        v[2] = x.z;
-        v[3] = x.w;
+}
+
+// Bit set where the B-bit states held in planes a and b differ.
+template <int B, int BP>
+__device__ __forceinline__ uint32_t differ(const uint32_t (&a)[BP], const uint32_t (&b)[BP])
+{
+    uint32_t d = a[0] ^ b[0];
+#pragma unroll
+    for (int p = 1; p < B; ++p) d |= a[p] ^ b[p];
+    return d;
+}
+
+// Bit set where the B-bit state in planes a equals the constant state s.
+template <int B, int BP>
+__device__ __forceinline__ uint32_t equal_state(const uint32_t (&a)[BP], int s)
+{
+    uint32_t d = 0;
+#pragma unroll
+    for (int p = 0; p < B; ++p) d |= a[p] ^ (((s >> p) & 1) ? 0xFFFFFFFFu : 0u);
+    return ~d;
+}
+
+__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum, uint32_t &carry)
+{
+    sum = a ^ b ^ c;
+    carry = (a & b) | (c & (a ^ b));
+}
+
+// Valid-column mask of word t of a row with WPR words and nb_last valid bits
+// in its last word.
+__device__ __forceinline__ uint32_t valid_mask(int t, int WPR, int nb_last)
+{
+    return (t < WPR - 1 || nb_last == 32) ? 0xFFFFFFFFu : ((1u << nb_last) - 1u);
+}
+
+// The row word H (other colour, row y) shifted so that bit b holds the
+// horizontal neighbour of column 32 t + b that is not at the same column:
+// column m + 1 when par = 1, column m - 1 when par = 0 (par = (x & 1) of the
+// row's sites).  E is the adjacent word of the row (t + 1 for par = 1, t - 1
+// for par = 0, cyclically); MODE 0 is L = 64 (one full word per row), MODE 1
+// rows of full words, MODE 2 rows whose last word holds nb_last < 32 columns.
+template <int MODE>
+__device__ __forceinline__ uint32_t shifted_row(uint32_t H, uint32_t E, int par, int nb, int nbe)
+{
+    if constexpr (MODE == 0) {
+        return __funnelshift_l(H, H, par ? 31 : 1);
+    } else if constexpr (MODE == 1) {
+        return par ? __funnelshift_r(H, E, 1) : __funnelshift_r(E, H, 31);
+    } else {
+        return par ? ((H >> 1) | ((E & 1u) << (nb - 1))) : ((H << 1) | ((E >> (nbe - 1)) & 1u));
     }
-    __device__ __forceinline__ void store(uint32_t *p) const
-    {
-        *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
-    }
-};
+}
 
 // Block-wide sum of ints; every thread receives it.  All threads must call.
 __device__ __forceinline__ int block_sum_int(int v)
@@ -118,8 +133,8 @@ __device__ __forceinline__ int block_sum_int(int v)
 // One group of resident replicas
 // ===========================================================================
 struct Group {
-    const uint8_t *in;       // buffer holding the parents (or the replicas themselves)
-    uint8_t *out;            // buffer receiving the swept replicas
+    const uint32_t *in;      // buffer holding the parents (or the replicas themselves)
+    uint32_t *out;           // buffer receiving the swept replicas
     const int32_t *parent;   // parent map of a pending resample (used when gather)
     const int32_t *anc_in;   // family ids (null: no families)
     int32_t *anc_out;
@@ -153,34 +168,66 @@ __device__ __forceinline__ void group_families(const Group &G)
     }
 }
 
-// Row-segment body (L % 8 == 0).  LT > 0 fixes L at compile time; S is the
-// number of 32-bit words (4 same-colour sites each) one thread updates per
-// loop step: S consecutive words of one row of one colour, read and written
-// with one vector access per neighbour row.  Each site takes one 32-bit
-// Philox word u: the high and low halves of u (q - 1) are its proposal offset
-// and its acceptance uniform.  s_thr holds T[dE + 4]; rk0 / rk1 the round keys.
-template <int LT, int S>
-__device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 *smem4, const uint32_t *s_thr,
+// Shared-memory table of the acceptance thresholds for the bitwise
+// comparison v < T[dE]: entry j (0..31) holds, for d = 1..4, all ones where
+// bit 31 - j of T[d] is set; entry 32 marks T[d] = 2^32.  The block's threads
+// share the 33 entries (blocks may have as few as 32 threads).
+__device__ __forceinline__ void build_threshold_table(uint4 *tab, const Thresholds &th)
+{
+    auto m = [](uint32_t bit) { return bit ? 0xFFFFFFFFu : 0u; };
+    for (int j = threadIdx.x; j < 33; j += blockDim.x) {
+        if (j < 32) {
+            const int b = 31 - j;
+            tab[j] = make_uint4(m((th.T[0] >> b) & 1u), m((th.T[1] >> b) & 1u), m((th.T[2] >> b) & 1u),
+                                m((th.T[3] >> b) & 1u));
+        } else {
+            tab[32] = make_uint4(m(th.full & 1u), m(th.full & 2u), m(th.full & 4u), m(th.full & 8u));
+        }
+    }
+}
+
+// Threshold bit of plane entry tb for each site: the site's dE class is
+// given by c0 (dE odd) and e1 (dE >= 3): dE = 1, 2, 3, 4 select .x, .y, .z, .w.
+__device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0, uint32_t e1)
+{
+    const uint32_t lo = (c0 & tb.x) | (~c0 & tb.y);
+    const uint32_t hi = (c0 & tb.z) | (~c0 & tb.w);
+    return (e1 & hi) | (~e1 & lo);
+}
+
+// Multi-spin-coded sweep body.  B = bits per state (compile time), MODE as
+// for shifted_row.  Each loop step of a thread updates one site word: 32
+// same-colour sites of one row.  The random numbers follow this rule: in
+// sweep k, colour c, the site word with index w = y WPR + t draws the stream
+// Z_0, Z_1, ... (Z_{4n+i} = word i of the Philox call with counter
+// (w, SWEEP | (2k + c) << 8 | n, step, slot | stream)); the site at bit b takes
+// bit b of each: direction sigma from Z_0, offset u from Z_1..Z_{B-1}, and
+// acceptance bits v_j from Z_{BP+j}, most significant first.  Proposal
+// s' = s + (1 + u) mod q (sigma = 0) or s - (1 + u) mod q (sigma = 1) by two
+// ripple-carry additions over the planes; dE + 4 is the count of eight
+// indicator bits (neighbours equal to s, neighbours different from s'), summed
+// by a carry-save tree; moves with dE > 0 compare v with T[dE] bit by bit, and
+// the warp draws further acceptance words only while some site is undecided.
+template <int B, int MODE>
+__device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32_t *sw, const uint4 *s_tab,
                                                  const uint32_t *rk0, const uint32_t *rk1, long long &sE,
                                                  long long &sE2, long long &sM)
 {
-    uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);
-    const int L = LT > 0 ? LT : Lrt;
+    constexpr int BP = plane_stride(B);
+    const int L = MODE == 0 ? 64 : Lrt;
     const int N = L * L;
-    const int L8 = L / 8;     // words per row of one colour
-    const int WPC = N / 8;    // words per colour per replica
-    const int WPR = N / 4;    // words per replica
-    const int UPR = N / 16;   // uint4 per replica
-    const int SPR = L8 / S;   // segments per row
-    const int UPC = L * SPR;  // segments per colour per replica
+    const int WPR = MODE == 0 ? 1 : row_words(L);
+    const int nb_last = L / 2 - 32 * (WPR - 1);
+    const int IPC = L * WPR;      // site words per colour per replica
+    const int RW = 2 * IPC * BP;  // words per replica
+    const int UPR = RW / 4;       // uint4 per replica
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const uint32_t qm1 = (uint32_t)(G.q - 1);
-    const uint32_t qb = (uint32_t)G.q;
-    const char *thr_bytes = reinterpret_cast<const char *>(s_thr);
+    const int q = G.q;
     const int first = G.first, nrep = G.nrep;
+    uint4 *smem4 = reinterpret_cast<uint4 *>(sw);
 
     // gather: replica first + r comes from its parent's lattice
     for (int i = tid; i < nrep * UPR; i += blockDim.x) {
@@ -188,71 +235,152 @@ __device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 
         const int o = i - r * UPR;
         const int slot = first + r;
         const int src = G.gather ? G.parent[slot] : slot;
-        smem4[r * UPR + o] = reinterpret_cast<const uint4 *>(G.in + (size_t)src * N)[o];
+        smem4[r * UPR + o] = reinterpret_cast<const uint4 *>(G.in + (size_t)src * RW)[o];
     }
     __syncthreads();
 
+    // q and 2^(B+1) - q as plane masks, for the reduction mod q
+    uint32_t qm[B + 1], nqm[B + 1];
+#pragma unroll
+    for (int p = 0; p <= B; ++p) {
+        qm[p] = ((q >> p) & 1) ? 0xFFFFFFFFu : 0u;
+        nqm[p] = ((((1 << (B + 1)) - q) >> p) & 1) ? 0xFFFFFFFFu : 0u;
+    }
+    const bool any_full = s_tab[32].x | s_tab[32].y | s_tab[32].z | s_tab[32].w;
+    const int total = nrep * IPC;
+
     for (int k = 0; k < G.theta; ++k) {
         for (int c = 0; c < 2; ++c) {
-            const uint32_t ctr1 = DOM_SWEEP | (uint32_t)(2 * k + c);
-            for (int i = tid; i < nrep * UPC; i += blockDim.x) {
-                const int r = i / UPC;
-                const int u = i - r * UPC;
-                const int y = u / SPR;
-                const int t0 = (u - y * SPR) * S;
-                uint32_t *own = sw + r * WPR + c * WPC;
-                const uint32_t *oth = sw + r * WPR + (c ^ 1) * WPC;
-                const int p = (y + c) & 1;  // 0: horizontal neighbours at m-1, m; 1: at m, m+1
-                const int row = y * L8;
+            const uint32_t ctr1 = DOM_SWEEP | ((uint32_t)(2 * k + c) << 8);
+            for (int base = warp * 32; base < total; base += nwarps * 32) {
+                const int i = base + lane;
+                const bool live = i < total;
+                const int ii = live ? i : total - 1;
+                const int r = ii / IPC;
+                const int rem = ii - r * IPC;
+                const int y = MODE == 0 ? rem : rem / WPR;
+                const int t = MODE == 0 ? 0 : rem - y * WPR;
+                uint32_t *rep = sw + r * RW;
+                uint32_t *own = rep + ((c * L + y) * WPR + t) * BP;
+                const uint32_t *oth = rep + (c ^ 1) * IPC * BP;
                 const int yu = (y == 0) ? L - 1 : y - 1;
                 const int yd = (y == L - 1) ? 0 : y + 1;
-                Vec<S> W, U, D, H;
-                W.load(own + row + t0);
-                U.load(oth + yu * L8 + t0);
-                D.load(oth + yd * L8 + t0);
-                H.load(oth + row + t0);
-                const int te = p ? (t0 + S == L8 ? 0 : t0 + S) : (t0 == 0 ? L8 - 1 : t0 - 1);
-                const uint32_t edge = oth[row + te];
-                const uint32_t sh = p ? 8u : 24u;
-                // sublattice index of byte 0 of word t0 is y*L/2 + 4*t0; one Philox
-                // call serves the four sites of a word (counter = index / 4)
-                const uint32_t quad0 = (uint32_t)(y * (L / 8) + t0);
-                const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
-                Vec<S> NW;
+                const int par = (y + c) & 1;
+                uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
+                load_planes<BP>(W, own);
+                load_planes<BP>(U, oth + (yu * WPR + t) * BP);
+                load_planes<BP>(D, oth + (yd * WPR + t) * BP);
+                load_planes<BP>(H, oth + (y * WPR + t) * BP);
+                uint32_t vmask = 0xFFFFFFFFu;
+                if constexpr (MODE == 0) {
 #pragma unroll
-                for (int j = 0; j < S; ++j) {
-                    const uint32_t lo = p ? H.v[j] : (j == 0 ? edge : H.v[j > 0 ? j - 1 : 0]);
-                    const uint32_t hi = p ? (j == S - 1 ? edge : H.v[j < S - 1 ? j + 1 : 0]) : H.v[j];
-                    const uint32_t shifted = __funnelshift_r(lo, hi, sh);
-                    const uint32_t Wj = W.v[j];
-                    // one word per site: (high, low) of the 64-bit product u (q-1) are the
-                    // proposal offset and the acceptance uniform
-                    const uint4 ru = philox10_rk(make_uint4(quad0 + j, ctr1, (uint32_t)G.step, slot), rk0, rk1);
-                    const uint64_t px = (uint64_t)ru.x * qm1, py = (uint64_t)ru.y * qm1;
-                    const uint64_t pz = (uint64_t)ru.z * qm1, pw = (uint64_t)ru.w * qm1;
-                    const uint32_t m = __byte_perm(__byte_perm((uint32_t)(px >> 32), (uint32_t)(py >> 32), 0x0040),
-                                                   __byte_perm((uint32_t)(pz >> 32), (uint32_t)(pw >> 32), 0x0040),
-                                                   0x5410);
-                    // proposals s' = s + 1 + m, reduced mod q bytewise
-                    uint32_t P = Wj + m + 0x01010101u;
-                    const uint32_t ge = (P + (0x80u - qb) * 0x01010101u) & 0x80808080u;
-                    P -= (ge >> 7) * qb;
-                    // 4 (dE + 4) per byte: byte offsets into the threshold table
-                    const uint32_t dW = count_differ(Wj, U.v[j], D.v[j], H.v[j], shifted);
-                    const uint32_t dP = count_differ(P, U.v[j], D.v[j], H.v[j], shifted);
-                    const uint32_t idx4 = (dP + 0x04040404u - dW) << 2;
-                    const uint32_t T0 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4440));
-                    const uint32_t T1 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4441));
-                    const uint32_t T2 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4442));
-                    const uint32_t T3 = *reinterpret_cast<const uint32_t *>(thr_bytes + __byte_perm(idx4, 0, 0x4443));
-                    uint32_t sel = 0x3210u;
-                    sel += ((uint32_t)px < T0) ? 0x4u : 0u;
-                    sel += ((uint32_t)py < T1) ? 0x40u : 0u;
-                    sel += ((uint32_t)pz < T2) ? 0x400u : 0u;
-                    sel += ((uint32_t)pw < T3) ? 0x4000u : 0u;
-                    NW.v[j] = __byte_perm(Wj, P, sel);
+                    for (int p = 0; p < B; ++p) X[p] = shifted_row<0>(H[p], 0u, par, 32, 32);
+                } else {
+                    const int te = par ? (t + 1 == WPR ? 0 : t + 1) : (t == 0 ? WPR - 1 : t - 1);
+                    uint32_t Eg[BP];
+                    load_planes<BP>(Eg, oth + (y * WPR + te) * BP);
+                    const int nb = t == WPR - 1 ? nb_last : 32;
+                    const int nbe = te == WPR - 1 ? nb_last : 32;
+#pragma unroll
+                    for (int p = 0; p < B; ++p) X[p] = shifted_row<MODE>(H[p], Eg[p], par, nb, nbe);
+                    vmask = valid_mask(t, WPR, nb_last);
                 }
-                NW.store(own + row + t0);
+
+                // proposal: direction sigma = Z_0, offset bits u = Z_1..Z_{B-1}
+                const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
+                const uint32_t w = (uint32_t)(y * WPR + t);
+                uint32_t Z[8];
+                {
+                    const uint4 z = philox10_rk(make_uint4(w, ctr1, (uint32_t)G.step, slot), rk0, rk1);
+                    Z[0] = z.x;
+                    Z[1] = z.y;
+                    Z[2] = z.z;
+                    Z[3] = z.w;
+                }
+                if constexpr (B > 4) {
+                    const uint4 z = philox10_rk(make_uint4(w, ctr1 | 1u, (uint32_t)G.step, slot), rk0, rk1);
+                    Z[4] = z.x;
+                    Z[5] = z.y;
+                    Z[6] = z.z;
+                    Z[7] = z.w;
+                }
+                const uint32_t sg = Z[0];
+                // S = s + 1 + u (sigma = 0) or s - 1 - u (sigma = 1), B + 1 bits
+                uint32_t S[B + 1];
+                uint32_t cy = ~sg;
+#pragma unroll
+                for (int p = 0; p < B; ++p) {
+                    const uint32_t x = (p < B - 1) ? (Z[p + 1] ^ sg) : sg;
+                    full_add(W[p], x, cy, S[p], cy);
+                }
+                S[B] = sg ^ cy;
+                // Tq = S - q (sigma = 0) or S + q (sigma = 1); take Tq where S >= q
+                // (sigma = 0) or S < 0 (sigma = 1)
+                uint32_t Tq[B + 1];
+                uint32_t cz = 0;
+#pragma unroll
+                for (int p = 0; p <= B; ++p) {
+                    const uint32_t yb = (sg & qm[p]) | (~sg & nqm[p]);
+                    full_add(S[p], yb, cz, Tq[p], cz);
+                }
+                const uint32_t take = (sg & S[B]) | (~sg & ~Tq[B]);
+                uint32_t P[BP];
+#pragma unroll
+                for (int p = 0; p < BP; ++p) P[p] = p < B ? ((take & Tq[p]) | (~take & S[p])) : 0u;
+
+                // dE + 4 = #(neighbours equal to s) + #(neighbours different from s')
+                const uint32_t a1 = ~differ<B, BP>(W, U), a2 = ~differ<B, BP>(W, D);
+                const uint32_t a3 = ~differ<B, BP>(W, H), a4 = ~differ<B, BP>(W, X);
+                const uint32_t b1 = differ<B, BP>(P, U), b2 = differ<B, BP>(P, D);
+                const uint32_t b3 = differ<B, BP>(P, H), b4 = differ<B, BP>(P, X);
+                uint32_t s1, k1, s2, k2, s3, k3, s5, k5;
+                full_add(a1, a2, a3, s1, k1);
+                full_add(a4, b1, b2, s2, k2);
+                full_add(b3, b4, s1, s3, k3);
+                const uint32_t c0 = s2 ^ s3, k4 = s2 & s3;
+                full_add(k1, k2, k3, s5, k5);
+                const uint32_t c1 = s5 ^ k4, k6 = s5 & k4;
+                const uint32_t c2 = k5 ^ k6, c3 = k5 & k6;
+                const uint32_t pos = vmask & (c3 | (c2 & (c1 | c0)));  // dE > 0
+                const uint32_t e1 = c3 | (c1 & c0);                     // dE >= 3
+
+                // acceptance: dE <= 0 always; otherwise v < T[dE], bit by bit
+                uint32_t acc = live ? (vmask & ~pos) : 0u;
+                uint32_t und = live ? pos : 0u;
+                if (any_full) {
+                    const uint32_t tj = threshold_bits(s_tab[32], c0, e1);
+                    acc |= und & tj;
+                    und &= ~tj;
+                }
+                bool more = true;
+                int j = 0;
+                auto plane = [&](uint32_t v) {
+                    if (more && j < 32) {
+                        more = __any_sync(0xFFFFFFFFu, und) != 0;
+                        if (more) {
+                            const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
+                            acc |= und & ~v & tj;
+                            und &= ~(v ^ tj);
+                        }
+                        ++j;
+                    }
+                };
+                if constexpr (BP < 4) {
+#pragma unroll
+                    for (int wi = BP; wi < 4; ++wi) plane(Z[wi]);
+                }
+                for (uint32_t ch = (uint32_t)((BP + 3) / 4); more && j < 32; ++ch) {
+                    const uint4 z = philox10_rk(make_uint4(w, ctr1 | ch, (uint32_t)G.step, slot), rk0, rk1);
+                    plane(z.x);
+                    plane(z.y);
+                    plane(z.z);
+                    plane(z.w);
+                }
+                if (live) {
+#pragma unroll
+                    for (int p = 0; p < B; ++p) W[p] = (acc & P[p]) | (~acc & W[p]);
+                    store_planes<BP>(own, W);
+                }
             }
             __syncthreads();
         }
@@ -260,50 +388,65 @@ __device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 
 
     // measurements: one warp per replica, or the whole block per replica when
     // the block holds fewer replicas than warps
-    if (2 * nrep > nwarps) {
-        for (int r = warp; r < nrep; r += nwarps) {
-            const uint32_t *rep = sw + r * WPR;
-            int agree = 0;
-            for (int w = lane; w < WPC; w += 32) {
-                const int y = w / L8;
-                const int t = w - y * L8;
-                const Neighbours nb = load_neighbours(rep + WPC, L, L8, y, t, y & 1);
-                const uint32_t d = count_differ(rep[w], nb.up, nb.down, nb.same, nb.shifted);
-                agree += 16 - (int)((d * 0x01010101u) >> 24);
+    const bool per_warp = 2 * nrep > nwarps;
+    const int n_owner = per_warp ? nwarps : 1;
+    const int owner = per_warp ? warp : 0;
+    const int stride = per_warp ? 32 : (int)blockDim.x;
+    const int me = per_warp ? lane : tid;
+    for (int r0 = 0; r0 < nrep; r0 += n_owner) {
+        const int r = r0 + owner;
+        const bool have = r < nrep;
+        const uint32_t *rep = sw + (have ? r : 0) * RW;
+        int agree = 0;
+        if (have) {
+            // each bond has one colour-0 end: count equal neighbours of colour-0 sites
+            for (int it = me; it < IPC; it += stride) {
+                const int y = MODE == 0 ? it : it / WPR;
+                const int t = MODE == 0 ? 0 : it - y * WPR;
+                const uint32_t *oth = rep + IPC * BP;
+                const int yu = (y == 0) ? L - 1 : y - 1;
+                const int yd = (y == L - 1) ? 0 : y + 1;
+                const int par = y & 1;
+                uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
+                load_planes<BP>(W, rep + (y * WPR + t) * BP);
+                load_planes<BP>(U, oth + (yu * WPR + t) * BP);
+                load_planes<BP>(D, oth + (yd * WPR + t) * BP);
+                load_planes<BP>(H, oth + (y * WPR + t) * BP);
+                uint32_t vmask = 0xFFFFFFFFu;
+                if constexpr (MODE == 0) {
+#pragma unroll
+                    for (int p = 0; p < B; ++p) X[p] = shifted_row<0>(H[p], 0u, par, 32, 32);
+                } else {
+                    const int te = par ? (t + 1 == WPR ? 0 : t + 1) : (t == 0 ? WPR - 1 : t - 1);
+                    uint32_t Eg[BP];
+                    load_planes<BP>(Eg, oth + (y * WPR + te) * BP);
+                    const int nb = t == WPR - 1 ? nb_last : 32;
+                    const int nbe = te == WPR - 1 ? nb_last : 32;
+#pragma unroll
+                    for (int p = 0; p < B; ++p) X[p] = shifted_row<MODE>(H[p], Eg[p], par, nb, nbe);
+                    vmask = valid_mask(t, WPR, nb_last);
+                }
+                agree += __popc(vmask & ~differ<B, BP>(W, U)) + __popc(vmask & ~differ<B, BP>(W, D)) +
+                         __popc(vmask & ~differ<B, BP>(W, H)) + __popc(vmask & ~differ<B, BP>(W, X));
             }
-            agree = __reduce_add_sync(0xFFFFFFFFu, agree);
-            int best = 0;
-            for (int s = 0; s < G.q; ++s) {
-                const uint32_t S4 = (uint32_t)s * 0x01010101u;
-                int cnt = 0;
-                for (int w = lane; w < WPR; w += 32) cnt += 4 - __popc(differ_bits(rep[w], S4));
-                cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-                best = max(best, cnt);
-            }
-            if (lane == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
         }
-    } else {
-        for (int r = 0; r < nrep; ++r) {
-            const uint32_t *rep = sw + r * WPR;
-            int agree = 0;
-            for (int w = tid; w < WPC; w += blockDim.x) {
-                const int y = w / L8;
-                const int t = w - y * L8;
-                const Neighbours nb = load_neighbours(rep + WPC, L, L8, y, t, y & 1);
-                const uint32_t d = count_differ(rep[w], nb.up, nb.down, nb.same, nb.shifted);
-                agree += 16 - (int)((d * 0x01010101u) >> 24);
+        agree = per_warp ? __reduce_add_sync(0xFFFFFFFFu, agree) : block_sum_int(agree);
+        int best = 0;
+        for (int s = 0; s < q; ++s) {
+            int cnt = 0;
+            if (have) {
+                for (int it = me; it < 2 * IPC; it += stride) {
+                    const int t = MODE == 0 ? 0 : it % WPR;
+                    uint32_t W[BP];
+                    load_planes<BP>(W, rep + it * BP);
+                    const uint32_t vmask = MODE == 0 ? 0xFFFFFFFFu : valid_mask(t, WPR, nb_last);
+                    cnt += __popc(vmask & equal_state<B, BP>(W, s));
+                }
             }
-            agree = block_sum_int(agree);
-            int best = 0;
-            for (int s = 0; s < G.q; ++s) {
-                const uint32_t S4 = (uint32_t)s * 0x01010101u;
-                int cnt = 0;
-                for (int w = tid; w < WPR; w += blockDim.x) cnt += 4 - __popc(differ_bits(rep[w], S4));
-                cnt = block_sum_int(cnt);
-                best = max(best, cnt);
-            }
-            if (tid == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
+            cnt = per_warp ? __reduce_add_sync(0xFFFFFFFFu, cnt) : block_sum_int(cnt);
+            best = max(best, cnt);
         }
+        if (have && me == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
     }
     group_families(G);
     __syncthreads();
@@ -311,98 +454,7 @@ __device__ __forceinline__ void sweep_group_rows(const Group &G, int Lrt, uint4 
         for (int i = tid; i < nrep * UPR; i += blockDim.x) {
             const int r = i / UPR;
             const int o = i - r * UPR;
-            reinterpret_cast<uint4 *>(G.out + (size_t)(first + r) * N)[o] = smem4[r * UPR + o];
-        }
-    }
-    __syncthreads();
-}
-
-// Per-site body for any even L (used where L % 8 != 0), same random-number
-// assignment as the row-segment body.
-__device__ __forceinline__ void sweep_group_sites(const Group &G, int L, uint4 *smem4, const uint32_t *s_thr,
-                                                  const uint32_t *rk0, const uint32_t *rk1, long long &sE,
-                                                  long long &sE2, long long &sM)
-{
-    uint8_t *sb = reinterpret_cast<uint8_t *>(smem4);
-    const int L2 = L / 2;
-    const int N = L * L;
-    const int NH = N / 2;
-    const int NP = (N + 15) & ~15;  // padded bytes per replica in shared memory
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const uint32_t qm1 = (uint32_t)(G.q - 1);
-    const int first = G.first, nrep = G.nrep;
-
-    for (int i = tid; i < nrep * N; i += blockDim.x) {
-        const int r = i / N;
-        const int o = i - r * N;
-        const int slot = first + r;
-        const int src = G.gather ? G.parent[slot] : slot;
-        sb[r * NP + o] = G.in[(size_t)src * N + o];
-    }
-    __syncthreads();
-    for (int k = 0; k < G.theta; ++k) {
-        for (int c = 0; c < 2; ++c) {
-            const uint32_t ctr1 = DOM_SWEEP | (uint32_t)(2 * k + c);
-            for (int i = tid; i < nrep * NH; i += blockDim.x) {
-                const int r = i / NH;
-                const int h = i - r * NH;
-                const int y = h / L2;
-                const int m = h - y * L2;
-                const int p = (y + c) & 1;
-                uint8_t *own = sb + r * NP + c * NH;
-                const uint8_t *oth = sb + r * NP + (c ^ 1) * NH;
-                const int yu = (y == 0) ? L - 1 : y - 1;
-                const int yd = (y == L - 1) ? 0 : y + 1;
-                const int mo = p ? (m + 1 == L2 ? 0 : m + 1) : (m == 0 ? L2 - 1 : m - 1);
-                const int n0 = oth[yu * L2 + m], n1 = oth[yd * L2 + m], n2 = oth[y * L2 + m], n3 = oth[y * L2 + mo];
-                const int s = own[h];
-                const uint4 rw = philox10_rk(
-                    make_uint4((uint32_t)h >> 2, ctr1, (uint32_t)G.step, (uint32_t)(first + r) | G.stream_hi), rk0, rk1);
-                const uint32_t u = pick_word(rw, h & 3);
-                int prop = s + 1 + (int)__umulhi(u, qm1);
-                if (prop >= G.q) prop -= G.q;
-                const int ns = (n0 == s) + (n1 == s) + (n2 == s) + (n3 == s);
-                const int np = (n0 == prop) + (n1 == prop) + (n2 == prop) + (n3 == prop);
-                if (u * qm1 < s_thr[ns - np + 4]) own[h] = (uint8_t)prop;
-            }
-            __syncthreads();
-        }
-    }
-    for (int r = warp; r < nrep; r += nwarps) {
-        const uint8_t *rep = sb + r * NP;
-        int agree = 0;
-        for (int h = lane; h < NH; h += 32) {
-            const int y = h / L2;
-            const int m = h - y * L2;
-            const int p = y & 1;
-            const uint8_t *oth = rep + NH;
-            const int yu = (y == 0) ? L - 1 : y - 1;
-            const int yd = (y == L - 1) ? 0 : y + 1;
-            const int mo = p ? (m + 1 == L2 ? 0 : m + 1) : (m == 0 ? L2 - 1 : m - 1);
-            const int s = rep[h];
-            agree += (oth[yu * L2 + m] == s) + (oth[yd * L2 + m] == s) + (oth[y * L2 + m] == s) +
-                     (oth[y * L2 + mo] == s);
-        }
-        agree = __reduce_add_sync(0xFFFFFFFFu, agree);
-        int best = 0;
-        for (int s = 0; s < G.q; ++s) {
-            int cnt = 0;
-            for (int i = lane; i < N; i += 32) cnt += rep[i] == s;
-            cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-            best = max(best, cnt);
-        }
-        if (lane == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
-    }
-    group_families(G);
-    __syncthreads();
-    if (G.write_back) {
-        for (int i = tid; i < nrep * N; i += blockDim.x) {
-            const int r = i / N;
-            const int o = i - r * N;
-            G.out[(size_t)(first + r) * N + o] = sb[r * NP + o];
+            reinterpret_cast<uint4 *>(G.out + (size_t)(first + r) * RW)[o] = smem4[r * UPR + o];
         }
     }
     __syncthreads();
@@ -493,38 +545,70 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *scratch32, int *
 }
 
 // ===========================================================================
-// Initial population (Sec. 2 step 1; Sec. 5 Eq. 6) for quads [i0, i1) of the
-// flattened (slot, site / 4) index.
+// Initial populations (Sec. 2 step 1; Sec. 5 Eq. 6)
 // ===========================================================================
-__device__ __forceinline__ void init_quad(uint8_t *spins, int32_t *anc, int q, int L, long long i, uint32_t k0,
+
+// One site word (32 columns of one colour and row) of one replica; i indexes
+// (slot, colour, row, word).  Random start: canonical site i_s = y L + x takes
+// floor(Z q / 2^32), Z = word (i_s & 3) of the Philox call with counter
+// (i_s >> 2, INIT, 0, slot | stream).  Ground start: every site of the replica
+// in the state floor(Z q / 2^32), Z = word (slot & 3) of counter
+// (slot >> 2, GROUND, 0, stream).
+__device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, int L, long long i, uint32_t k0,
                                           uint32_t k1, uint32_t stream_hi, int ground)
 {
-    const int N = L * L;
-    const int NH = N / 2;
-    const int L2 = L / 2;
-    const int slot = (int)(i / (N / 4));
-    const int quad = (int)(i - (long long)slot * (N / 4));
-    uint8_t *rep = spins + (size_t)slot * N;
-    uint8_t v[4];
+    const int B = state_bits(q);
+    const int BP = plane_stride(B);
+    const int WPR = row_words(L);
+    const int nb_last = L / 2 - 32 * (WPR - 1);
+    const int IPR = 2 * L * WPR;  // site words per replica
+    const int slot = (int)(i / IPR);
+    const int rem = (int)(i - (long long)slot * IPR);
+    const int c = rem / (L * WPR);
+    const int rem2 = rem - c * L * WPR;
+    const int y = rem2 / WPR, t = rem2 - y * WPR;
+    const int nb = t == WPR - 1 ? nb_last : 32;
+    uint32_t planes[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     if (ground) {
         const uint4 w = philox10(make_uint4((uint32_t)slot >> 2, DOM_GROUND, 0u, stream_hi), k0, k1);
-        const uint8_t alpha = (uint8_t)__umulhi(pick_word(w, slot & 3), (uint32_t)q);
-        v[0] = v[1] = v[2] = v[3] = alpha;
+        const uint32_t alpha = __umulhi(pick_word(w, slot & 3), (uint32_t)q);
+        const uint32_t vm = nb == 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+        for (int p = 0; p < B; ++p) planes[p] = ((alpha >> p) & 1u) ? vm : 0u;
     } else {
-        const uint4 w = philox10(make_uint4((uint32_t)quad, DOM_INIT, 0u, (uint32_t)slot | stream_hi), k0, k1);
-        v[0] = (uint8_t)__umulhi(w.x, (uint32_t)q);
-        v[1] = (uint8_t)__umulhi(w.y, (uint32_t)q);
-        v[2] = (uint8_t)__umulhi(w.z, (uint32_t)q);
-        v[3] = (uint8_t)__umulhi(w.w, (uint32_t)q);
+        int last = -1;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        for (int b = 0; b < nb; ++b) {
+            const int x = 2 * (32 * t + b) + ((y + c) & 1);
+            const int site = y * L + x;
+            if ((site >> 2) != last) {
+                last = site >> 2;
+                w = philox10(make_uint4((uint32_t)last, DOM_INIT, 0u, (uint32_t)slot | stream_hi), k0, k1);
+            }
+            const uint32_t s = __umulhi(pick_word(w, site & 3), (uint32_t)q);
+            for (int p = 0; p < B; ++p) planes[p] |= ((s >> p) & 1u) << b;
+        }
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int site = 4 * quad + j;  // canonical y*L + x
-        const int y = site / L, x = site - y * L;
-        const int c = (x + y) & 1;
-        rep[c * NH + y * L2 + (x >> 1)] = v[j];
-    }
-    if (quad == 0 && anc) anc[slot] = slot;
+    uint32_t *dst = spins + (size_t)slot * (IPR * BP) + (size_t)rem * BP;
+    for (int p = 0; p < BP; ++p) dst[p] = planes[p];
+    if (rem == 0 && anc) anc[slot] = slot;
+}
+
+// State of canonical site i (= r N + y L + x) of a multi-spin-coded population.
+__device__ __forceinline__ uint8_t canonical_state(const uint32_t *spins, int q, int L, long long i)
+{
+    const int N = L * L;
+    const int B = state_bits(q);
+    const int BP = plane_stride(B);
+    const int WPR = row_words(L);
+    const long long r = i / N;
+    const int site = (int)(i - r * N);
+    const int y = site / L, x = site - y * L;
+    const int c = (x + y) & 1;
+    const int m = x >> 1;
+    const uint32_t *w = spins + (size_t)r * (2 * L * WPR * BP) + (size_t)(((c * L + y) * WPR + (m >> 5)) * BP);
+    uint32_t s = 0;
+    for (int p = 0; p < B; ++p) s |= ((w[p] >> (m & 31)) & 1u) << p;
+    return (uint8_t)s;
 }
 
 // ===========================================================================

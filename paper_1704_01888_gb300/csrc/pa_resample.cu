@@ -3,7 +3,8 @@
 // arXiv:1704.01888).
 //
 //   k_init      Sec. 2 step 1 (uniform spins at beta_0 = 0) or Sec. 5 Eq. 6
-//               (a uniformly chosen ground state per replica).
+//               (a uniformly chosen ground state per replica), written in the
+//               multi-spin-coded layout.
 //   k_weights   Sec. 2 step 2: reference energy, Boltzmann factors
 //               w_k = exp(-dbeta (E_k - E_ref)) per energy bin, their
 //               histogram-weighted sum S and ln Q_i = -dbeta E_ref + ln(S/R_{i-1}).
@@ -24,13 +25,13 @@ namespace {
 
 constexpr int kBlock = 1024;
 
-__global__ void k_init(uint8_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
+__global__ void k_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
                        uint32_t stream_hi, int ground)
 {
-    const long long total = (long long)R * (L * L / 4);
+    const long long total = (long long)R * (2 * L * row_words(L));
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x)
-        dev::init_quad(spins, anc, q, L, i, k0, k1, stream_hi, ground);
+        dev::init_item(spins, anc, q, L, i, k0, k1, stream_hi, ground);
 }
 
 __global__ void __launch_bounds__(kBlock) k_weights(const int32_t *hist, int nbins, double dbeta, DevState *st,
@@ -68,20 +69,12 @@ __global__ void __launch_bounds__(kBlock) k_finalize(DevState *st, unsigned long
     dev::finalize_body(st, acc, fam, R0, obs, beta, q, N, gathered, resampled, s_d, s_l);
 }
 
-__global__ void k_to_canonical(const uint8_t *spins, uint8_t *out, int L, long long count)
+__global__ void k_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, long long count)
 {
-    const int N = L * L;
-    const int NH = N / 2;
-    const int L2 = L / 2;
-    const long long total = count * N;
+    const long long total = count * L * L;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / N;
-        const int site = (int)(i - r * N);
-        const int y = site / L, x = site - y * L;
-        const int c = (x + y) & 1;
-        out[i] = spins[r * N + c * NH + y * L2 + (x >> 1)];
-    }
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = dev::canonical_state(spins, q, L, i);
 }
 
 int grid_for(long long work, int threads)
@@ -94,10 +87,10 @@ int grid_for(long long work, int threads)
 
 }  // namespace
 
-cudaError_t launch_init(uint8_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
+cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
                         uint32_t stream_hi, int ground, cudaStream_t s)
 {
-    const long long work = (long long)R * (L * L / 4);
+    const long long work = (long long)R * (2 * L * row_words(L));
     k_init<<<grid_for(work, 256), 256, 0, s>>>(spins, anc, q, L, R, k0, k1, stream_hi, ground);
     bump_launch_count(1);
     return cudaGetLastError();
@@ -126,9 +119,9 @@ cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam,
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_canonical(const uint8_t *spins, uint8_t *out, int L, int64_t count, cudaStream_t s)
+cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count, cudaStream_t s)
 {
-    k_to_canonical<<<grid_for(count * L * L, 256), 256, 0, s>>>(spins, out, L, count);
+    k_to_canonical<<<grid_for(count * L * L, 256), 256, 0, s>>>(spins, out, q, L, count);
     bump_launch_count(1);
     return cudaGetLastError();
 }

@@ -9,14 +9,13 @@
 // temperature step.  Blocks are persistent: they stride over groups of rpb
 // replicas until the device-side population size is covered.
 //
-// Inner loop (lattices with L % 8 == 0): one thread updates four consecutive
-// same-colour sites held in one 32-bit word.  Their neighbours are the
-// aligned words of the other colour in the rows above and below and in the
-// same row, plus that row word shifted by one byte.  Neighbour agreement is
-// counted four bytes at a time (SWAR).  Each site takes one 32-bit Philox
-// word u: the high and low halves of u (q-1) are its proposal offset and its
-// acceptance uniform.  Lattices with other even L use a per-site kernel with
-// the same random-number assignment, so both give identical results.
+// Spins are multi-spin coded: the states of 32 same-colour sites of a row sit
+// in B bit planes (B = ceil(log2 q)), and each thread updates such a site
+// word with 32-bit logic: the proposal by ripple-carry additions over the
+// planes, the energy change by bitwise equality tests and a carry-save count,
+// the acceptance by a most-significant-bit-first comparison of random bits
+// with the thresholds (the body is dev::sweep_group_bits).  One kernel is
+// compiled per B and row geometry.
 #include "pa_kernels.cuh"
 
 namespace pa {
@@ -48,14 +47,15 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
     return G;
 }
 
-// Row-segment kernel (L % 8 == 0): persistent blocks stride over groups of
-// rpb replicas of the current population.
-template <int LT, int S>
-__global__ void __launch_bounds__(1024) k_sweep_rows(const SweepArgs a)
+// Persistent blocks stride over groups of rpb replicas of the current
+// population.  B: bits per state; MODE: 0 for L = 64, 1 for L a multiple of
+// 64, 2 otherwise (rows padded to whole words).
+template <int B, int MODE>
+__global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
 {
     extern __shared__ uint4 smem4[];
-    __shared__ uint32_t s_thr[9];
-    if (threadIdx.x < 9) s_thr[threadIdx.x] = a.thr[threadIdx.x];
+    __shared__ uint4 s_tab[33];
+    dev::build_threshold_table(s_tab, a.thr);
     DevState *st = a.st;
     if (st->err) return;
     const int parity = st->parity;
@@ -64,26 +64,8 @@ __global__ void __launch_bounds__(1024) k_sweep_rows(const SweepArgs a)
     for (int g = blockIdx.x; g * a.rpb < R; g += gridDim.x) {
         const int first = g * a.rpb;
         const dev::Group G = make_group(a, parity, first, min(a.rpb, R - first));
-        dev::sweep_group_rows<LT, S>(G, a.L, smem4, s_thr, a.rk0, a.rk1, sE, sE2, sM);
-    }
-    if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(a.acc, sE, sE2, sM);
-}
-
-// Site kernel: any even L (used where L % 8 != 0).
-__global__ void __launch_bounds__(1024) k_sweep_sites(const SweepArgs a)
-{
-    extern __shared__ uint4 smem4[];
-    __shared__ uint32_t s_thr[9];
-    if (threadIdx.x < 9) s_thr[threadIdx.x] = a.thr[threadIdx.x];
-    DevState *st = a.st;
-    if (st->err) return;
-    const int parity = st->parity;
-    const int R = a.gather ? st->pop_next : st->pop;
-    long long sE = 0, sE2 = 0, sM = 0;
-    for (int g = blockIdx.x; g * a.rpb < R; g += gridDim.x) {
-        const int first = g * a.rpb;
-        const dev::Group G = make_group(a, parity, first, min(a.rpb, R - first));
-        dev::sweep_group_sites(G, a.L, smem4, s_thr, a.rk0, a.rk1, sE, sE2, sM);
+        dev::sweep_group_bits<B, MODE>(G, a.L, reinterpret_cast<uint32_t *>(smem4), s_tab, a.rk0, a.rk1, sE, sE2,
+                                       sM);
     }
     if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(a.acc, sE, sE2, sM);
 }
@@ -99,35 +81,36 @@ cudaError_t prepare(KernelFnPtr kernel)
     return e;
 }
 
-KernelFnPtr pick_kernel(int L)
+template <int MODE>
+KernelFnPtr pick_bits(int B)
 {
-    if (L % 8 != 0) return k_sweep_sites;
-    switch (L) {
-    case 16: return k_sweep_rows<16, 2>;
-    case 32: return k_sweep_rows<32, 4>;
-    case 48: return k_sweep_rows<48, 2>;
-    case 64: return k_sweep_rows<64, 4>;
-    case 128: return k_sweep_rows<128, 4>;
-    case 256: return k_sweep_rows<256, 4>;
-    default:
-        if ((L / 8) % 4 == 0) return k_sweep_rows<0, 4>;
-        if ((L / 8) % 2 == 0) return k_sweep_rows<0, 2>;
-        return k_sweep_rows<0, 1>;
+    switch (B) {
+    case 1: return k_sweep<1, MODE>;
+    case 2: return k_sweep<2, MODE>;
+    case 3: return k_sweep<3, MODE>;
+    case 4: return k_sweep<4, MODE>;
+    case 5: return k_sweep<5, MODE>;
+    case 6: return k_sweep<6, MODE>;
+    default: return k_sweep<7, MODE>;
     }
+}
+
+KernelFnPtr pick_kernel(int q, int L)
+{
+    const int B = state_bits(q);
+    if (L == 64) return pick_bits<0>(B);
+    if (L % 64 == 0) return pick_bits<1>(B);
+    return pick_bits<2>(B);
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int L, int rpb)
-{
-    const size_t N = (size_t)L * L;
-    return (size_t)rpb * ((N + 15) & ~(size_t)15);
-}
+size_t sweep_smem_bytes(int q, int L, int rpb) { return (size_t)rpb * replica_bytes(q, L); }
 
-int sweep_max_blocks_per_sm(int L, int rpb, int threads)
+int sweep_max_blocks_per_sm(int q, int L, int rpb, int threads)
 {
-    KernelFnPtr k = pick_kernel(L);
-    const size_t smem = sweep_smem_bytes(L, rpb);
+    KernelFnPtr k = pick_kernel(q, L);
+    const size_t smem = sweep_smem_bytes(q, L, rpb);
     if (prepare(k) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
@@ -136,8 +119,8 @@ int sweep_max_blocks_per_sm(int L, int rpb, int threads)
 
 cudaError_t launch_sweep(const SweepArgs &a, int threads, int grid, cudaStream_t s)
 {
-    KernelFnPtr k = pick_kernel(a.L);
-    const size_t smem = sweep_smem_bytes(a.L, a.rpb);
+    KernelFnPtr k = pick_kernel(a.q, a.L);
+    const size_t smem = sweep_smem_bytes(a.q, a.L, a.rpb);
     k<<<grid, threads, smem, s>>>(a);
     bump_launch_count(1);
     return cudaGetLastError();

@@ -54,9 +54,10 @@ def test_status_strings_and_validation_without_gpu():
         cfg = pa.Config(bad["q"], bad["L"], bad["R"], bad.get("R_cap", 0), 1, 0, 0, 0.0, 0, bad.get("stream", 0))
         assert lib.pa_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == pa.PA_ERR_INVALID
         assert not ctx.value
-    # a lattice larger than a block's shared memory: L = 454 > sqrt(204800)
-    for L in (454, 1024):
-        cfg = pa.Config(10, L, 10, 0, 1, 0, 0, 0.0, 0, 0)
+    # replicas whose bit planes exceed a block's shared memory (204800 bytes):
+    # q = 128 (8 planes) at L = 450, q = 10 (4 planes) at L = 642 and 1024
+    for q, L in ((128, 450), (10, 642), (10, 1024)):
+        cfg = pa.Config(q, L, 10, 0, 1, 0, 0, 0.0, 0, 0)
         assert lib.pa_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == pa.PA_ERR_TOO_LARGE
         assert not ctx.value
     assert lib.pa_kernel_launch_count() == 0
