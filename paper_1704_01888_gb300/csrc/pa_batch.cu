@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kB) k_batch_scatter(const BatchArgs b)
 __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
 {
     extern __shared__ uint4 smem4[];
-    __shared__ uint4 s_tab[33];
+    __shared__ uint4 s_tab[dev::kThresholdEntries];
     __shared__ int s_prefix[kMaxRuns + 1];
     const int i = *b.step_counter;
     if (threadIdx.x == 0) {

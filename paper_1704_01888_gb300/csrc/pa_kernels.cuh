@@ -170,18 +170,24 @@ __device__ __forceinline__ void group_families(const Group &G)
 
 // Shared-memory table of the acceptance thresholds for the bitwise
 // comparison v < T[dE]: entry j (0..31) holds, for d = 1..4, all ones where
-// bit 31 - j of T[d] is set; entry 32 marks T[d] = 2^32.  The block's threads
-// share the 33 entries (blocks may have as few as 32 threads).
+// bit 31 - j of T[d] is set; entries 32..39 are zero (planes past the last bit
+// of v, which the loop may draw when it takes acceptance words four at a time:
+// a zero threshold bit never accepts); entry 40 marks T[d] = 2^32.  The
+// block's threads share the 41 entries (blocks may have as few as 32 threads).
+constexpr int kThresholdEntries = 41;
+constexpr int kThresholdFull = 40;
 __device__ __forceinline__ void build_threshold_table(uint4 *tab, const Thresholds &th)
 {
     auto m = [](uint32_t bit) { return bit ? 0xFFFFFFFFu : 0u; };
-    for (int j = threadIdx.x; j < 33; j += blockDim.x) {
+    for (int j = threadIdx.x; j < kThresholdEntries; j += blockDim.x) {
         if (j < 32) {
             const int b = 31 - j;
             tab[j] = make_uint4(m((th.T[0] >> b) & 1u), m((th.T[1] >> b) & 1u), m((th.T[2] >> b) & 1u),
                                 m((th.T[3] >> b) & 1u));
+        } else if (j < kThresholdFull) {
+            tab[j] = make_uint4(0u, 0u, 0u, 0u);
         } else {
-            tab[32] = make_uint4(m(th.full & 1u), m(th.full & 2u), m(th.full & 4u), m(th.full & 8u));
+            tab[kThresholdFull] = make_uint4(m(th.full & 1u), m(th.full & 2u), m(th.full & 4u), m(th.full & 8u));
         }
     }
 }
@@ -246,7 +252,8 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
         qm[p] = ((q >> p) & 1) ? 0xFFFFFFFFu : 0u;
         nqm[p] = ((((1 << (B + 1)) - q) >> p) & 1) ? 0xFFFFFFFFu : 0u;
     }
-    const bool any_full = s_tab[32].x | s_tab[32].y | s_tab[32].z | s_tab[32].w;
+    const bool any_full = s_tab[kThresholdFull].x | s_tab[kThresholdFull].y | s_tab[kThresholdFull].z |
+                          s_tab[kThresholdFull].w;
     const int total = nrep * IPC;
 
     for (int k = 0; k < G.theta; ++k) {
@@ -348,33 +355,31 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 uint32_t acc = live ? (vmask & ~pos) : 0u;
                 uint32_t und = live ? pos : 0u;
                 if (any_full) {
-                    const uint32_t tj = threshold_bits(s_tab[32], c0, e1);
+                    const uint32_t tj = threshold_bits(s_tab[kThresholdFull], c0, e1);
                     acc |= und & tj;
                     und &= ~tj;
                 }
-                bool more = true;
-                int j = 0;
-                auto plane = [&](uint32_t v) {
-                    if (more && j < 32) {
-                        more = __any_sync(0xFFFFFFFFu, und) != 0;
-                        if (more) {
-                            const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
-                            acc |= und & ~v & tj;
-                            und &= ~(v ^ tj);
-                        }
-                        ++j;
-                    }
+                auto plane = [&](uint32_t v, int j) {
+                    const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
+                    acc |= und & ~v & tj;
+                    und &= ~(v ^ tj);
                 };
                 if constexpr (BP < 4) {
+                    if (__any_sync(0xFFFFFFFFu, und)) {
 #pragma unroll
-                    for (int wi = BP; wi < 4; ++wi) plane(Z[wi]);
+                        for (int wi = BP; wi < 4; ++wi) plane(Z[wi], wi - BP);
+                    }
                 }
-                for (uint32_t ch = (uint32_t)((BP + 3) / 4); more && j < 32; ++ch) {
-                    const uint4 z = philox10_rk(make_uint4(w, ctr1 | ch, (uint32_t)G.step, slot), rk0, rk1);
-                    plane(z.x);
-                    plane(z.y);
-                    plane(z.z);
-                    plane(z.w);
+                constexpr int fc = (BP + 3) / 4;
+#pragma unroll 1
+                for (int ch = fc; ch < fc + 8; ++ch) {
+                    if (!__any_sync(0xFFFFFFFFu, und)) break;
+                    const uint4 za = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
+                    const int j0 = 4 * ch - BP;
+                    plane(za.x, j0);
+                    plane(za.y, j0 + 1);
+                    plane(za.z, j0 + 2);
+                    plane(za.w, j0 + 3);
                 }
                 if (live) {
 #pragma unroll

@@ -54,7 +54,7 @@ template <int B, int MODE>
 __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
 {
     extern __shared__ uint4 smem4[];
-    __shared__ uint4 s_tab[33];
+    __shared__ uint4 s_tab[dev::kThresholdEntries];
     dev::build_threshold_table(s_tab, a.thr);
     DevState *st = a.st;
     if (st->err) return;
