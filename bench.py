@@ -34,13 +34,41 @@ from paper_1704_01888_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "spin-flip attempts/ns & PA steps/s, q=10 L=64 R=1e5; batched vs plain, %roofline"
 UNIT = "attempts/ns"
-# Algorithmic integer issue slots per Metropolis attempt, counted for a scalar
-# implementation with a 64-bit product as two slots: a quarter of a
-# Philox4x32-10 call (10 rounds x (2 products x 2 + 2 three-input xors) = 60
-# per call, 15 per attempt), the product u (q - 1) (2), the proposal modulo q
-# (2), eight neighbour equality tests with their two sums (9), the threshold
-# compare and select (2): 30 in all.  The issue roofline divides by this.
-OPS_PER_ATTEMPT = 30
+# Algorithmic integer issue slots of the multi-spin-coded Metropolis update,
+# per site word (32 same-colour sites, one attempt each) for B = ceil(log2 q)
+# bit planes, a 64-bit product counted as two slots:
+#   Philox4x32-10 words: B for the proposal, ACC_PLANES for the acceptance,
+#     a quarter call each (10 rounds x (2 products x 2 + 2 three-input xors)
+#     = 60 per call): 15 (B + ACC_PLANES);
+#   proposal s +- (1 + u) mod q: two ripple-carry adders over B and B + 1
+#     planes (3 per plane), the choice of result and its select: 7B + 4;
+#   dE class: eight B-plane equality tests, a carry-save count of the eight
+#     indicator bits (14) and the class bits (3): 8B + 17;
+#   acceptance: per plane of v, the threshold-bit select (3) and the compare
+#     update (3): 6 ACC_PLANES;  merge of the accepted proposals: B.
+# ACC_PLANES = 6: a site's comparison of v with T ends at the first differing
+# bit (geometric with mean 2), and a word of 32 such sites needs the largest
+# of 32 such depths, about log2(32) + 1.3.
+ACC_PLANES = 6
+
+
+def ops_per_word(q: int) -> int:
+    B = max(1, (q - 1).bit_length())
+    return 15 * (B + ACC_PLANES) + (7 * B + 4) + (8 * B + 17) + 6 * ACC_PLANES + B
+
+
+def ops_per_attempt(q: int) -> float:
+    return ops_per_word(q) / 32.0
+
+
+def replica_bytes(q: int, L: int) -> int:
+    """Device bytes of one replica: 2 colours x L rows x ceil(L/64) words x
+    P planes x 4 bytes, P = ceil(log2 q) rounded up to 1, 2, 4 or 8."""
+    B = max(1, (q - 1).bit_length())
+    P = 1 if B <= 1 else 2 if B <= 2 else 4 if B <= 4 else 8
+    return 2 * L * ((L + 63) // 64) * P * 4
+
+
 LANES_PER_SM_PER_CLK = 128  # 4 schedulers x 32 lanes issue one integer op each per clock
 PA_OBS_BYTES = 104
 DEVSTATE_BYTES = 48
@@ -165,7 +193,7 @@ def _sweep_sources() -> bytes:
 def _sweep_issue_active():
     """smsp__issue_active of the sweep kernel from the committed ncu summary
     (fraction of the SM issue rate), valid only while the sources are unchanged."""
-    path = os.path.join(ROOT, "profiles", "k_sweep_rows_q10-L64-R32768.md")
+    path = os.path.join(ROOT, "profiles", "k_sweep_q10-L64-R1e5.md")
     try:
         text = open(path).read()
     except OSError:
@@ -321,14 +349,15 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peaks = _peaks()
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    achieved = OPS_PER_ATTEMPT * per_launch_attempts / sweep_avg_s / 1e12
+    achieved = ops_per_attempt(w.q) * per_launch_attempts / sweep_avg_s / 1e12
     peak = sms * LANES_PER_SM_PER_CLK * f_max / 1e12
     tpr = _sweep_traffic_per_replica()
+    per_launch_replicas = per_launch_attempts / (w.N * w.theta)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": (tpr * per_launch_attempts / (w.N * w.theta)) if tpr else None,
+                "traffic": (tpr * per_launch_replicas) if tpr else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write, scaled by replicas)",
-                "algorithmic_bytes_per_launch": 2 * w.N * per_launch_attempts / (w.N * w.theta),
-                "kernel": "k_sweep_rows", "ops_per_attempt": OPS_PER_ATTEMPT,
+                "algorithmic_bytes_per_launch": 2 * replica_bytes(w.q, w.L) * per_launch_replicas,
+                "kernel": "k_sweep", "ops_per_attempt": ops_per_attempt(w.q),
                 "kernel_ms_avg": sweep_avg_s * 1e3, "kernel_share": sweep_ms / elapsed_ms,
                 "peak_basis": f"{sms} SMs x {LANES_PER_SM_PER_CLK} lanes x {f_max / 1e6:.0f} MHz (max SM clock)"}
     issue = _sweep_issue_active()

@@ -51,6 +51,8 @@ struct BatchArgs {
     const RunDev *runs;
     const StepDev *steps;  // (K_max + 1) x M
     const int32_t *step_counter;
+    int32_t *work;         // per step: next replica group to hand out (zeroed at start)
+    const int32_t *order;  // runs by decreasing estimated cost of one group
     int32_t M, total_chunks;
     long long total_items;
     uint32_t k0, k1;
@@ -132,17 +134,21 @@ __global__ void __launch_bounds__(kB) k_batch_scatter(const BatchArgs b)
                       r.nbins, r.st, s_l);
 }
 
-// One persistent launch over the replica groups of every active run.
+// One persistent launch over the replica groups of every active run.  Blocks
+// take groups from a shared counter, the groups of the costliest runs first,
+// so that the heterogeneous groups of different runs balance over the SMs.
 __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
 {
     extern __shared__ uint4 smem4[];
     __shared__ uint4 s_tab[dev::kThresholdEntries];
     __shared__ int s_prefix[kMaxRuns + 1];
+    __shared__ int s_group;
     const int i = *b.step_counter;
     if (threadIdx.x == 0) {
         int acc = 0;
-        for (int m = 0; m < b.M; ++m) {
-            s_prefix[m] = acc;
+        for (int k = 0; k < b.M; ++k) {
+            s_prefix[k] = acc;
+            const int m = b.order[k];
             const RunDev &r = b.runs[m];
             const StepDev &sp = b.steps[(size_t)i * b.M + m];
             if (sp.active && !r.st->err) {
@@ -154,18 +160,23 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
     }
     __syncthreads();
     const int total = s_prefix[b.M];
-    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_group = atomicAdd(b.work + i, 1);
+        __syncthreads();
+        const int g = s_group;
+        __syncthreads();
+        if (g >= total) break;
         int lo = 0, hi = b.M - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
             if (s_prefix[mid] <= g) lo = mid; else hi = mid - 1;
         }
-        const int m = lo;
+        const int m = b.order[lo];
         const RunDev &r = b.runs[m];
         const StepDev &sp = b.steps[(size_t)i * b.M + m];
         const int parity = r.st->parity;
         const int R = b.gather ? r.st->pop_next : r.st->pop;
-        const int first = (g - s_prefix[m]) * r.rpb;
+        const int first = (g - s_prefix[lo]) * r.rpb;
         dev::Group G;
         G.in = r.buf[parity];
         G.out = b.gather ? r.buf[parity ^ 1] : r.buf[parity];
@@ -232,6 +243,8 @@ struct pa_batch {
     uint8_t *stage = nullptr;  // canonical-layout staging for pa_batch_get_spins
     size_t stage_bytes = 0;
     int32_t *counter_d = nullptr;
+    int32_t *work_d = nullptr;   // (Kmax + 1) group counters of the sweep kernel
+    int32_t *order_d = nullptr;  // run order of the sweep kernel's groups
     std::vector<void *> allocs;
     pa::BatchArgs args{};
     int smem_budget = 65536, threads = 512, grid = 0, sms = 0;
@@ -301,6 +314,16 @@ pa_status apply_launch(pa_batch *b, int budget, int threads)
     b->smem_budget = budget;
     b->threads = threads;
     b->grid = per_sm * b->sms;
+    // groups of the costliest runs first: cost ~ replicas x sites x sweeps x (4 + bits per state)
+    std::vector<int32_t> order(b->M);
+    std::vector<double> cost(b->M);
+    for (int m = 0; m < b->M; ++m) {
+        order[m] = m;
+        const pa_config &g = b->cfg[m];
+        cost[m] = (double)b->rpb[m] * g.L * g.L * std::max(b->theta[m], 1) * (4 + pa::state_bits(g.q));
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    PB_CK(cudaMemcpyAsync(b->order_d, order.data(), sizeof(int32_t) * b->M, cudaMemcpyHostToDevice, b->stream));
     PB_CK(cudaMemcpyAsync(b->runs_d, b->runs_h.data(), sizeof(pa::RunDev) * b->M, cudaMemcpyHostToDevice, b->stream));
     PB_CK(cudaStreamSynchronize(b->stream));
     return PA_OK;
@@ -310,6 +333,7 @@ pa_status apply_launch(pa_batch *b, int budget, int threads)
 pa_status enqueue_start(pa_batch *b)
 {
     PB_CK(cudaMemsetAsync(b->counter_d, 0, sizeof(int32_t), b->stream));
+    PB_CK(cudaMemsetAsync(b->work_d, 0, sizeof(int32_t) * (size_t)(b->Kmax + 1), b->stream));
     for (int m = 0; m < b->M; ++m) {
         const pa::RunDev &r = b->runs_h[m];
         pa::DevState h{};
@@ -479,7 +503,8 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         }
     }
     if ((s = balloc(b, &b->runs_d, M)) || (s = balloc(b, &b->steps_d, steps.size())) ||
-        (s = balloc(b, &b->counter_d, 1)))
+        (s = balloc(b, &b->counter_d, 1)) || (s = balloc(b, &b->work_d, (size_t)b->Kmax + 1)) ||
+        (s = balloc(b, &b->order_d, M)))
         return fail(s);
     e = cudaMemcpy(b->steps_d, steps.data(), sizeof(pa::StepDev) * steps.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(bfail(e));
@@ -488,6 +513,8 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
     a.steps = b->steps_d;
     a.runs = b->runs_d;
     a.step_counter = b->counter_d;
+    a.work = b->work_d;
+    a.order = b->order_d;
     a.M = M;
     a.total_chunks = chunk0;
     a.total_items = item0;

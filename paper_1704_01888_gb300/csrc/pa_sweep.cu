@@ -47,9 +47,13 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
     return G;
 }
 
-// Persistent blocks stride over groups of rpb replicas of the current
-// population.  B: bits per state; MODE: 0 for L = 64, 1 for L a multiple of
-// 64, 2 otherwise (rows padded to whole words).
+// Persistent blocks, each with an equal share of the current population
+// (R_i is known only on the device), split into groups of at most rpb
+// replicas.  Shares are counted in quanta of blockDim / (site words per
+// colour) replicas, the number that fills one pass of the block's threads
+// over the site words, so that no block and no pass is left part-empty.
+// B: bits per state; MODE: 0 for L = 64, 1 for L a multiple of 64, 2
+// otherwise (rows padded to whole words).
 template <int B, int MODE>
 __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
 {
@@ -60,10 +64,14 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
     if (st->err) return;
     const int parity = st->parity;
     const int R = a.gather ? st->pop_next : st->pop;
+    const int words = a.L * row_words(a.L);
+    const int quantum = max(1, min(a.rpb, (int)blockDim.x / words));
+    const long long nq = (R + quantum - 1) / quantum;
+    const int begin = (int)(nq * blockIdx.x / gridDim.x) * quantum;
+    const int end = min(R, (int)(nq * (blockIdx.x + 1) / gridDim.x) * quantum);
     long long sE = 0, sE2 = 0, sM = 0;
-    for (int g = blockIdx.x; g * a.rpb < R; g += gridDim.x) {
-        const int first = g * a.rpb;
-        const dev::Group G = make_group(a, parity, first, min(a.rpb, R - first));
+    for (int first = begin; first < end; first += a.rpb) {
+        const dev::Group G = make_group(a, parity, first, min(a.rpb, end - first));
         dev::sweep_group_bits<B, MODE>(G, a.L, reinterpret_cast<uint32_t *>(smem4), s_tab, a.rk0, a.rk1, sE, sE2,
                                        sM);
     }
