@@ -87,16 +87,16 @@ __global__ void k_batch_init(const BatchArgs b)
 // The sweep body for a run's bits per state and row geometry.
 template <int MODE>
 __device__ __forceinline__ void batch_body(int B, const dev::Group &G, int L, uint32_t *sw, const uint4 *s_tab,
-                                           const BatchArgs &b, long long &sE, long long &sE2, long long &sM)
+                                           uint32_t *q, const BatchArgs &b, long long &sE, long long &sE2, long long &sM)
 {
     switch (B) {
-    case 1: dev::sweep_group_bits<1, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 2: dev::sweep_group_bits<2, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 3: dev::sweep_group_bits<3, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 4: dev::sweep_group_bits<4, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 5: dev::sweep_group_bits<5, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 6: dev::sweep_group_bits<6, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
-    default: dev::sweep_group_bits<7, MODE>(G, L, sw, s_tab, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 1: dev::sweep_group_bits<1, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 2: dev::sweep_group_bits<2, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 3: dev::sweep_group_bits<3, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 4: dev::sweep_group_bits<4, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 5: dev::sweep_group_bits<5, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
+    case 6: dev::sweep_group_bits<6, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
+    default: dev::sweep_group_bits<7, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
     }
 }
 
@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
     __shared__ uint4 s_tab[dev::kThresholdEntries];
     __shared__ int s_prefix[kMaxRuns + 1];
     __shared__ int s_group;
+    __shared__ uint32_t s_queue[dev::queue_words(7)];
     const int i = *b.step_counter;
     if (threadIdx.x == 0) {
         int acc = 0;
@@ -200,11 +201,11 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
         uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);
         const int B = state_bits(r.q);
         if (r.L == 64)
-            batch_body<0>(B, G, 64, sw, s_tab, b, sE, sE2, sM);
+            batch_body<0>(B, G, 64, sw, s_tab, s_queue, b, sE, sE2, sM);
         else if (r.L % 64 == 0)
-            batch_body<1>(B, G, r.L, sw, s_tab, b, sE, sE2, sM);
+            batch_body<1>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         else
-            batch_body<2>(B, G, r.L, sw, s_tab, b, sE, sE2, sM);
+            batch_body<2>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(r.acc, sE, sE2, sM);
     }
 }

@@ -176,6 +176,19 @@ __device__ __forceinline__ void group_families(const Group &G)
 // block's threads share the 41 entries (blocks may have as few as 32 threads).
 constexpr int kThresholdEntries = 41;
 constexpr int kThresholdFull = 40;
+
+// Two-pass acceptance.  In the first pass every site word draws at most
+// kFirstPassCalls Philox calls of acceptance words (the warp stops early when
+// all its sites are decided); a word with sites still undecided after that
+// (about 8 % of words at low temperature) goes to a block-wide queue, and in
+// the second pass whole warps serve only queued words, so a warp no longer
+// waits for the slowest of its ~700 sites.  Queue layout in shared memory:
+// two counters, kQueueCap entries of (site-word index, accepted, undecided,
+// class bits c0, e1, B proposal planes).  A full queue is not an error: the
+// word's own thread finishes it.
+constexpr int kFirstPassCalls = 2;
+constexpr int kQueueCap = 512;
+__host__ __device__ constexpr int queue_words(int B) { return 2 + (5 + B) * kQueueCap; }
 __device__ __forceinline__ void build_threshold_table(uint4 *tab, const Thresholds &th)
 {
     auto m = [](uint32_t bit) { return bit ? 0xFFFFFFFFu : 0u; };
@@ -216,8 +229,8 @@ __device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0,
 // the warp draws further acceptance words only while some site is undecided.
 template <int B, int MODE>
 __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32_t *sw, const uint4 *s_tab,
-                                                 const uint32_t *rk0, const uint32_t *rk1, long long &sE,
-                                                 long long &sE2, long long &sM)
+                                                 uint32_t *qbuf, const uint32_t *rk0, const uint32_t *rk1,
+                                                 long long &sE, long long &sE2, long long &sM)
 {
     constexpr int BP = plane_stride(B);
     const int L = MODE == 0 ? 64 : Lrt;
@@ -256,9 +269,20 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                           s_tab[kThresholdFull].w;
     const int total = nrep * IPC;
 
+    // site words still undecided after the first pass wait in qbuf for the second
+    int *q_count = reinterpret_cast<int *>(qbuf);
+    int *q_item = q_count + 2;
+    uint32_t(*q_mask)[kQueueCap] = reinterpret_cast<uint32_t(*)[kQueueCap]>(qbuf + 2 + kQueueCap);  // acc, und, c0, e1
+    uint32_t(*q_prop)[kQueueCap] = reinterpret_cast<uint32_t(*)[kQueueCap]>(qbuf + 2 + 5 * kQueueCap);
+    if (tid < 2) q_count[tid] = 0;
+    __syncthreads();
+    int half = 0;
+
     for (int k = 0; k < G.theta; ++k) {
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < 2; ++c, ++half) {
             const uint32_t ctr1 = DOM_SWEEP | ((uint32_t)(2 * k + c) << 8);
+            if (tid == 0) q_count[(half + 1) & 1] = 0;
+            int *qc = q_count + (half & 1);
             for (int base = warp * 32; base < total; base += nwarps * 32) {
                 const int i = base + lane;
                 const bool live = i < total;
@@ -372,7 +396,71 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 }
                 constexpr int fc = (BP + 3) / 4;
 #pragma unroll 1
-                for (int ch = fc; ch < fc + 8; ++ch) {
+                for (int ch = fc; ch < fc + kFirstPassCalls; ++ch) {
+                    if (!__any_sync(0xFFFFFFFFu, und)) break;
+                    const uint4 za = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
+                    const int j0 = 4 * ch - BP;
+                    plane(za.x, j0);
+                    plane(za.y, j0 + 1);
+                    plane(za.z, j0 + 2);
+                    plane(za.w, j0 + 3);
+                }
+                bool queued = false;
+                if (und) {
+                    const int e = atomicAdd(qc, 1);
+                    if (e < kQueueCap) {
+                        q_item[e] = ii;
+                        q_mask[0][e] = acc;
+                        q_mask[1][e] = und;
+                        q_mask[2][e] = c0;
+                        q_mask[3][e] = e1;
+#pragma unroll
+                        for (int p = 0; p < B; ++p) q_prop[p][e] = P[p];
+                        queued = true;
+                    } else {
+                        // queue full: this thread finishes its word alone (no warp votes)
+                        for (int ch = fc + kFirstPassCalls; und && ch < fc + 8; ++ch) {
+                            const uint4 za =
+                                philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
+                            const int j0 = 4 * ch - BP;
+                            plane(za.x, j0);
+                            plane(za.y, j0 + 1);
+                            plane(za.z, j0 + 2);
+                            plane(za.w, j0 + 3);
+                        }
+                    }
+                }
+                if (live && !queued) {
+#pragma unroll
+                    for (int p = 0; p < B; ++p) W[p] = (acc & P[p]) | (~acc & W[p]);
+                    store_planes<BP>(own, W);
+                }
+            }
+            __syncthreads();
+            // second pass: the queued site words, 32 to a warp
+            const int nq = min(*qc, kQueueCap);
+            for (int base = warp * 32; base < nq; base += nwarps * 32) {
+                const int e = base + lane;
+                const bool live = e < nq;
+                const int ee = live ? e : nq - 1;
+                const int ii = q_item[ee];
+                const int r = ii / IPC;
+                const int rem = ii - r * IPC;
+                const int y = MODE == 0 ? rem : rem / WPR;
+                const int t = MODE == 0 ? 0 : rem - y * WPR;
+                uint32_t acc = q_mask[0][ee];
+                uint32_t und = live ? q_mask[1][ee] : 0u;
+                const uint32_t c0 = q_mask[2][ee], e1 = q_mask[3][ee];
+                const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
+                const uint32_t w = (uint32_t)(y * WPR + t);
+                auto plane = [&](uint32_t v, int j) {
+                    const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
+                    acc |= und & ~v & tj;
+                    und &= ~(v ^ tj);
+                };
+                constexpr int fc = (BP + 3) / 4;
+#pragma unroll 1
+                for (int ch = fc + kFirstPassCalls; ch < fc + 8; ++ch) {
                     if (!__any_sync(0xFFFFFFFFu, und)) break;
                     const uint4 za = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
                     const int j0 = 4 * ch - BP;
@@ -382,8 +470,11 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     plane(za.w, j0 + 3);
                 }
                 if (live) {
+                    uint32_t *own = sw + r * RW + ((c * L + y) * WPR + t) * BP;
+                    uint32_t W[BP];
+                    load_planes<BP>(W, own);
 #pragma unroll
-                    for (int p = 0; p < B; ++p) W[p] = (acc & P[p]) | (~acc & W[p]);
+                    for (int p = 0; p < B; ++p) W[p] = (acc & q_prop[p][ee]) | (~acc & W[p]);
                     store_planes<BP>(own, W);
                 }
             }

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
 {
     extern __shared__ uint4 smem4[];
     __shared__ uint4 s_tab[dev::kThresholdEntries];
+    __shared__ uint32_t s_queue[dev::queue_words(B)];
     dev::build_threshold_table(s_tab, a.thr);
     DevState *st = a.st;
     if (st->err) return;
@@ -72,20 +73,23 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
     long long sE = 0, sE2 = 0, sM = 0;
     for (int first = begin; first < end; first += a.rpb) {
         const dev::Group G = make_group(a, parity, first, min(a.rpb, end - first));
-        dev::sweep_group_bits<B, MODE>(G, a.L, reinterpret_cast<uint32_t *>(smem4), s_tab, a.rk0, a.rk1, sE, sE2,
-                                       sM);
+        dev::sweep_group_bits<B, MODE>(G, a.L, reinterpret_cast<uint32_t *>(smem4), s_tab, s_queue, a.rk0, a.rk1,
+                                       sE, sE2, sM);
     }
     if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(a.acc, sE, sE2, sM);
 }
 
-// Allows each kernel the device's full opt-in shared memory, so that the
-// per-launch request alone decides occupancy.
+// Allows each kernel the device's full opt-in shared memory (less its static
+// shared memory), so that the per-launch request alone decides occupancy.
 cudaError_t prepare(KernelFnPtr kernel)
 {
     int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
     return e;
 }
 
