@@ -232,7 +232,8 @@ static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
  * of the Philox call with counter (w, SWEEP | ((2k + c) << 8) | n, step,
  * slot | stream << 24), and the site at bit b takes bit b of each:
  *   sigma = bit of Z_0,  u = sum_{i=1}^{B-1} bit(Z_i) 2^(i-1),
- *   v = sum_{j=0}^{31} bit(Z_{P+j}) 2^(31-j),  P = B rounded up to a power of 2.
+ *   v = sum_{j=0}^{31} bit(Z_{B+j}) 2^(31-j),
+ * i.e. the acceptance bits follow the proposal bits with no gap.
  * The stream of one word is drawn once per half sweep (lazily, on first use). */
 struct orc_word_stream {
     uint64_t seed;
@@ -273,8 +274,6 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], in
                                uint32_t step, uint32_t slot, uint64_t seed, uint32_t stream)
 {
     int B = orc_state_bits(q);
-    int P = 1;
-    while (P < B) P *= 2;
     int words_per_row = (L + 63) / 64;
     for (int k = 0; k < theta; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
@@ -303,7 +302,7 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], in
                          * bit by bit and only when the move raises the energy */
                         int accept = 1;
                         if (dE > 0) {
-                            struct orc_v_source src = {&st, P, b};
+                            struct orc_v_source src = {&st, B, b};
                             accept = orc_below(orc_v_bit, &src, T[dE]);
                         }
                         if (accept) s[y * L + x] = (uint8_t)prop;

@@ -158,7 +158,7 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
     const long long units = (long long)L * pa::row_words(L);
     int rpb = rpb_req;
     if (rpb <= 0) {
-        int rpb_mem = (int)(65536 / RB);
+        int rpb_mem = (int)(81920 / RB);
         if (rpb_mem < 1) rpb_mem = 1;
         int rpb_fill = c->cfg.R / (4 * c->sms);
         if (rpb_fill < 1) rpb_fill = 1;

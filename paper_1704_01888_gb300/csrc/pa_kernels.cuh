@@ -187,7 +187,7 @@ constexpr int kThresholdFull = 40;
 // class bits c0, e1, B proposal planes).  A full queue is not an error: the
 // word's own thread finishes it.
 constexpr int kFirstPassCalls = 2;
-constexpr int kQueueCap = 512;
+constexpr int kQueueCap = 256;
 __host__ __device__ constexpr int queue_words(int B) { return 2 + (5 + B) * kQueueCap; }
 __device__ __forceinline__ void build_threshold_table(uint4 *tab, const Thresholds &th)
 {
@@ -221,7 +221,7 @@ __device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0,
 // Z_0, Z_1, ... (Z_{4n+i} = word i of the Philox call with counter
 // (w, SWEEP | (2k + c) << 8 | n, step, slot | stream)); the site at bit b takes
 // bit b of each: direction sigma from Z_0, offset u from Z_1..Z_{B-1}, and
-// acceptance bits v_j from Z_{BP+j}, most significant first.  Proposal
+// acceptance bits v_j from Z_{B+j}, most significant first.  Proposal
 // s' = s + (1 + u) mod q (sigma = 0) or s - (1 + u) mod q (sigma = 1) by two
 // ripple-carry additions over the planes; dE + 4 is the count of eight
 // indicator bits (neighbours equal to s, neighbours different from s'), summed
@@ -388,18 +388,19 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     acc |= und & ~v & tj;
                     und &= ~(v ^ tj);
                 };
-                if constexpr (BP < 4) {
+                // acceptance bit j is word B + j: the rest of the last proposal call first
+                if constexpr (B % 4 != 0) {
                     if (__any_sync(0xFFFFFFFFu, und)) {
 #pragma unroll
-                        for (int wi = BP; wi < 4; ++wi) plane(Z[wi], wi - BP);
+                        for (int wi = B; wi < 4 * ((B + 3) / 4); ++wi) plane(Z[wi], wi - B);
                     }
                 }
-                constexpr int fc = (BP + 3) / 4;
+                constexpr int fc = (B + 3) / 4;
 #pragma unroll 1
                 for (int ch = fc; ch < fc + kFirstPassCalls; ++ch) {
                     if (!__any_sync(0xFFFFFFFFu, und)) break;
                     const uint4 za = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
-                    const int j0 = 4 * ch - BP;
+                    const int j0 = 4 * ch - B;
                     plane(za.x, j0);
                     plane(za.y, j0 + 1);
                     plane(za.z, j0 + 2);
@@ -422,7 +423,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                         for (int ch = fc + kFirstPassCalls; und && ch < fc + 8; ++ch) {
                             const uint4 za =
                                 philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
-                            const int j0 = 4 * ch - BP;
+                            const int j0 = 4 * ch - B;
                             plane(za.x, j0);
                             plane(za.y, j0 + 1);
                             plane(za.z, j0 + 2);
@@ -458,12 +459,12 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     acc |= und & ~v & tj;
                     und &= ~(v ^ tj);
                 };
-                constexpr int fc = (BP + 3) / 4;
+                constexpr int fc = (B + 3) / 4;
 #pragma unroll 1
                 for (int ch = fc + kFirstPassCalls; ch < fc + 8; ++ch) {
                     if (!__any_sync(0xFFFFFFFFu, und)) break;
                     const uint4 za = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
-                    const int j0 = 4 * ch - BP;
+                    const int j0 = 4 * ch - B;
                     plane(za.x, j0);
                     plane(za.y, j0 + 1);
                     plane(za.z, j0 + 2);
