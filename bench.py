@@ -387,7 +387,7 @@ def run_ours(args):
         "config": {"workload": w.name, "q": w.q, "L": w.L, "R": w.R, "theta": w.theta,
                    "beta": f"0 -> {w.beta_end} in {w.K} equal steps (timed steps {W + 1}..{W + K})",
                    "parallelism": f"independent populations x{world}",
-                   "l2": f"inputs larger than L2: 2 x {w.R * w.N / 1e6:.0f} MB spin buffers",
+                   "l2": f"inputs larger than L2: 2 x {w.R * replica_bytes(w.q, w.L) / 1e6:.0f} MB spin buffers",
                    "launch": {"replicas_per_block": launch_used[0], "threads_per_block": launch_used[1],
                               "blocks": launch_used[2]}},
         "pa_steps_per_s": K / (elapsed_ms / 1e3),
