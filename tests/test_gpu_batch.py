@@ -20,9 +20,11 @@ def _built():
 
 
 def _mixed_runs():
-    """Mixed q, L (the site body for L = 6, run-time L = 24, 40), R, K, theta."""
+    """Mixed q (B = 1..5 bit planes), L (every row geometry: padded single
+    words, one full word at L = 64, two full words at L = 128), R, K, theta."""
     spec = [(5, 16, 700, 6, 3), (10, 8, 400, 9, 2), (8, 6, 300, 5, 2), (6, 32, 500, 4, 3),
-            (10, 24, 350, 7, 2), (3, 40, 200, 3, 1), (20, 16, 900, 8, 0), (2, 64, 150, 2, 2)]
+            (10, 24, 350, 7, 2), (3, 40, 200, 3, 1), (20, 16, 900, 8, 0), (2, 64, 150, 2, 2),
+            (12, 128, 60, 3, 2)]
     runs = []
     for m, (q, L, R, K, theta) in enumerate(spec):
         p = pa.PAParams(q=q, L=L, R=R, seed=9, stream=m)

@@ -115,18 +115,24 @@ def test_step_api_graph_and_launch_shapes_agree():
 
 
 # ---------------------------------------------------------------------------
-# Edge cases: tiny and ragged lattices (site kernel for L % 8 != 0), the word
-# kernel with a run-time L, q = 2 and q = 128, R = 1, theta = 0, rounding
-# mode, heating from the ground state, families.
+# Edge cases: every row geometry of the multi-spin-coded kernel (L = 64; rows
+# of whole words; rows padded to whole words, one or several words per row),
+# bit-plane counts B = 1..7 (q = 2 .. 128), R = 1, theta = 0, rounding modes.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("q,L,R,theta,K,extra", [
-    (3, 2, 64, 3, 8, {}),
-    (5, 4, 200, 4, 10, {}),
+    (3, 2, 64, 3, 8, {}),               # smallest lattice: 1 column per row and colour
+    (5, 4, 200, 4, 10, {}),             # q - 1 = 4: uniform proposal, B = 3
     (10, 6, 150, 2, 10, {}),
-    (10, 8, 300, 3, 10, {}),            # word kernel, run-time L
-    (2, 16, 257, 5, 12, {}),            # Ising-like q = 2, ragged R
-    (128, 16, 100, 2, 6, {}),           # largest q
-    (10, 24, 90, 2, 6, {}),             # word kernel, run-time L, 3 words per row
+    (10, 8, 300, 3, 10, {}),
+    (2, 16, 257, 5, 12, {}),            # Ising-like q = 2 (B = 1), ragged R
+    (128, 16, 100, 2, 6, {}),           # largest q (B = 7)
+    (40, 16, 120, 2, 6, {}),            # B = 6
+    (10, 24, 90, 2, 6, {}),             # 12 columns in a 32-bit word
+    (9, 64, 200, 3, 6, {}),             # one full word per row; q - 1 = 8 uniform
+    (10, 128, 30, 2, 4, {}),            # rows of two full words
+    (20, 66, 40, 2, 4, {}),             # 33 columns: a full word and one column (B = 5)
+    (17, 96, 30, 2, 4, {}),             # 48 columns: a full and a half word; q - 1 = 16 uniform
+    (2, 130, 8, 2, 3, {}),              # 65 columns: three words per row, q = 2
     (10, 16, 1, 3, 10, {}),             # one replica
     (6, 16, 500, 0, 8, {}),             # resampling only
     (8, 16, 400, 3, 10, {"mode": pa.RESAMPLE_ROUND}),
