@@ -224,17 +224,26 @@ static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
     nb[3] = s[((y + 1) % L) * L + x];
 }
 
-/* reading (random numbers of a sweep): the sites of colour c ((x + y) mod 2)
- * in row y, with column index m = x >> 1, are grouped 32 columns to a "site
- * word": word t = m >> 5 of the row, bit b = m & 31, word index
- * w = y ceil(L / 64) + t.  In sweep k, colour c, temperature step `step`, the
- * word draws a stream Z_0, Z_1, ... of 32-bit numbers, Z_{4n+i} being word i
- * of the Philox call with counter (w, SWEEP | ((2k + c) << 8) | n, step,
- * slot | stream << 24), and the site at bit b takes bit b of each:
+/* reading (random numbers of a sweep): the sites of one colour c ((x + y)
+ * mod 2), with column index m = x >> 1, are grouped 32 to a "site word".  When
+ * a whole number of that colour's rows fills 32 columns (L = 8, 16, 32, 64,
+ * i.e. L/2 divides 32), the colour's sites in row-major order, h = y L/2 + m,
+ * fill the words in turn: word w = h >> 5, bit b = h & 31.  Otherwise each row
+ * starts a new word: word t = m >> 5 of the row, bit b = m & 31, word index
+ * w = y ceil(L / 64) + t.  (At L = 64 both rules coincide.)  In sweep k,
+ * colour c, temperature step `step`, the word draws a stream Z_0, Z_1, ... of
+ * 32-bit numbers, Z_{4n+i} being word i of the Philox call with counter
+ * (w, SWEEP | ((2k + c) << 8) | n, step, slot | stream << 24), and the site at
+ * bit b takes bit b of each:
  *   sigma = bit of Z_0,  u = sum_{i=1}^{B-1} bit(Z_i) 2^(i-1),
  *   v = sum_{j=0}^{31} bit(Z_{B+j}) 2^(31-j),
  * i.e. the acceptance bits follow the proposal bits with no gap.
  * The stream of one word is drawn once per half sweep (lazily, on first use). */
+static int orc_rows_packed(int L)
+{
+    return L >= 8 && 64 % L == 0;
+}
+
 struct orc_word_stream {
     uint64_t seed;
     uint32_t w, c1base, step, c3;
@@ -263,6 +272,28 @@ static int orc_v_bit(void *ctx, int j)
     return (int)(orc_stream_word(src->st, src->first + j) >> src->b) & 1;
 }
 
+/* One attempt on site (x, y), which takes bit b of the word stream st. */
+static void orc_attempt(int q, int B, int L, uint8_t *s, int x, int y, struct orc_word_stream *st, int b,
+                        const uint64_t T[5])
+{
+    int sigma = (int)(orc_stream_word(st, 0) >> b) & 1;
+    uint32_t u = 0;
+    for (int i = 1; i < B; ++i) u |= ((orc_stream_word(st, i) >> b) & 1u) << (i - 1);
+    int nb[4];
+    orc_neighbours(L, s, x, y, nb);
+    int cur = s[y * L + x];
+    int prop = orc_propose(q, cur, sigma, u);
+    int dE = orc_delta_energy(cur, prop, nb);
+    /* the Metropolis acceptance of orc_accept, with v read bit by bit and only
+     * when the move raises the energy */
+    int accept = 1;
+    if (dE > 0) {
+        struct orc_v_source src = {st, B, b};
+        accept = orc_below(orc_v_bit, &src, T[dE]);
+    }
+    if (accept) s[y * L + x] = (uint8_t)prop;
+}
+
 /* theta checkerboard sweeps of one replica at the thresholds T.
  * reading: one sweep updates the colour-0 sites ((x+y) even) and then the
  * colour-1 sites, each colour row by row and, within a row, by increasing x.
@@ -277,35 +308,33 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], in
     int words_per_row = (L + 63) / 64;
     for (int k = 0; k < theta; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
-            for (int y = 0; y < L; ++y) {
-                int x0 = (colour + y) & 1;  /* first column of this colour in row y */
-                for (int t = 0; t < words_per_row; ++t) {
-                    struct orc_word_stream st;
-                    st.seed = seed;
-                    st.w = (uint32_t)(y * words_per_row + t);
-                    st.c1base = ORC_DOM_SWEEP | ((uint32_t)(2 * k + colour) << 8);
-                    st.step = step;
-                    st.c3 = slot | (stream << 24);
+            struct orc_word_stream st;
+            st.seed = seed;
+            st.c1base = ORC_DOM_SWEEP | ((uint32_t)(2 * k + colour) << 8);
+            st.step = step;
+            st.c3 = slot | (stream << 24);
+            if (orc_rows_packed(L)) {
+                int half = L / 2;
+                for (int w = 0; w < L * half / 32; ++w) {
+                    st.w = (uint32_t)w;
                     st.have = 0;
                     for (int b = 0; b < 32; ++b) {
-                        int x = 2 * (32 * t + b) + x0;
-                        if (x >= L) break;
-                        int sigma = (int)(orc_stream_word(&st, 0) >> b) & 1;
-                        uint32_t u = 0;
-                        for (int i = 1; i < B; ++i) u |= ((orc_stream_word(&st, i) >> b) & 1u) << (i - 1);
-                        int nb[4];
-                        orc_neighbours(L, s, x, y, nb);
-                        int cur = s[y * L + x];
-                        int prop = orc_propose(q, cur, sigma, u);
-                        int dE = orc_delta_energy(cur, prop, nb);
-                        /* the Metropolis acceptance of orc_accept, with v read
-                         * bit by bit and only when the move raises the energy */
-                        int accept = 1;
-                        if (dE > 0) {
-                            struct orc_v_source src = {&st, B, b};
-                            accept = orc_below(orc_v_bit, &src, T[dE]);
+                        int h = 32 * w + b;
+                        int y = h / half, m = h % half;
+                        orc_attempt(q, B, L, s, 2 * m + ((colour + y) & 1), y, &st, b, T);
+                    }
+                }
+            } else {
+                for (int y = 0; y < L; ++y) {
+                    int x0 = (colour + y) & 1;  /* first column of this colour in row y */
+                    for (int t = 0; t < words_per_row; ++t) {
+                        st.w = (uint32_t)(y * words_per_row + t);
+                        st.have = 0;
+                        for (int b = 0; b < 32; ++b) {
+                            int x = 2 * (32 * t + b) + x0;
+                            if (x >= L) break;
+                            orc_attempt(q, B, L, s, x, y, &st, b, T);
                         }
-                        if (accept) s[y * L + x] = (uint8_t)prop;
                     }
                 }
             }
