@@ -204,6 +204,8 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
             batch_body<0>(B, G, 64, sw, s_tab, s_queue, b, sE, sE2, sM);
         else if (r.L % 64 == 0)
             batch_body<1>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
+        else if (rows_packed(r.L))
+            batch_body<3>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         else
             batch_body<2>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(r.acc, sE, sE2, sM);
@@ -472,7 +474,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         chunk0 += nc;
         b->nchunks[m] = nc;
         r.item0 = item0;
-        item0 += (long long)g.R * (2 * g.L * pa::row_words(g.L));
+        item0 += (long long)g.R * (2 * pa::colour_words(g.L));
         const size_t spin_bytes = (size_t)r.R_cap * pa::replica_bytes(g.q, g.L);
         stage_bytes = std::max(stage_bytes, std::min((size_t)r.R_cap * r.N, (size_t)64 << 20));
         if ((s = balloc(b, &r.buf[0], spin_bytes)) || (s = balloc(b, &r.buf[1], spin_bytes)) ||

@@ -155,7 +155,7 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
     const int L = c->cfg.L;
     const size_t RB = pa::replica_bytes(c->cfg.q, L);
     // work items per replica and half sweep: the site words of one colour
-    const long long units = (long long)L * pa::row_words(L);
+    const long long units = pa::colour_words(L);
     int rpb = rpb_req;
     if (rpb <= 0) {
         int rpb_mem = (int)(81920 / RB);

@@ -2,17 +2,20 @@
 // translation units of the GB300 population-annealing library.
 //
 // Device layout of one replica (multi-spin coding).  A state 0..q-1 takes
-// B = ceil(log2 q) bits; the sites of colour c = (x + y) & 1 in row y, with
-// column index m = x >> 1, are packed 32 columns to a word: word t = m >> 5 of
-// the row, bit b = m & 31.  Each such site word is stored as BP 32-bit planes
-// (BP = B rounded up to 1, 2, 4 or 8; plane p holds bit p of the states):
-//   word index ((c * L + y) * WPR + t) * BP + p,   WPR = ceil(L / 64).
-// Bits of columns >= L/2 and planes >= B are always zero.  One replica takes
-// RW = 2 L WPR BP words; replica s starts at word s * RW of its buffer.  The
-// four neighbours of a site word are the words of the other colour in rows
-// y-1, y+1 and y and that row word shifted by one bit, so one 32-bit logic
-// instruction serves 32 sites.  The canonical [y][x] byte layout exists only at
-// the API boundary (pa_get_spins).
+// B = ceil(log2 q) bits.  The sites of colour c = (x + y) & 1, with column index
+// m = x >> 1, are packed 32 to a "site word", stored as BP 32-bit planes (BP = B
+// rounded up to 1, 2, 4 or 8; plane p holds bit p of the states):
+//   word index (c * IPC + w) * BP + p,   IPC = site words per colour.
+// When L/2 divides 32 (L = 8, 16, 32, 64) the colour's sites in row-major order
+// h = y L/2 + m fill the words in turn (w = h >> 5, bit h & 31; IPC = L^2/64).
+// Otherwise each row starts a new word: w = y WPR + (m >> 5), bit m & 31,
+// WPR = ceil(L / 64), IPC = L WPR, and columns >= L/2 of a row's last word are
+// always zero.  Planes >= B are always zero.  One replica takes RW = 2 IPC BP
+// words, rounded up to a multiple of 4; replica s starts at word s * RW.  The four neighbours of
+// a site word are words of the other colour (rows above and below, the same
+// row, and that row shifted by one column), so one 32-bit logic instruction
+// serves 32 sites.  The canonical [y][x] byte layout exists only at the API
+// boundary (pa_get_spins).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -39,7 +42,13 @@ constexpr int kMaxLatticeBytes = 200 * 1024;
 __host__ __device__ constexpr int state_bits(int q) { return q <= 2 ? 1 : q <= 4 ? 2 : q <= 8 ? 3 : q <= 16 ? 4 : q <= 32 ? 5 : q <= 64 ? 6 : 7; }
 __host__ __device__ constexpr int plane_stride(int B) { return B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8; }
 __host__ __device__ constexpr int row_words(int L) { return (L + 63) / 64; }
-__host__ __device__ constexpr int replica_words(int q, int L) { return 2 * L * row_words(L) * plane_stride(state_bits(q)); }
+// Rows packed several to a word: L/2 divides 32 (L = 8, 16, 32; at L = 64 both
+// layouts coincide).
+__host__ __device__ constexpr bool rows_packed(int L) { return L >= 8 && 64 % L == 0; }
+__host__ __device__ constexpr int colour_words(int L) { return rows_packed(L) ? L * L / 64 : L * row_words(L); }
+// Words of one replica, padded to whole 16-byte vectors (the gather moves uint4).
+__host__ __device__ constexpr int replica_words_of(int B, int L) { return (2 * colour_words(L) * plane_stride(B) + 3) & ~3; }
+__host__ __device__ constexpr int replica_words(int q, int L) { return replica_words_of(state_bits(q), L); }
 inline size_t replica_bytes(int q, int L) { return (size_t)replica_words(q, L) * 4; }
 
 // Acceptance thresholds T[d] = floor(exp(-beta d) 2^32), d = 1..4, as the low 32

@@ -13,6 +13,7 @@
 // their scan, parent map; estimators (Sec. 2 step 4, Eqs. 4-5).
 #pragma once
 #include <climits>
+#include <type_traits>
 
 #include "pa_internal.cuh"
 
@@ -107,6 +108,83 @@ __device__ __forceinline__ uint32_t shifted_row(uint32_t H, uint32_t E, int par,
         return par ? __funnelshift_r(H, E, 1) : __funnelshift_r(E, H, 31);
     } else {
         return par ? ((H >> 1) | ((E & 1u) << (nb - 1))) : ((H << 1) | ((E >> (nbe - 1)) & 1u));
+    }
+}
+
+// Packed rows (MODE 3, L = 8, 16, 32): the horizontal neighbour word of H.
+// Each word holds 32 / S rows of S = L/2 columns; in a row whose sites sit at
+// odd x (par = 1) the neighbour not at the same column is column m + 1, else
+// m - 1, both cyclic within the row's S-bit segment.  Rows alternate par, and
+// `odd` marks the segments with par = 1 (the same in every word of a colour).
+template <int S>
+__device__ __forceinline__ uint32_t shifted_packed(uint32_t H, uint32_t odd)
+{
+    constexpr uint32_t bot = S == 4 ? 0x11111111u : S == 8 ? 0x01010101u : 0x00010001u;
+    constexpr uint32_t top = bot << (S - 1);
+    const uint32_t right = ((H >> 1) & ~top) | ((H << (S - 1)) & top);  // column m + 1
+    const uint32_t left = ((H << 1) & ~bot) | ((H >> (S - 1)) & bot);   // column m - 1
+    return (odd & right) | (~odd & left);
+}
+
+template <int S>
+__device__ __forceinline__ constexpr uint32_t odd_segments()
+{
+    return S == 4 ? 0xF0F0F0F0u : S == 8 ? 0xFF00FF00u : 0xFFFF0000u;
+}
+
+// The four neighbour words of site word `it` (its index within its colour) of
+// colour c: up, down and same-row words of the other colour (oth) and the
+// same-row word shifted by one column.  Returns the mask of the word's valid
+// columns.  MODE as for shifted_row, or 3 for packed rows.
+template <int B, int MODE, int BP>
+__device__ __forceinline__ uint32_t neighbour_planes(const uint32_t *oth, int L, int IPC, int WPR, int nb_last,
+                                                     int it, int c, uint32_t (&U)[BP], uint32_t (&D)[BP],
+                                                     uint32_t (&H)[BP], uint32_t (&X)[BP])
+{
+    if constexpr (MODE == 3) {
+        const int wu = it == 0 ? IPC - 1 : it - 1;
+        const int wd = it == IPC - 1 ? 0 : it + 1;
+        uint32_t Hu[BP], Hd[BP];
+        load_planes<BP>(H, oth + it * BP);
+        load_planes<BP>(Hu, oth + wu * BP);
+        load_planes<BP>(Hd, oth + wd * BP);
+        auto body = [&](auto S_tag) {
+            constexpr int S = decltype(S_tag)::value;
+            const uint32_t seg = c ? ~odd_segments<S>() : odd_segments<S>();
+#pragma unroll
+            for (int p = 0; p < B; ++p) {
+                U[p] = (H[p] << S) | (Hu[p] >> (32 - S));
+                D[p] = (H[p] >> S) | (Hd[p] << (32 - S));
+                X[p] = shifted_packed<S>(H[p], seg);
+            }
+        };
+        if (L == 8) body(std::integral_constant<int, 4>{});
+        else if (L == 16) body(std::integral_constant<int, 8>{});
+        else body(std::integral_constant<int, 16>{});
+        return 0xFFFFFFFFu;
+    } else {
+        const int y = MODE == 0 ? it : it / WPR;
+        const int t = MODE == 0 ? 0 : it - y * WPR;
+        const int yu = (y == 0) ? L - 1 : y - 1;
+        const int yd = (y == L - 1) ? 0 : y + 1;
+        const int par = (y + c) & 1;
+        load_planes<BP>(U, oth + (yu * WPR + t) * BP);
+        load_planes<BP>(D, oth + (yd * WPR + t) * BP);
+        load_planes<BP>(H, oth + (y * WPR + t) * BP);
+        if constexpr (MODE == 0) {
+#pragma unroll
+            for (int p = 0; p < B; ++p) X[p] = shifted_row<0>(H[p], 0u, par, 32, 32);
+            return 0xFFFFFFFFu;
+        } else {
+            const int te = par ? (t + 1 == WPR ? 0 : t + 1) : (t == 0 ? WPR - 1 : t - 1);
+            uint32_t Eg[BP];
+            load_planes<BP>(Eg, oth + (y * WPR + te) * BP);
+            const int nb = t == WPR - 1 ? nb_last : 32;
+            const int nbe = te == WPR - 1 ? nb_last : 32;
+#pragma unroll
+            for (int p = 0; p < B; ++p) X[p] = shifted_row<MODE>(H[p], Eg[p], par, nb, nbe);
+            return valid_mask(t, WPR, nb_last);
+        }
     }
 }
 
@@ -237,8 +315,8 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
     const int N = L * L;
     const int WPR = MODE == 0 ? 1 : row_words(L);
     const int nb_last = L / 2 - 32 * (WPR - 1);
-    const int IPC = L * WPR;      // site words per colour per replica
-    const int RW = 2 * IPC * BP;  // words per replica
+    const int IPC = colour_words(L);  // site words per colour per replica
+    const int RW = replica_words_of(B, L);  // words per replica
     const int UPR = RW / 4;       // uint4 per replica
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -288,38 +366,17 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 const bool live = i < total;
                 const int ii = live ? i : total - 1;
                 const int r = ii / IPC;
-                const int rem = ii - r * IPC;
-                const int y = MODE == 0 ? rem : rem / WPR;
-                const int t = MODE == 0 ? 0 : rem - y * WPR;
+                const int it = ii - r * IPC;  // site word within the colour = its counter word w
                 uint32_t *rep = sw + r * RW;
-                uint32_t *own = rep + ((c * L + y) * WPR + t) * BP;
+                uint32_t *own = rep + (c * IPC + it) * BP;
                 const uint32_t *oth = rep + (c ^ 1) * IPC * BP;
-                const int yu = (y == 0) ? L - 1 : y - 1;
-                const int yd = (y == L - 1) ? 0 : y + 1;
-                const int par = (y + c) & 1;
                 uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
                 load_planes<BP>(W, own);
-                load_planes<BP>(U, oth + (yu * WPR + t) * BP);
-                load_planes<BP>(D, oth + (yd * WPR + t) * BP);
-                load_planes<BP>(H, oth + (y * WPR + t) * BP);
-                uint32_t vmask = 0xFFFFFFFFu;
-                if constexpr (MODE == 0) {
-#pragma unroll
-                    for (int p = 0; p < B; ++p) X[p] = shifted_row<0>(H[p], 0u, par, 32, 32);
-                } else {
-                    const int te = par ? (t + 1 == WPR ? 0 : t + 1) : (t == 0 ? WPR - 1 : t - 1);
-                    uint32_t Eg[BP];
-                    load_planes<BP>(Eg, oth + (y * WPR + te) * BP);
-                    const int nb = t == WPR - 1 ? nb_last : 32;
-                    const int nbe = te == WPR - 1 ? nb_last : 32;
-#pragma unroll
-                    for (int p = 0; p < B; ++p) X[p] = shifted_row<MODE>(H[p], Eg[p], par, nb, nbe);
-                    vmask = valid_mask(t, WPR, nb_last);
-                }
+                const uint32_t vmask = neighbour_planes<B, MODE, BP>(oth, L, IPC, WPR, nb_last, it, c, U, D, H, X);
 
                 // proposal: direction sigma = Z_0, offset bits u = Z_1..Z_{B-1}
                 const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
-                const uint32_t w = (uint32_t)(y * WPR + t);
+                const uint32_t w = (uint32_t)it;
                 uint32_t Z[8];
                 {
                     const uint4 z = philox10_rk(make_uint4(w, ctr1, (uint32_t)G.step, slot), rk0, rk1);
@@ -446,14 +503,12 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 const int ee = live ? e : nq - 1;
                 const int ii = q_item[ee];
                 const int r = ii / IPC;
-                const int rem = ii - r * IPC;
-                const int y = MODE == 0 ? rem : rem / WPR;
-                const int t = MODE == 0 ? 0 : rem - y * WPR;
+                const int it = ii - r * IPC;
                 uint32_t acc = q_mask[0][ee];
                 uint32_t und = live ? q_mask[1][ee] : 0u;
                 const uint32_t c0 = q_mask[2][ee], e1 = q_mask[3][ee];
                 const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
-                const uint32_t w = (uint32_t)(y * WPR + t);
+                const uint32_t w = (uint32_t)it;
                 auto plane = [&](uint32_t v, int j) {
                     const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
                     acc |= und & ~v & tj;
@@ -471,7 +526,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     plane(za.w, j0 + 3);
                 }
                 if (live) {
-                    uint32_t *own = sw + r * RW + ((c * L + y) * WPR + t) * BP;
+                    uint32_t *own = sw + r * RW + (c * IPC + it) * BP;
                     uint32_t W[BP];
                     load_planes<BP>(W, own);
 #pragma unroll
@@ -498,31 +553,10 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
         if (have) {
             // each bond has one colour-0 end: count equal neighbours of colour-0 sites
             for (int it = me; it < IPC; it += stride) {
-                const int y = MODE == 0 ? it : it / WPR;
-                const int t = MODE == 0 ? 0 : it - y * WPR;
-                const uint32_t *oth = rep + IPC * BP;
-                const int yu = (y == 0) ? L - 1 : y - 1;
-                const int yd = (y == L - 1) ? 0 : y + 1;
-                const int par = y & 1;
                 uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
-                load_planes<BP>(W, rep + (y * WPR + t) * BP);
-                load_planes<BP>(U, oth + (yu * WPR + t) * BP);
-                load_planes<BP>(D, oth + (yd * WPR + t) * BP);
-                load_planes<BP>(H, oth + (y * WPR + t) * BP);
-                uint32_t vmask = 0xFFFFFFFFu;
-                if constexpr (MODE == 0) {
-#pragma unroll
-                    for (int p = 0; p < B; ++p) X[p] = shifted_row<0>(H[p], 0u, par, 32, 32);
-                } else {
-                    const int te = par ? (t + 1 == WPR ? 0 : t + 1) : (t == 0 ? WPR - 1 : t - 1);
-                    uint32_t Eg[BP];
-                    load_planes<BP>(Eg, oth + (y * WPR + te) * BP);
-                    const int nb = t == WPR - 1 ? nb_last : 32;
-                    const int nbe = te == WPR - 1 ? nb_last : 32;
-#pragma unroll
-                    for (int p = 0; p < B; ++p) X[p] = shifted_row<MODE>(H[p], Eg[p], par, nb, nbe);
-                    vmask = valid_mask(t, WPR, nb_last);
-                }
+                load_planes<BP>(W, rep + it * BP);
+                const uint32_t vmask =
+                    neighbour_planes<B, MODE, BP>(rep + IPC * BP, L, IPC, WPR, nb_last, it, 0, U, D, H, X);
                 agree += __popc(vmask & ~differ<B, BP>(W, U)) + __popc(vmask & ~differ<B, BP>(W, D)) +
                          __popc(vmask & ~differ<B, BP>(W, H)) + __popc(vmask & ~differ<B, BP>(W, X));
             }
@@ -533,10 +567,10 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
             int cnt = 0;
             if (have) {
                 for (int it = me; it < 2 * IPC; it += stride) {
-                    const int t = MODE == 0 ? 0 : it % WPR;
                     uint32_t W[BP];
                     load_planes<BP>(W, rep + it * BP);
-                    const uint32_t vmask = MODE == 0 ? 0xFFFFFFFFu : valid_mask(t, WPR, nb_last);
+                    const uint32_t vmask =
+                        (MODE == 0 || MODE == 3) ? 0xFFFFFFFFu : valid_mask(it % WPR, WPR, nb_last);
                     cnt += __popc(vmask & equal_state<B, BP>(W, s));
                 }
             }
@@ -658,13 +692,14 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
     const int BP = plane_stride(B);
     const int WPR = row_words(L);
     const int nb_last = L / 2 - 32 * (WPR - 1);
-    const int IPR = 2 * L * WPR;  // site words per replica
+    const int IPC = colour_words(L);
+    const int IPR = 2 * IPC;  // site words per replica
     const int slot = (int)(i / IPR);
     const int rem = (int)(i - (long long)slot * IPR);
-    const int c = rem / (L * WPR);
-    const int rem2 = rem - c * L * WPR;
-    const int y = rem2 / WPR, t = rem2 - y * WPR;
-    const int nb = t == WPR - 1 ? nb_last : 32;
+    const int c = rem / IPC;
+    const int it = rem - c * IPC;
+    const bool packed = rows_packed(L);
+    const int nb = packed ? 32 : ((it % WPR) == WPR - 1 ? nb_last : 32);
     uint32_t planes[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     if (ground) {
         const uint4 w = philox10(make_uint4((uint32_t)slot >> 2, DOM_GROUND, 0u, stream_hi), k0, k1);
@@ -675,7 +710,16 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
         int last = -1;
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         for (int b = 0; b < nb; ++b) {
-            const int x = 2 * (32 * t + b) + ((y + c) & 1);
+            int y, m;
+            if (packed) {
+                const int h = 32 * it + b;
+                y = h / (L / 2);
+                m = h - y * (L / 2);
+            } else {
+                y = it / WPR;
+                m = 32 * (it - y * WPR) + b;
+            }
+            const int x = 2 * m + ((y + c) & 1);
             const int site = y * L + x;
             if ((site >> 2) != last) {
                 last = site >> 2;
@@ -685,7 +729,7 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
             for (int p = 0; p < B; ++p) planes[p] |= ((s >> p) & 1u) << b;
         }
     }
-    uint32_t *dst = spins + (size_t)slot * (IPR * BP) + (size_t)rem * BP;
+    uint32_t *dst = spins + (size_t)slot * replica_words_of(B, L) + (size_t)rem * BP;
     for (int p = 0; p < BP; ++p) dst[p] = planes[p];
     if (rem == 0 && anc) anc[slot] = slot;
 }
@@ -696,15 +740,24 @@ __device__ __forceinline__ uint8_t canonical_state(const uint32_t *spins, int q,
     const int N = L * L;
     const int B = state_bits(q);
     const int BP = plane_stride(B);
-    const int WPR = row_words(L);
+    const int IPC = colour_words(L);
     const long long r = i / N;
     const int site = (int)(i - r * N);
     const int y = site / L, x = site - y * L;
     const int c = (x + y) & 1;
     const int m = x >> 1;
-    const uint32_t *w = spins + (size_t)r * (2 * L * WPR * BP) + (size_t)(((c * L + y) * WPR + (m >> 5)) * BP);
+    int it, b;
+    if (rows_packed(L)) {
+        const int h = y * (L / 2) + m;
+        it = h >> 5;
+        b = h & 31;
+    } else {
+        it = y * row_words(L) + (m >> 5);
+        b = m & 31;
+    }
+    const uint32_t *w = spins + (size_t)r * replica_words_of(B, L) + (size_t)((c * IPC + it) * BP);
     uint32_t s = 0;
-    for (int p = 0; p < B; ++p) s |= ((w[p] >> (m & 31)) & 1u) << p;
+    for (int p = 0; p < B; ++p) s |= ((w[p] >> b) & 1u) << p;
     return (uint8_t)s;
 }
 

@@ -28,7 +28,7 @@ constexpr int kBlock = 1024;
 __global__ void k_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
                        uint32_t stream_hi, int ground)
 {
-    const long long total = (long long)R * (2 * L * row_words(L));
+    const long long total = (long long)R * (2 * colour_words(L));
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x)
         dev::init_item(spins, anc, q, L, i, k0, k1, stream_hi, ground);
@@ -90,7 +90,7 @@ int grid_for(long long work, int threads)
 cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
                         uint32_t stream_hi, int ground, cudaStream_t s)
 {
-    const long long work = (long long)R * (2 * L * row_words(L));
+    const long long work = (long long)R * (2 * colour_words(L));
     k_init<<<grid_for(work, 256), 256, 0, s>>>(spins, anc, q, L, R, k0, k1, stream_hi, ground);
     bump_launch_count(1);
     return cudaGetLastError();

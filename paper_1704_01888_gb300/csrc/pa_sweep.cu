@@ -52,8 +52,9 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
 // replicas.  Shares are counted in quanta of blockDim / (site words per
 // colour) replicas, the number that fills one pass of the block's threads
 // over the site words, so that no block and no pass is left part-empty.
-// B: bits per state; MODE: 0 for L = 64, 1 for L a multiple of 64, 2
-// otherwise (rows padded to whole words).
+// B: bits per state; MODE: 0 for L = 64, 1 for L a multiple of 64, 3 for
+// L = 8, 16, 32 (rows packed several to a word), 2 otherwise (rows padded to
+// whole words).
 template <int B, int MODE>
 __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
 {
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
     if (st->err) return;
     const int parity = st->parity;
     const int R = a.gather ? st->pop_next : st->pop;
-    const int words = a.L * row_words(a.L);
+    const int words = colour_words(a.L);
     const int quantum = max(1, min(a.rpb, (int)blockDim.x / words));
     const long long nq = (R + quantum - 1) / quantum;
     const int begin = (int)(nq * blockIdx.x / gridDim.x) * quantum;
@@ -112,6 +113,7 @@ KernelFnPtr pick_kernel(int q, int L)
     const int B = state_bits(q);
     if (L == 64) return pick_bits<0>(B);
     if (L % 64 == 0) return pick_bits<1>(B);
+    if (rows_packed(L)) return pick_bits<3>(B);
     return pick_bits<2>(B);
 }
 

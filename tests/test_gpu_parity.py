@@ -116,14 +116,17 @@ def test_step_api_graph_and_launch_shapes_agree():
 
 # ---------------------------------------------------------------------------
 # Edge cases: every row geometry of the multi-spin-coded kernel (L = 64; rows
-# of whole words; rows padded to whole words, one or several words per row),
+# of whole words; rows packed several to a word at L = 8, 16, 32; rows padded
+# to whole words, one or several words per row),
 # bit-plane counts B = 1..7 (q = 2 .. 128), R = 1, theta = 0, rounding modes.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("q,L,R,theta,K,extra", [
     (3, 2, 64, 3, 8, {}),               # smallest lattice: 1 column per row and colour
     (5, 4, 200, 4, 10, {}),             # q - 1 = 4: uniform proposal, B = 3
     (10, 6, 150, 2, 10, {}),
-    (10, 8, 300, 3, 10, {}),
+    (10, 8, 300, 3, 10, {}),            # packed rows: the whole colour in one word
+    (2, 8, 100, 3, 6, {}),              # q = 2 at L = 8: a replica of 2 words, padded to 4
+    (10, 32, 200, 3, 6, {}),            # packed rows: two rows per word
     (2, 16, 257, 5, 12, {}),            # Ising-like q = 2 (B = 1), ragged R
     (128, 16, 100, 2, 6, {}),           # largest q (B = 7)
     (40, 16, 120, 2, 6, {}),            # B = 6
