@@ -100,8 +100,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=197)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"],
-                    help="c3 runs the batch of 64 runs alone (its first --steps steps)")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "widths"],
+                    help="c3 runs the batch of 64 runs alone (its first --steps steps); widths runs the "
+                         "histogram-width study (20 runs, one batch)")
     ap.add_argument("--batch-launch", default="", help="smem_budget,threads for the batched sweep kernel (c3)")
     ap.add_argument("--no-graph", action="store_true", help="c3 without graph capture")
     ap.add_argument("--no-e2e", action="store_true")
@@ -572,12 +573,52 @@ def run_batch_only(args):
     return 0
 
 
+def run_width_study(args):
+    """Histogram widths in the style of the paper's Table I: q in {6, 8, 10,
+    20} x L in {16, ..., 256}, R = 1000, theta = 100, 100 steps to beta_t(q),
+    all 20 runs as one batch; FWHM of the energy-per-site and magnetisation
+    histograms of each final population.  One JSON line."""
+    import torch
+
+    import paper_1704_01888_gb300 as pa
+    from paper_1704_01888_gb300 import analysis
+    from paper_1704_01888_gb300 import build as pabuild
+
+    torch.cuda.set_device(0)
+    pabuild.build()
+    ws = wl.width_study_runs()
+    runs = [(pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed, stream=w.stream), w.betas(), w.theta) for w in ws]
+    b = pa.Batch(runs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(use_graph=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    att = sum(sum(o["R"] for o in b.observables(m)[1:]) * ws[m].N * ws[m].theta for m in range(len(ws)))
+    table = []
+    for m, w in enumerate(ws):
+        E, Mt = b.measurements(m)
+        we, wm = analysis.widths(w.q, w.L, E, Mt)
+        table.append({"q": w.q, "L": w.L, "omega_e": round(we, 5), "omega_m": round(wm, 5),
+                      "meanE_per_site": round(float(E.mean()) / w.N, 5)})
+    shape = b.launch_shape()
+    b.close()
+    print(json.dumps({"metric": "histogram widths (FWHM) at beta_t; PA steps/s", "value": len(ws) * ws[0].K / dt,
+                      "unit": "PA steps/s", "n_gpus": 1, "attempts_per_ns": att / dt / 1e9, "seconds": dt,
+                      "config": {"workload": "width study: q 6, 8, 10, 20 x L 16-256, R=1000, theta=100, "
+                                             "100 steps to beta_t(q), one batch", "launch": shape},
+                      "widths": table}))
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c3":
         return run_batch_only(args)
+    if args.workload == "widths":
+        return run_width_study(args)
     return run_ours(args)
 
 

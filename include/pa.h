@@ -152,6 +152,13 @@ pa_status pa_sweep(pa_ctx *ctx, double beta, int32_t theta, int32_t step);
  * call synchronises).  Only the first R_i values are written. */
 pa_status pa_energy(pa_ctx *ctx, int32_t *E_out, int32_t on_device);
 
+/* Per-replica occupation of the most common state, Mt_j = max over states a
+ * of the number of sites in state a (Sec. 3, Eq. 5: the magnetisation of
+ * replica j is m_j = (q Mt_j / N - 1) / (q - 1)), of the current population,
+ * [R_i] int32, into host memory (synchronises) or device memory (on_device
+ * != 0, enqueued).  Errors as pa_energy. */
+pa_status pa_occupations(pa_ctx *ctx, int32_t *Mt_out, int32_t on_device);
+
 /* Synchronises and returns the estimators of the latest completed step.  If
  * hist_out is non-NULL, also the energy histogram of the current population:
  * hist_out[k] = number of replicas with E = k - 2N, k = 0..2N, so hist_len
@@ -299,6 +306,11 @@ pa_status pa_batch_get_spins(pa_batch *b, int32_t m, int64_t slot_begin, int64_t
 /* Current population size of run m (synchronises); returns that run's error
  * (e.g. PA_ERR_CAPACITY) if it stopped. */
 pa_status pa_batch_population_size(pa_batch *b, int32_t m, int32_t *R_out);
+
+/* Per-replica energies E_j (Eq. 3) and occupations of the most common state
+ * Mt_j (Eq. 5) of run m's current population, [R_i] int32 each, into host
+ * memory (synchronises); either pointer may be NULL. */
+pa_status pa_batch_measurements(pa_batch *b, int32_t m, int32_t *E_out, int32_t *Mt_out);
 
 /* Releases the batch (synchronises its stream). */
 void pa_batch_destroy(pa_batch *b);

@@ -40,7 +40,7 @@ EXPORTED = (
     "pa_get_launch", "pa_resample_noalloc", "pa_reweight_forward", "pa_reweight_scale", "pa_reweight_grad_O",
     "pa_overlap", "pa_next_dbeta", "pa_run_adaptive", "pa_batch_create", "pa_batch_autotune", "pa_batch_set_launch",
     "pa_batch_get_launch", "pa_batch_run", "pa_batch_observables", "pa_batch_get_spins", "pa_batch_destroy",
-    "pa_batch_population_size", "pa_save", "pa_load",
+    "pa_batch_population_size", "pa_save", "pa_load", "pa_occupations", "pa_batch_measurements",
 )
 
 
@@ -125,6 +125,8 @@ def load_library(path: str | None = None):
         "pa_batch_get_spins": ([P, i32, i64, i64, P], st),
         "pa_batch_destroy": ([P], None),
         "pa_batch_population_size": ([P, i32, P], st),
+        "pa_occupations": ([P, P, i32], st),
+        "pa_batch_measurements": ([P, i32, P, P], st),
         "pa_save": ([P, ctypes.c_char_p], st),
         "pa_load": ([ctypes.c_char_p, P, ctypes.POINTER(P)], st),
     }
@@ -301,6 +303,12 @@ class Population:
     def energies_to_device(self, dev_ptr: int):
         _check(self.lib.pa_energy(self._ctx, ctypes.c_void_p(dev_ptr), 1), "pa_energy")
 
+    def occupations(self) -> np.ndarray:
+        """Per-replica occupation of the most common state (Eq. 5)."""
+        out = np.zeros(self.size(), dtype=np.int32)
+        _check(self.lib.pa_occupations(self._ctx, _ptr(out), 0), "pa_occupations")
+        return out
+
     def spins(self, begin: int = 0, count: int | None = None) -> np.ndarray:
         if count is None:
             count = self.size() - begin
@@ -444,3 +452,12 @@ class Batch:
         out = np.zeros((count, L, L), dtype=np.uint8)
         _check(self.lib.pa_batch_get_spins(self._b, m, begin, count, _ptr(out)), "pa_batch_get_spins")
         return out
+
+    def measurements(self, m: int):
+        """(E, Mt) of run m's current population: energies (Eq. 3) and
+        occupations of the most common state (Eq. 5)."""
+        n = self.size(m)
+        E = np.zeros(n, dtype=np.int32)
+        Mt = np.zeros(n, dtype=np.int32)
+        _check(self.lib.pa_batch_measurements(self._b, m, _ptr(E), _ptr(Mt)), "pa_batch_measurements")
+        return E, Mt

@@ -1,13 +1,15 @@
 """Post-processing of population histograms (Sec. 4 of arXiv:1704.01888).
 
 The energy histogram of a population (hist[k] = number of replicas with
-E = k - 2N, as returned by the library) is rebinned and reduced to the full
-width at half maximum, which the paper uses to follow the broadening of the
-distribution near a first-order transition: the distance between the two
-intersections of the histogram with the line at half its maximum.  Reading:
-the intersections are the outermost half-maximum crossings, located by linear
-interpolation between neighbouring bins.  Plain numpy on data already copied
-to the host; nothing here touches the device.
+E = k - 2N, as returned by the library) and the histogram of the replicas'
+magnetisations m_j = (q Mt_j / N - 1) / (q - 1) (Eq. 5, from the occupations
+Mt_j of the most common state) are reduced to their full widths at half
+maximum, which the paper uses to follow the broadening of the distributions
+near a first-order transition: the distance between the two intersections of
+the histogram with the line at half its maximum.  Reading: the intersections
+are the outermost half-maximum crossings, located by linear interpolation
+between neighbouring bins.  Plain numpy on data already copied to the host;
+nothing here touches the device.
 """
 from __future__ import annotations
 
@@ -63,3 +65,30 @@ def peaks(h: np.ndarray, min_separation: int = 2, rel_height: float = 0.2):
         if all(abs(i - j) >= min_separation for j in out):
             out.append(i)
     return sorted(out)
+
+
+def magnetisation(q: int, N: int, Mt: np.ndarray) -> np.ndarray:
+    """m_j = (q Mt_j / N - 1) / (q - 1), the magnetisation of Eq. 5 per replica."""
+    return (q * np.asarray(Mt, dtype=np.float64) / N - 1.0) / (q - 1.0)
+
+
+def energy_histogram(E: np.ndarray, N: int) -> np.ndarray:
+    """hist[k] = number of replicas with E = k - 2N (the library's layout)."""
+    E = np.asarray(E, dtype=np.int64)
+    return np.bincount(E + 2 * N, minlength=2 * N + 1)
+
+
+def widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, e_bin: int = 4, m_bins: int = 60):
+    """(omega_e, omega_m): FWHM of the energy-per-site histogram (bins of
+    e_bin energy units) and of the magnetisation histogram (m_bins equal bins
+    spanning the population's range of m, so that the bins stay narrower than
+    the distribution at every L) of one population."""
+    N = L * L
+    x, h = rebin_energy_histogram(energy_histogram(E, N), N, e_bin)
+    m = magnetisation(q, N, Mt)
+    lo, hi = float(m.min()), float(m.max())
+    if hi <= lo:
+        return fwhm(x, h), 0.0
+    hm, edges = np.histogram(m, bins=m_bins, range=(lo, hi))
+    xm = 0.5 * (edges[:-1] + edges[1:])
+    return fwhm(x, h), fwhm(xm, hm)

@@ -688,6 +688,18 @@ pa_status pa_batch_population_size(pa_batch *b, int32_t m, int32_t *R_out)
     return h.err ? (pa_status)h.err : PA_OK;
 }
 
+pa_status pa_batch_measurements(pa_batch *b, int32_t m, int32_t *E_out, int32_t *Mt_out)
+{
+    if (!b || m < 0 || m >= b->M) return PA_ERR_INVALID;
+    PB_CK(cudaStreamSynchronize(b->stream));
+    const pa::RunDev &r = b->runs_h[m];
+    pa::DevState h;
+    PB_CK(cudaMemcpy(&h, r.st, sizeof(h), cudaMemcpyDeviceToHost));
+    if (E_out) PB_CK(cudaMemcpy(E_out, r.E, sizeof(int32_t) * h.pop, cudaMemcpyDeviceToHost));
+    if (Mt_out) PB_CK(cudaMemcpy(Mt_out, r.Mt, sizeof(int32_t) * h.pop, cudaMemcpyDeviceToHost));
+    return h.err ? (pa_status)h.err : PA_OK;
+}
+
 void pa_batch_destroy(pa_batch *b)
 {
     if (!b) return;

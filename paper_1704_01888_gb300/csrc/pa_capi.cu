@@ -597,6 +597,18 @@ pa_status pa_energy(pa_ctx *c, int32_t *E_out, int32_t on_device)
     return PA_OK;
 }
 
+pa_status pa_occupations(pa_ctx *c, int32_t *Mt_out, int32_t on_device)
+{
+    if (!c || !Mt_out) return PA_ERR_INVALID;
+    pa::DevState h;
+    pa_status s = sync_state(c, &h);
+    if (s) return s;
+    PA_CK(cudaMemcpyAsync(Mt_out, c->Mt, sizeof(int32_t) * h.pop,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) PA_CK(cudaStreamSynchronize(c->stream));
+    return PA_OK;
+}
+
 pa_status pa_observables_history(pa_ctx *c, int32_t count, pa_obs *out)
 {
     if (!c || !out || count < 1) return PA_ERR_INVALID;

@@ -100,3 +100,20 @@ def scaled(wl: Workload, R: int | None = None, K: int | None = None, name: str |
     return Workload(name or wl.name + "-scaled", q=wl.q, L=wl.L, R=wl.R if R is None else R, K=K2,
                     beta_end=wl.beta_end * K2 / wl.K, theta=wl.theta, seed=wl.seed, hist_bin=wl.hist_bin,
                     track_families=wl.track_families)
+
+
+def width_study_runs(seed: int = 1, qs=(6, 8, 10, 20), Ls=(16, 32, 64, 128, 256), R: int = 1000,
+                     theta: int = 100, K: int = 100):
+    """Histogram-width study in the style of the paper's Table I (Sec. 4): for
+    each q and L a population of R = 1000 replicas, theta = 100 sweeps per
+    step, cooled in K equal steps from beta = 0 to beta_t(q) = ln(1 + sqrt q);
+    the energy and magnetisation histograms are taken at the last step.  All
+    runs share the seed; run m has stream m."""
+    runs = []
+    m = 0
+    for q in qs:
+        for L in Ls:
+            runs.append(Workload(f"width-q{q}-L{L}", q=q, L=L, R=R, K=K, beta_end=beta_t(q), theta=theta,
+                                 seed=seed, stream=m))
+            m += 1
+    return runs

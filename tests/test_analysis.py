@@ -33,3 +33,31 @@ def test_rebin_energy_histogram():
     assert e[0] == pytest.approx((-32 + 1.5) / 16)
     e1, c1 = analysis.rebin_energy_histogram(hist, N)
     assert np.array_equal(c1, hist) and e1[0] == -2.0 and e1[-1] == 0.0
+
+
+def test_magnetisation_and_energy_histogram():
+    q, L = 10, 8
+    N = L * L
+    Mt = np.array([N, N // q + 0, 40])
+    m = analysis.magnetisation(q, N, Mt)
+    assert m[0] == pytest.approx(1.0)              # ordered: every site in one state
+    assert m[1] == pytest.approx((q * (N // q) / N - 1) / (q - 1))
+    assert m[2] == pytest.approx((10 * 40 / 64 - 1) / 9)
+    assert analysis.magnetisation(q, N, [N / q])[0] == pytest.approx(0.0)  # equal occupations
+    E = np.array([-2 * N, -2 * N, -3, 0])
+    h = analysis.energy_histogram(E, N)
+    assert h.size == 2 * N + 1 and h[0] == 2 and h[2 * N - 3] == 1 and h[2 * N] == 1 and h.sum() == 4
+
+
+def test_widths_of_gaussian_populations():
+    rng = np.random.default_rng(5)
+    q, L = 8, 32
+    N = L * L
+    R = 400000
+    E = np.clip(np.round(rng.normal(-1.2 * N, 40.0, R)), -2 * N, 0).astype(np.int32)
+    m_target = rng.normal(0.5, 0.08, R)
+    Mt = np.round((m_target * (q - 1) + 1) * N / q).astype(np.int32)
+    we, wm = analysis.widths(q, L, E, Mt, e_bin=4, m_bins=120)
+    c = 2 * math.sqrt(2 * math.log(2))
+    assert we == pytest.approx(c * 40.0 / N, rel=0.05)
+    assert wm == pytest.approx(c * 0.08, rel=0.05)

@@ -33,10 +33,12 @@ def _mixed_runs():
     return runs
 
 
-def _lone(p, betas, theta):
+def _lone(p, betas, theta, measurements=False):
     with pa.Population(p) as pop:
         obs0 = pop.observables()
         obs, _ = pop.run(betas, theta)
+        if measurements:
+            return [obs0] + obs, pop.spins(), (pop.energies(), pop.occupations())
         return [obs0] + obs, pop.spins()
 
 
@@ -46,13 +48,15 @@ def test_batch_runs_equal_lone_runs(graph):
     with pa.Batch(runs) as b:
         b.run(use_graph=graph)
         got = [(b.observables(m), b.spins(m, 0, b.observables(m)[-1]["R"])) for m in range(len(runs))]
+        meas = [b.measurements(m) for m in range(len(runs))]
     for m, (p, betas, theta) in enumerate(runs):
-        obs, spins = _lone(p, betas, theta)
+        obs, spins, (E, Mt) = _lone(p, betas, theta, measurements=True)
         bobs, bspins = got[m]
         assert [o["sumE"] for o in bobs] == [o["sumE"] for o in obs], m
         assert [o["lnZ"] for o in bobs] == [o["lnZ"] for o in obs], m
         assert [o["R"] for o in bobs] == [o["R"] for o in obs], m
         assert np.array_equal(bspins, spins), m
+        assert np.array_equal(meas[m][0], E) and np.array_equal(meas[m][1], Mt), m
 
 
 def test_batch_launch_shapes_and_autotune_do_not_change_results():

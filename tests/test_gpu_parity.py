@@ -51,7 +51,8 @@ def _gpu_run(q, L, R, seed, theta, betas, mode=pa.RESAMPLE_NEAREST_INT, init=pa.
         else:
             obs, hs = pop.run(betas, theta, hist_steps=hist_steps, use_graph=graph)
             hists = {s: hs[k] for k, s in enumerate(hist_steps)}
-        out = {"obs": [obs0] + list(obs), "spins": pop.spins(), "E": pop.energies(), "hists": hists}
+        out = {"obs": [obs0] + list(obs), "spins": pop.spins(), "E": pop.energies(), "hists": hists,
+               "Mt": pop.occupations(), "q": q}
         _, out["hist_final"] = pop.observables(with_hist=True)
         if fam:
             out["anc"] = pop.ancestors()
@@ -81,6 +82,8 @@ def _compare(g, o, fam=False, check_hists=True):
     assert g["spins"].shape[0] == Rf
     assert np.array_equal(g["spins"], o["spins"])
     assert np.array_equal(g["E"], o["E"])
+    # occupations of the most common state (Eq. 5) against the oracle's count on its own spins
+    assert np.array_equal(g["Mt"], [oracle.max_count(g["q"], s) for s in o["spins"]])
     assert np.array_equal(g["hist_final"], o["hist"][K])
     if check_hists:
         for s, h in g["hists"].items():
