@@ -85,10 +85,13 @@ def widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, e_bin: int = 4, m_bins
     the distribution at every L) of one population."""
     N = L * L
     x, h = rebin_energy_histogram(energy_histogram(E, N), N, e_bin)
-    m = magnetisation(q, N, Mt)
-    lo, hi = float(m.min()), float(m.max())
+    # m takes the discrete values of Mt = 1..N: bins of a whole number of Mt
+    # values avoid the aliasing of bins that straddle a varying count of them
+    Mt = np.asarray(Mt, dtype=np.int64)
+    lo, hi = int(Mt.min()), int(Mt.max())
     if hi <= lo:
         return fwhm(x, h), 0.0
-    hm, edges = np.histogram(m, bins=m_bins, range=(lo, hi))
-    xm = 0.5 * (edges[:-1] + edges[1:])
-    return fwhm(x, h), fwhm(xm, hm)
+    width = max(1, -(-(hi - lo + 1) // m_bins))
+    counts = np.bincount((Mt - lo) // width)
+    centres = magnetisation(q, N, lo + width * np.arange(counts.size) + (width - 1) / 2.0)
+    return fwhm(x, h), fwhm(centres, counts)

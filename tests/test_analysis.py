@@ -57,7 +57,7 @@ def test_widths_of_gaussian_populations():
     E = np.clip(np.round(rng.normal(-1.2 * N, 40.0, R)), -2 * N, 0).astype(np.int32)
     m_target = rng.normal(0.5, 0.08, R)
     Mt = np.round((m_target * (q - 1) + 1) * N / q).astype(np.int32)
-    we, wm = analysis.widths(q, L, E, Mt, e_bin=4, m_bins=120)
+    we, wm = analysis.widths(q, L, E, Mt, e_bin=4, m_bins=100)
     c = 2 * math.sqrt(2 * math.log(2))
     assert we == pytest.approx(c * 40.0 / N, rel=0.05)
     assert wm == pytest.approx(c * 0.08, rel=0.05)
