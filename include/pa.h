@@ -104,16 +104,21 @@ typedef struct {
 
 typedef struct pa_ctx pa_ctx;
 
-/* Creates a context, allocates its device buffers (two spin buffers of R_cap*N
- * bytes plus O(R_cap + N) words) and enqueues the initial population at
+/* Creates a context, allocates its device buffers (two spin buffers of R_cap
+ * replicas in the multi-spin-coded layout below, plus O(R_cap + N) words) and
+ * enqueues the initial population at
  * cfg->beta0 (Sec. 2 step 1 or Sec. 5 Eq. 6) with its energies, largest-state
  * occupations, energy histogram and step-0 estimators.
  * Errors: PA_ERR_INVALID for q outside 2..128, odd or out-of-range L, R < 1,
  * R_cap < R or R_cap >= 2^24, beta0 < 0, an unknown mode, or a stream outside
  * 0..255; PA_ERR_TOO_LARGE when a replica's bit planes exceed 204800 bytes
- * (a sweep block keeps whole lattices in shared memory; a replica takes
- * 2 L ceil(L/64) P 4 bytes, P = ceil(log2 q) rounded up to 1, 2, 4 or 8, so
- * L <= 640 for q <= 16 and L <= 448 for q <= 128); PA_ERR_NOMEM or
+ * (a sweep block keeps whole lattices in shared memory).  Device layout of a
+ * replica: a state takes B = ceil(log2 q) bits, stored as P bit planes (B
+ * rounded up to 1, 2, 4 or 8); the sites of each colour ((x + y) mod 2) are
+ * packed 32 to a 32-bit word per plane (row-major over the colour's sites
+ * when L/2 divides 32, else each row padded to whole words), so a replica
+ * takes 2 W P 4 bytes, W = L^2/64 or L ceil(L/64) words per colour: L <= 640
+ * for q <= 16 and L <= 448 for q <= 128.  PA_ERR_NOMEM or
  * PA_ERR_CUDA if allocation or a launch fails (nothing is leaked; *out = NULL). */
 pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 
@@ -283,7 +288,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
  * Only before pa_batch_run (PA_ERR_STATE after). */
 pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *threads_out);
 
-/* Sets the budget (bytes, >= the largest lattice) and threads per block
+/* Sets the budget (bytes, >= the largest replica) and threads per block
  * (multiple of 32, 64..1024) by hand; PA_ERR_INVALID if they do not fit. */
 pa_status pa_batch_set_launch(pa_batch *b, int32_t smem_budget, int32_t threads);
 
@@ -321,7 +326,8 @@ void pa_batch_destroy(pa_batch *b);
  * estimators, with a checksum.  The random numbers are counter-based, so a
  * run resumed with pa_load continues bit for bit as the uninterrupted run.
  * Synchronises.  PA_ERR_STATE with a resample pending or a failed context;
- * PA_ERR_INVALID if the file cannot be written.  Files are read back on
+ * PA_ERR_INVALID if the file cannot be written.  Spins are stored in the
+ * device layout (format version 2); files are read back by this library on
  * machines of the same byte order. */
 pa_status pa_save(pa_ctx *ctx, const char *path);
 
