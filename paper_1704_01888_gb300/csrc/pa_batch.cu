@@ -229,8 +229,6 @@ __global__ void k_batch_advance(int32_t *step_counter)
     if (threadIdx.x == 0 && blockIdx.x == 0) *step_counter += 1;
 }
 
-size_t batch_smem(int budget) { return (size_t)budget; }
-
 }  // namespace
 
 }  // namespace pa

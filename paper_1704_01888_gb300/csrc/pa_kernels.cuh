@@ -293,7 +293,7 @@ __device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0,
 }
 
 // Multi-spin-coded sweep body.  B = bits per state (compile time), MODE as
-// for shifted_row.  Each loop step of a thread updates one site word: 32
+// for neighbour_planes, Q = q when fixed at compile time (0: q from G).  Each loop step of a thread updates one site word: 32
 // same-colour sites of one row.  The random numbers follow this rule: in
 // sweep k, colour c, the site word with index w = y WPR + t draws the stream
 // Z_0, Z_1, ... (Z_{4n+i} = word i of the Philox call with counter
@@ -305,7 +305,7 @@ __device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0,
 // indicator bits (neighbours equal to s, neighbours different from s'), summed
 // by a carry-save tree; moves with dE > 0 compare v with T[dE] bit by bit, and
 // the warp draws further acceptance words only while some site is undecided.
-template <int B, int MODE>
+template <int B, int MODE, int Q = 0>
 __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32_t *sw, const uint4 *s_tab,
                                                  uint32_t *qbuf, const uint32_t *rk0, const uint32_t *rk1,
                                                  long long &sE, long long &sE2, long long &sM)
@@ -322,7 +322,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int q = G.q;
+    const int q = Q > 0 ? Q : G.q;  // Q > 0: q fixed at compile time, the mod-q masks fold
     const int first = G.first, nrep = G.nrep;
     uint4 *smem4 = reinterpret_cast<uint4 *>(sw);
 

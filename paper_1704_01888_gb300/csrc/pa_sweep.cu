@@ -55,7 +55,7 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
 // B: bits per state; MODE: 0 for L = 64, 1 for L a multiple of 64, 3 for
 // L = 8, 16, 32 (rows packed several to a word), 2 otherwise (rows padded to
 // whole words).
-template <int B, int MODE>
+template <int B, int MODE, int Q>
 __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
 {
     extern __shared__ uint4 smem4[];
@@ -74,8 +74,8 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
     long long sE = 0, sE2 = 0, sM = 0;
     for (int first = begin; first < end; first += a.rpb) {
         const dev::Group G = make_group(a, parity, first, min(a.rpb, end - first));
-        dev::sweep_group_bits<B, MODE>(G, a.L, reinterpret_cast<uint32_t *>(smem4), s_tab, s_queue, a.rk0, a.rk1,
-                                       sE, sE2, sM);
+        dev::sweep_group_bits<B, MODE, Q>(G, a.L, reinterpret_cast<uint32_t *>(smem4), s_tab, s_queue, a.rk0,
+                                          a.rk1, sE, sE2, sM);
     }
     if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(a.acc, sE, sE2, sM);
 }
@@ -94,27 +94,38 @@ cudaError_t prepare(KernelFnPtr kernel)
     return e;
 }
 
+// Kernels for the common q with q fixed at compile time (the reduction mod q
+// then uses constant masks), and one kernel per bit count for any other q.
 template <int MODE>
-KernelFnPtr pick_bits(int B)
+KernelFnPtr pick_q(int q)
 {
-    switch (B) {
-    case 1: return k_sweep<1, MODE>;
-    case 2: return k_sweep<2, MODE>;
-    case 3: return k_sweep<3, MODE>;
-    case 4: return k_sweep<4, MODE>;
-    case 5: return k_sweep<5, MODE>;
-    case 6: return k_sweep<6, MODE>;
-    default: return k_sweep<7, MODE>;
+    switch (q) {
+    case 2: return k_sweep<state_bits(2), MODE, 2>;
+    case 3: return k_sweep<state_bits(3), MODE, 3>;
+    case 4: return k_sweep<state_bits(4), MODE, 4>;
+    case 5: return k_sweep<state_bits(5), MODE, 5>;
+    case 6: return k_sweep<state_bits(6), MODE, 6>;
+    case 8: return k_sweep<state_bits(8), MODE, 8>;
+    case 10: return k_sweep<state_bits(10), MODE, 10>;
+    case 20: return k_sweep<state_bits(20), MODE, 20>;
+    }
+    switch (state_bits(q)) {
+    case 1: return k_sweep<1, MODE, 0>;
+    case 2: return k_sweep<2, MODE, 0>;
+    case 3: return k_sweep<3, MODE, 0>;
+    case 4: return k_sweep<4, MODE, 0>;
+    case 5: return k_sweep<5, MODE, 0>;
+    case 6: return k_sweep<6, MODE, 0>;
+    default: return k_sweep<7, MODE, 0>;
     }
 }
 
 KernelFnPtr pick_kernel(int q, int L)
 {
-    const int B = state_bits(q);
-    if (L == 64) return pick_bits<0>(B);
-    if (L % 64 == 0) return pick_bits<1>(B);
-    if (rows_packed(L)) return pick_bits<3>(B);
-    return pick_bits<2>(B);
+    if (L == 64) return pick_q<0>(q);
+    if (L % 64 == 0) return pick_q<1>(q);
+    if (rows_packed(L)) return pick_q<3>(q);
+    return pick_q<2>(q);
 }
 
 }  // namespace
