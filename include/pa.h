@@ -371,9 +371,10 @@ pa_status pa_profile_read(pa_ctx *ctx, double *ms_out2, int64_t *launches_out2);
 
 /* Resampling without any device allocation.  This call has no counterpart in
  * the paper: it exists for callers that may not allocate device memory --
- * code running while a CUDA graph is being captured in a mode that forbids
- * allocation, plug-ins whose host framework owns every device allocation,
- * and runtimes that must not call the allocator once set up.
+ * plug-ins whose host framework owns every device allocation (a cudaMalloc
+ * behind its back would escape its accounting and limits), and runtimes that
+ * must not call the allocator once set up (an allocation can synchronise the
+ * device or fail under memory pressure in the middle of their work).
  *
  * It computes, for the R_prev energies E[0..R_prev) (device int32, each in
  * [-2N, 0], N = L*L) of a population, the same quantities as pa_resample: ln Q

@@ -3,10 +3,11 @@
 // pa_resample_noalloc() runs the same resampling kernels as pa_resample(), but
 // on caller-owned arrays (energies in, parent map out) and with its working
 // memory taken from one fixed array in the library's own device image
-// instead of cudaMalloc.  It serves callers that may not allocate: code
-// running while a CUDA graph is being captured in a mode that forbids
-// allocation, plug-ins whose host framework owns every device allocation, and
-// runtimes that must not touch the allocator once they are set up.
+// instead of cudaMalloc.  It serves callers that may not allocate: plug-ins
+// whose host framework owns every device allocation (memory taken behind its
+// back escapes its accounting and limits), and runtimes that must not touch
+// the allocator once they are set up (an allocation can synchronise the device
+// or fail under memory pressure in the middle of their work).
 //
 // The array is a file-scope __device__ variable, so every GPU that loads this
 // library holds it (kScratchBytes, about 3.6 MB) until the process exits.

@@ -1,7 +1,6 @@
 """pa_resample_noalloc, the resampling entry point for callers that may not
-allocate device memory (for example code running under a CUDA graph capture
-that forbids allocation, or a plug-in whose host framework owns all device
-memory).  It must give what pa_resample gives on the same population: the
+allocate device memory (for example a plug-in whose host framework owns all
+device memory, or a runtime that must not touch the allocator after set-up).  It must give what pa_resample gives on the same population: the
 same new size, ln Q within the tolerance of the other parity tests, and a
 parent map that reproduces the population pa_resample builds.  Checked on two
 calls in a row (the fixed working memory is reused and must be cleared).
