@@ -386,7 +386,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u8", "data": "synthetic",
+        "dtype": "u32", "data": "synthetic",
         "config": {"workload": w.name, "q": w.q, "L": w.L, "R": w.R, "theta": w.theta,
                    "beta": f"0 -> {w.beta_end} in {w.K} equal steps (timed steps {W + 1}..{W + K})",
                    "parallelism": f"independent populations x{world}",
