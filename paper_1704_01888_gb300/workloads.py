@@ -69,7 +69,7 @@ C2 = Workload("plain-q10-L64-R100000", q=10, L=64, R=100000, K=200, beta_end=1.6
 C2.hist_steps = (nearest_step(C2, beta_t(10)),)
 
 # Differentiable / adaptive case, q = 8, L = 128, R = 200000 (beta range and
-# theta are not given; 1.1 * beta_t and theta = 10 are this build's reading).
+# theta are not given; 1.1 * beta_t and theta = 10 are the reading taken here).
 C4 = Workload("adaptive-q8-L128-R200000", q=8, L=128, R=200000, K=200, beta_end=1.1 * beta_t(8), theta=10)
 
 # Strong first-order case, q = 20, L = 256, R = 100000, 300 steps to 1.9,
