@@ -11,7 +11,7 @@
 // dbeta >= 0, highest otherwise) in a fixed order, with explicitly rounded
 // double operations.
 //
-// Adaptive step (the paper uses constant steps; this is the build's reading):
+// Adaptive step (the paper uses constant steps; this is a reading added here):
 // with mean-one weights t_j = R w_j / S, the overlap of the populations at
 // beta and beta + dbeta is alpha = (1/R) sum_j min(1, t_j), with derivative
 // alpha' = (1/R) sum_{t_j < 1} t_j (<E>_tau - E_j).  The step solves
