@@ -34,12 +34,13 @@ from paper_1704_01888_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "spin-flip attempts/ns & PA steps/s, q=10 L=64 R=1e5; batched vs plain, %roofline"
 UNIT = "attempts/ns"
-# Algorithmic integer issue slots of the multi-spin-coded Metropolis update,
-# per site word (32 same-colour sites, one attempt each) for B = ceil(log2 q)
-# bit planes, a 64-bit product counted as two slots:
-#   Philox4x32-10 words: B for the proposal, ACC_PLANES for the acceptance,
-#     a quarter call each (10 rounds x (2 products x 2 + 2 three-input xors)
-#     = 60 per call): 15 (B + ACC_PLANES);
+# Algorithmic ALU-pipe operations of the multi-spin-coded Metropolis update, per
+# site word (32 same-colour sites, one attempt each) for B = ceil(log2 q) bit
+# planes.  The update is integer logic; its binding unit is the ALU pipe (it
+# executes every three-input logic operation); the 32 x 32 -> 64 bit products of
+# Philox run on the FMA-heavy pipe, which is not binding and is not counted:
+#   Philox4x32-10 words: B for the proposal, ACC_PLANES for the acceptance, a
+#     quarter call each (10 rounds x 2 three-input xors = 20 per call): 5 (B + ACC_PLANES);
 #   proposal s +- (1 + u) mod q: two ripple-carry adders over B and B + 1
 #     planes (3 per plane), the choice of result and its select: 7B + 4;
 #   dE class: eight B-plane equality tests, a carry-save count of the eight
@@ -54,24 +55,16 @@ ACC_PLANES = 6
 
 def ops_per_word(q: int) -> int:
     B = max(1, (q - 1).bit_length())
-    return 15 * (B + ACC_PLANES) + (7 * B + 4) + (8 * B + 17) + 6 * ACC_PLANES + B
+    return 5 * (B + ACC_PLANES) + (7 * B + 4) + (8 * B + 17) + 6 * ACC_PLANES + B
 
 
 def ops_per_attempt(q: int) -> float:
     return ops_per_word(q) / 32.0
 
 
-def replica_bytes(q: int, L: int) -> int:
-    """Device bytes of one replica: 2 colours x site words per colour x P planes
-    x 4 bytes, P = ceil(log2 q) rounded up to 1, 2, 4 or 8; a colour has
-    L^2 / 64 site words when L/2 divides 32 (rows packed), else L ceil(L/64)."""
-    B = max(1, (q - 1).bit_length())
-    P = 1 if B <= 1 else 2 if B <= 2 else 4 if B <= 4 else 8
-    words = L * L // 64 if (L >= 8 and 64 % L == 0) else L * ((L + 63) // 64)
-    return (2 * words * P + 3) // 4 * 4 * 4
-
-
-LANES_PER_SM_PER_CLK = 128  # 4 schedulers x 32 lanes issue one integer op each per clock
+# ALU pipe: 4 schedulers x 16 lanes per SM and clock (ncu counts its peak as half a
+# warp instruction per scheduler and cycle)
+LANES_PER_SM_PER_CLK = 64
 PA_OBS_BYTES = 104
 DEVSTATE_BYTES = 48
 
@@ -362,7 +355,7 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": 2 * replica_bytes(w.q, w.L) * per_launch_replicas,
                 "kernel": "k_sweep", "ops_per_attempt": ops_per_attempt(w.q),
                 "kernel_ms_avg": sweep_avg_s * 1e3, "kernel_share": sweep_ms / elapsed_ms,
-                "peak_basis": f"{sms} SMs x {LANES_PER_SM_PER_CLK} lanes x {f_max / 1e6:.0f} MHz (max SM clock)"}
+                "peak_basis": f"ALU pipe: {sms} SMs x {LANES_PER_SM_PER_CLK} lanes x {f_max / 1e6:.0f} MHz (max SM clock)"}
     issue = _sweep_issue_active()
     if issue is not None:
         roofline["issue_active_ncu"] = issue
