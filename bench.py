@@ -62,6 +62,16 @@ def ops_per_attempt(q: int) -> float:
     return ops_per_word(q) / 32.0
 
 
+def replica_bytes(q: int, L: int) -> int:
+    """Device bytes of one replica: 2 colours x site words per colour x P planes
+    x 4 bytes, P = ceil(log2 q) rounded up to 1, 2, 4 or 8; a colour has
+    L^2 / 64 site words when L/2 divides 32 (rows packed), else L ceil(L/64)."""
+    B = max(1, (q - 1).bit_length())
+    P = 1 if B <= 1 else 2 if B <= 2 else 4 if B <= 4 else 8
+    words = L * L // 64 if (L >= 8 and 64 % L == 0) else L * ((L + 63) // 64)
+    return (2 * words * P + 3) // 4 * 4 * 4
+
+
 # ALU pipe: 4 schedulers x 16 lanes per SM and clock (ncu counts its peak as half a
 # warp instruction per scheduler and cycle)
 LANES_PER_SM_PER_CLK = 64

@@ -48,3 +48,39 @@ def test_reduce_over_two_gloo_ranks():
     assert [r[1] for r in res] == [15.0, 15.0]
     assert [r[2] for r in res] == [3000.0, 3000.0]
     assert [r[3] for r in res] == [1, 2]
+
+
+def test_bench_helpers_and_global_names():
+    """The benchmark's layout and roofline helpers give the documented figures,
+    and every global name its functions read exists (a code path that only runs
+    on a GPU machine must not fail there on a missing helper)."""
+    import builtins
+    import dis
+    import types
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.replica_bytes(10, 64) == 2048
+    assert bench.replica_bytes(10, 16) == 128
+    assert bench.replica_bytes(20, 256) == 65536
+    assert bench.replica_bytes(2, 8) == 16        # 2 words padded to 4
+    assert bench.ops_per_word(10) == 171
+
+    missing = set()
+
+    def visit(code):
+        for ins in dis.get_instructions(code):
+            if ins.opname == "LOAD_GLOBAL":
+                name = ins.argval if isinstance(ins.argval, str) else str(ins.argval)
+                name = name.split(" + ")[-1].replace("NULL + ", "")
+                if not hasattr(bench, name) and not hasattr(builtins, name):
+                    missing.add((code.co_name, name))
+        for c in code.co_consts:
+            if isinstance(c, types.CodeType):
+                visit(c)
+
+    for obj in vars(bench).values():
+        if isinstance(obj, types.FunctionType) and obj.__module__ == "bench":
+            visit(obj.__code__)
+    assert not missing, sorted(missing)
