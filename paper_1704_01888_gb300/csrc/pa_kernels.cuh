@@ -292,6 +292,39 @@ __device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0,
     return (e1 & hi) | (~e1 & lo);
 }
 
+// One bit plane j of the acceptance numbers v (bits of the word v_bits): sites
+// still undecided accept where v's bit is 0 and T's is 1, and stay undecided
+// where the two bits agree.
+__device__ __forceinline__ void acceptance_plane(uint32_t v_bits, int j, const uint4 *s_tab, uint32_t c0, uint32_t e1,
+                                                 uint32_t &acc, uint32_t &und)
+{
+    const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
+    acc |= und & ~v_bits & tj;
+    und &= ~(v_bits ^ tj);
+}
+
+// Acceptance words of Philox calls n = ch_begin .. ch_end - 1 of a site word's
+// stream (words 4n .. 4n + 3, i.e. planes j = 4n - B ..), drawn while a site is
+// undecided: in the whole warp (WARP_VOTE, all lanes must take part) or in this
+// thread's word alone.
+template <int B, bool WARP_VOTE>
+__device__ __forceinline__ void acceptance_calls(int ch_begin, int ch_end, uint32_t w, uint32_t ctr1, uint32_t step,
+                                                 uint32_t slot, const uint32_t *rk0, const uint32_t *rk1,
+                                                 const uint4 *s_tab, uint32_t c0, uint32_t e1, uint32_t &acc,
+                                                 uint32_t &und)
+{
+#pragma unroll 1
+    for (int ch = ch_begin; ch < ch_end; ++ch) {
+        if (WARP_VOTE ? !__any_sync(0xFFFFFFFFu, und) : !und) break;
+        const uint4 z = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, step, slot), rk0, rk1);
+        const int j0 = 4 * ch - B;
+        acceptance_plane(z.x, j0, s_tab, c0, e1, acc, und);
+        acceptance_plane(z.y, j0 + 1, s_tab, c0, e1, acc, und);
+        acceptance_plane(z.z, j0 + 2, s_tab, c0, e1, acc, und);
+        acceptance_plane(z.w, j0 + 3, s_tab, c0, e1, acc, und);
+    }
+}
+
 // Multi-spin-coded sweep body.  B = bits per state (compile time), MODE as
 // for neighbour_planes, Q = q when fixed at compile time (0: q from G).  Each loop step of a thread updates one site word: 32
 // same-colour sites of one row.  The random numbers follow this rule: in
@@ -440,29 +473,17 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     acc |= und & tj;
                     und &= ~tj;
                 }
-                auto plane = [&](uint32_t v, int j) {
-                    const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
-                    acc |= und & ~v & tj;
-                    und &= ~(v ^ tj);
-                };
                 // acceptance bit j is word B + j: the rest of the last proposal call first
                 if constexpr (B % 4 != 0) {
                     if (__any_sync(0xFFFFFFFFu, und)) {
 #pragma unroll
-                        for (int wi = B; wi < 4 * ((B + 3) / 4); ++wi) plane(Z[wi], wi - B);
+                        for (int wi = B; wi < 4 * ((B + 3) / 4); ++wi)
+                            acceptance_plane(Z[wi], wi - B, s_tab, c0, e1, acc, und);
                     }
                 }
                 constexpr int fc = (B + 3) / 4;
-#pragma unroll 1
-                for (int ch = fc; ch < fc + kFirstPassCalls; ++ch) {
-                    if (!__any_sync(0xFFFFFFFFu, und)) break;
-                    const uint4 za = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
-                    const int j0 = 4 * ch - B;
-                    plane(za.x, j0);
-                    plane(za.y, j0 + 1);
-                    plane(za.z, j0 + 2);
-                    plane(za.w, j0 + 3);
-                }
+                acceptance_calls<B, true>(fc, fc + kFirstPassCalls, w, ctr1, (uint32_t)G.step, slot, rk0, rk1, s_tab,
+                                          c0, e1, acc, und);
                 bool queued = false;
                 if (und) {
                     const int e = atomicAdd(qc, 1);
@@ -477,15 +498,8 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                         queued = true;
                     } else {
                         // queue full: this thread finishes its word alone (no warp votes)
-                        for (int ch = fc + kFirstPassCalls; und && ch < fc + 8; ++ch) {
-                            const uint4 za =
-                                philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
-                            const int j0 = 4 * ch - B;
-                            plane(za.x, j0);
-                            plane(za.y, j0 + 1);
-                            plane(za.z, j0 + 2);
-                            plane(za.w, j0 + 3);
-                        }
+                        acceptance_calls<B, false>(fc + kFirstPassCalls, fc + 8, w, ctr1, (uint32_t)G.step, slot, rk0,
+                                                   rk1, s_tab, c0, e1, acc, und);
                     }
                 }
                 if (live && !queued) {
@@ -509,22 +523,9 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 const uint32_t c0 = q_mask[2][ee], e1 = q_mask[3][ee];
                 const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
                 const uint32_t w = (uint32_t)it;
-                auto plane = [&](uint32_t v, int j) {
-                    const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
-                    acc |= und & ~v & tj;
-                    und &= ~(v ^ tj);
-                };
                 constexpr int fc = (B + 3) / 4;
-#pragma unroll 1
-                for (int ch = fc + kFirstPassCalls; ch < fc + 8; ++ch) {
-                    if (!__any_sync(0xFFFFFFFFu, und)) break;
-                    const uint4 za = philox10_rk(make_uint4(w, ctr1 | (uint32_t)ch, (uint32_t)G.step, slot), rk0, rk1);
-                    const int j0 = 4 * ch - B;
-                    plane(za.x, j0);
-                    plane(za.y, j0 + 1);
-                    plane(za.z, j0 + 2);
-                    plane(za.w, j0 + 3);
-                }
+                acceptance_calls<B, true>(fc + kFirstPassCalls, fc + 8, w, ctr1, (uint32_t)G.step, slot, rk0, rk1,
+                                          s_tab, c0, e1, acc, und);
                 if (live) {
                     uint32_t *own = sw + r * RW + (c * IPC + it) * BP;
                     uint32_t W[BP];
