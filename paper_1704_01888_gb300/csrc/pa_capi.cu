@@ -170,8 +170,13 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
     if ((size_t)rpb * RB > (size_t)pa::kMaxLatticeBytes) return rpb == 1 ? PA_ERR_TOO_LARGE : PA_ERR_INVALID;
     int threads = threads_req;
     if (threads <= 0) {
+        // one thread per site word, at most 512; a block that holds a single
+        // large replica takes about four words per thread instead (measured
+        // best at q = 20, L = 256: fewer words per thread leave the barriers
+        // and the queue pass of each half sweep poorly amortised)
         const long long work = (long long)rpb * units;
-        threads = (int)((work + 31) / 32 * 32);
+        const long long per_thread = rpb == 1 ? 4 : 1;
+        threads = (int)(((work + per_thread - 1) / per_thread + 31) / 32 * 32);
         if (threads > 512) threads = 512;
         if (threads < 32) threads = 32;
     }
