@@ -12,6 +12,8 @@
 //               block-local exclusive scan (warp shuffles).
 //   k_scatter   block offsets, the new population size R_i (checked against
 //               the capacity) and the parent map parent[off_j + c] = j.
+//   k_resample_small  the three stages above in one block, for capacities
+//               of at most 4096 replicas.
 //   k_finalize  Sec. 2 step 4 / Sec. 3 Eq. 4: population averages from exact
 //               integer sums, the fluctuation-formula specific heat, the
 //               magnetisation of Eq. 5, ln Z of Eq. 2 and the family entropy.
@@ -60,6 +62,36 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t *counts, const
     dev::scatter_body(blockIdx.x, gridDim.x, counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st, s_l);
 }
 
+// Small populations (R_cap <= kSmallResample replicas): the three resampling
+// stages in one block, one after the other, with the bodies of k_weights,
+// k_counts and k_scatter run chunk by chunk.  Same arithmetic and the same
+// results; two launches fewer per step where launch latency dominates.
+constexpr int kSmallResample = 4 * kBlock;
+
+__global__ void __launch_bounds__(kBlock) k_resample_small(const int32_t *hist, int nbins, const int32_t *E,
+                                                           double dbeta, int R_target, int R_cap, int mode, int step,
+                                                           uint32_t stream_hi, uint32_t k0, uint32_t k1, double *wtab,
+                                                           int32_t *counts, int32_t *local_off, int32_t *blocksum,
+                                                           int32_t *parent, int32_t *hist_zero, DevState *st)
+{
+    __shared__ double s_d[32];
+    __shared__ long long s_l[32];
+    __shared__ int s_i[32];
+    dev::weights_body(hist, nbins, dbeta, st, wtab, s_d, s_l);
+    __syncthreads();
+    const int nb = (R_cap + kBlock - 1) / kBlock;
+    for (int chunk = 0; chunk < nb; ++chunk) {
+        dev::counts_body(chunk, E, nbins - 1, R_target, mode, step, stream_hi, k0, k1, wtab, counts, local_off,
+                         blocksum, st, s_i);
+        __syncthreads();
+    }
+    const int nb2 = nb > (nbins + kBlock - 1) / kBlock ? nb : (nbins + kBlock - 1) / kBlock;
+    for (int chunk = 0; chunk < nb2; ++chunk) {
+        dev::scatter_body(chunk, nb2, counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st, s_l);
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kBlock) k_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0,
                                                      DevObs *obs, double beta, int q, int N, int gathered,
                                                      int resampled)
@@ -101,6 +133,12 @@ cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, do
                             int32_t *counts, int32_t *local_off, int32_t *blocksum, int32_t *parent,
                             int32_t *hist_zero, DevState *st, cudaStream_t s)
 {
+    if (R_cap <= kSmallResample) {
+        k_resample_small<<<1, kBlock, 0, s>>>(hist, nbins, E, dbeta, R_target, R_cap, mode, step, stream_hi, k0, k1,
+                                              wtab, counts, local_off, blocksum, parent, hist_zero, st);
+        bump_launch_count(1);
+        return cudaGetLastError();
+    }
     const int nb = (R_cap + kBlock - 1) / kBlock;
     k_weights<<<1, kBlock, 0, s>>>(hist, nbins, dbeta, st, wtab);
     k_counts<<<nb, kBlock, 0, s>>>(E, nbins - 1, R_target, mode, step, stream_hi, k0, k1, wtab, counts, local_off,

@@ -184,8 +184,23 @@ def test_families_cooling():
     _compare(g, o, fam=True)
 
 
-def test_capacity_overflow_keeps_previous_population():
-    q, L, R = 10, 16, 1000
+@pytest.mark.parametrize("mode", [pa.RESAMPLE_NEAREST_INT, pa.RESAMPLE_ROUND, pa.RESAMPLE_POISSON,
+                                  pa.RESAMPLE_OFF])
+def test_single_and_multi_block_resampling_bit_exact(mode):
+    """Capacities up to 4096 replicas resample in one block that runs the
+    weight, copy-number and scatter stages in turn; larger capacities use one
+    kernel per stage over many blocks.  Both against the oracle."""
+    q, L, R, K = 8, 16, 700, 10
+    b = np.array([1.5 * i / K for i in range(K + 1)])
+    for cap in (0, 5000):
+        g = _gpu_run(q, L, R, 13, 3, b, mode=mode, R_cap=cap)
+        o = _oracle_run(q, L, R, 13, 3, b, mode=mode, R_cap=cap or None)
+        _compare(g, o)
+
+
+@pytest.mark.parametrize("R", [1000, 5000])
+def test_capacity_overflow_keeps_previous_population(R):
+    q, L = 10, 16
     p = pa.PAParams(q=q, L=L, R=R, seed=3, R_cap=R)
     with pa.Population(p) as pop:
         beta = 0.0
@@ -202,9 +217,11 @@ def test_capacity_overflow_keeps_previous_population():
             beta += 0.05
             pop.sweep(beta, 2, i)
         assert hit, "population never exceeded a capacity equal to R"
-        # the context is usable again at the previous step
-        pop.resample(0.0, i + 1, sync=True)
-        pop.sweep(beta, 1, i + 1)
+        # the context is usable again at the previous step (a resample with
+        # dbeta = 0 could itself overflow: rho_j = R / R_{i-1} > 1 when the
+        # population has shrunk below R)
+        pop.sweep(beta, 1, i - 1)
+        assert pop.energies().shape[0] == before.shape[0]
 
 
 def test_call_order_is_enforced():
