@@ -84,11 +84,21 @@ __global__ void k_batch_init(const BatchArgs b)
     }
 }
 
-// The sweep body for a run's bits per state and row geometry.
+// The sweep body for a run's q (q = 5, 6, 8, 10 fixed at compile time, so
+// that the reduction mod q uses constant masks), else its bits per state, and
+// its row geometry.
 template <int MODE>
-__device__ __forceinline__ void batch_body(int B, const dev::Group &G, int L, uint32_t *sw, const uint4 *s_tab,
-                                           uint32_t *q, const BatchArgs &b, long long &sE, long long &sE2, long long &sM)
+__device__ __forceinline__ void batch_body(int qv, int B, const dev::Group &G, int L, uint32_t *sw,
+                                           const uint4 *s_tab, uint32_t *q, const BatchArgs &b, long long &sE,
+                                           long long &sE2, long long &sM)
 {
+    switch (qv) {
+    case 5: dev::sweep_group_bits<3, MODE, 5>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
+    case 6: dev::sweep_group_bits<3, MODE, 6>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
+    case 8: dev::sweep_group_bits<3, MODE, 8>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
+    case 10: dev::sweep_group_bits<4, MODE, 10>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
+    default: break;
+    }
     switch (B) {
     case 1: dev::sweep_group_bits<1, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
     case 2: dev::sweep_group_bits<2, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
@@ -201,13 +211,13 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
         uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);
         const int B = state_bits(r.q);
         if (r.L == 64)
-            batch_body<0>(B, G, 64, sw, s_tab, s_queue, b, sE, sE2, sM);
+            batch_body<0>(r.q, B, G, 64, sw, s_tab, s_queue, b, sE, sE2, sM);
         else if (r.L % 64 == 0)
-            batch_body<1>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
+            batch_body<1>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         else if (rows_packed(r.L))
-            batch_body<3>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
+            batch_body<3>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         else
-            batch_body<2>(B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
+            batch_body<2>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(r.acc, sE, sE2, sM);
     }
 }
