@@ -267,28 +267,34 @@ constexpr int kThresholdFull = 40;
 constexpr int kFirstPassCalls = 2;
 constexpr int kQueueCap = 256;
 __host__ __device__ constexpr int queue_words(int B) { return 2 + (5 + B) * kQueueCap; }
+// Entry j holds, for the threshold bits t_1..t_4 of plane j (bit 31 - j of
+// T[1..4]), the coefficients of two multiply-adds: c0 * (t_1 - t_2) - t_2
+// gives the threshold bits of the dE = 1, 2 sites (c0: dE odd) and
+// c0 * (t_3 - t_4) - t_4 those of the dE = 3, 4 sites, bit for bit: the four
+// results 0, c0, ~c0 = -c0 - 1 and ~0 are the four two-way selections.  The
+// selections thus run on the multiply-add pipe; only the choice by e1 is a
+// logic operation.
 __device__ __forceinline__ void build_threshold_table(uint4 *tab, const Thresholds &th)
 {
-    auto m = [](uint32_t bit) { return bit ? 0xFFFFFFFFu : 0u; };
+    auto coef = [](uint32_t ta, uint32_t tb) { return make_uint2(ta - tb, 0u - tb); };
     for (int j = threadIdx.x; j < kThresholdEntries; j += blockDim.x) {
+        uint32_t t[4] = {0u, 0u, 0u, 0u};
         if (j < 32) {
-            const int b = 31 - j;
-            tab[j] = make_uint4(m((th.T[0] >> b) & 1u), m((th.T[1] >> b) & 1u), m((th.T[2] >> b) & 1u),
-                                m((th.T[3] >> b) & 1u));
-        } else if (j < kThresholdFull) {
-            tab[j] = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-            tab[kThresholdFull] = make_uint4(m(th.full & 1u), m(th.full & 2u), m(th.full & 4u), m(th.full & 8u));
+            for (int d = 0; d < 4; ++d) t[d] = (th.T[d] >> (31 - j)) & 1u;
+        } else if (j == kThresholdFull) {
+            for (int d = 0; d < 4; ++d) t[d] = (th.full >> d) & 1u;
         }
+        const uint2 lo = coef(t[0], t[1]), hi = coef(t[2], t[3]);
+        tab[j] = make_uint4(lo.x, lo.y, hi.x, hi.y);
     }
 }
 
 // Threshold bit of plane entry tb for each site: the site's dE class is
-// given by c0 (dE odd) and e1 (dE >= 3): dE = 1, 2, 3, 4 select .x, .y, .z, .w.
+// given by c0 (dE odd) and e1 (dE >= 3).
 __device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0, uint32_t e1)
 {
-    const uint32_t lo = (c0 & tb.x) | (~c0 & tb.y);
-    const uint32_t hi = (c0 & tb.z) | (~c0 & tb.w);
+    const uint32_t lo = c0 * tb.x + tb.y;  // dE = 1 where c0, dE = 2 elsewhere
+    const uint32_t hi = c0 * tb.z + tb.w;  // dE = 3 where c0, dE = 4 elsewhere
     return (e1 & hi) | (~e1 & lo);
 }
 
