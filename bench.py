@@ -45,8 +45,11 @@ UNIT = "attempts/ns"
 #     planes (3 per plane), the choice of result and its select: 7B + 4;
 #   dE class: eight B-plane equality tests, a carry-save count of the eight
 #     indicator bits (14) and the class bits (3): 8B + 17;
-#   acceptance: per plane of v, the threshold-bit select (3) and the compare
-#     update (3): 6 ACC_PLANES;  merge of the accepted proposals: B.
+#   acceptance: per plane of v, the choice between the two threshold-bit
+#     selections by the class bit dE >= 3 (1; the selections themselves are
+#     multiply-adds on the FMA-heavy pipe) and the outcome and undecided
+#     updates (2): 3 ACC_PLANES;  merge of the accepted proposals: the mask of
+#     decided acceptances and B selects, B + 1.
 # ACC_PLANES = 6: a site's comparison of v with T ends at the first differing
 # bit (geometric with mean 2), and a word of 32 such sites needs the largest
 # of 32 such depths, about log2(32) + 1.3.
@@ -55,7 +58,7 @@ ACC_PLANES = 6
 
 def ops_per_word(q: int) -> int:
     B = max(1, (q - 1).bit_length())
-    return 5 * (B + ACC_PLANES) + (7 * B + 4) + (8 * B + 17) + 6 * ACC_PLANES + B
+    return 5 * (B + ACC_PLANES) + (7 * B + 4) + (8 * B + 17) + 3 * ACC_PLANES + B + 1
 
 
 def ops_per_attempt(q: int) -> float:

@@ -261,8 +261,8 @@ constexpr int kThresholdFull = 40;
 // (about 8 % of words at low temperature) goes to a block-wide queue, and in
 // the second pass whole warps serve only queued words, so a warp no longer
 // waits for the slowest of its ~700 sites.  Queue layout in shared memory:
-// two counters, kQueueCap entries of (site-word index, accepted, undecided,
-// class bits c0, e1, B proposal planes).  A full queue is not an error: the
+// two counters, kQueueCap entries of (site-word index, outcome bits acc,
+// undecided, class bits c0, e1, B proposal planes).  A full queue is not an error: the
 // word's own thread finishes it.
 constexpr int kFirstPassCalls = 2;
 constexpr int kQueueCap = 256;
@@ -298,14 +298,16 @@ __device__ __forceinline__ uint32_t threshold_bits(const uint4 &tb, uint32_t c0,
     return (e1 & hi) | (~e1 & lo);
 }
 
-// One bit plane j of the acceptance numbers v (bits of the word v_bits): sites
-// still undecided accept where v's bit is 0 and T's is 1, and stay undecided
-// where the two bits agree.
+// One bit plane j of the acceptance numbers v (bits of the word v_bits).  A
+// site still undecided takes T's bit into acc -- the outcome of v < T if v's
+// bit differs from it -- and stays undecided where the two bits agree.  So
+// once the planes are done a site is accepted where acc is set and und is
+// clear (a site whose v equals T in every plane is rejected).
 __device__ __forceinline__ void acceptance_plane(uint32_t v_bits, int j, const uint4 *s_tab, uint32_t c0, uint32_t e1,
                                                  uint32_t &acc, uint32_t &und)
 {
     const uint32_t tj = threshold_bits(s_tab[j], c0, e1);
-    acc |= und & ~v_bits & tj;
+    acc = (und & tj) | (~und & acc);
     und &= ~(v_bits ^ tj);
 }
 
@@ -509,8 +511,9 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     }
                 }
                 if (live && !queued) {
+                    const uint32_t a = acc & ~und;
 #pragma unroll
-                    for (int p = 0; p < B; ++p) W[p] = (acc & P[p]) | (~acc & W[p]);
+                    for (int p = 0; p < B; ++p) W[p] = (a & P[p]) | (~a & W[p]);
                     store_planes<BP>(own, W);
                 }
             }
@@ -536,8 +539,9 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     uint32_t *own = sw + r * RW + (c * IPC + it) * BP;
                     uint32_t W[BP];
                     load_planes<BP>(W, own);
+                    const uint32_t a = acc & ~und;
 #pragma unroll
-                    for (int p = 0; p < B; ++p) W[p] = (acc & q_prop[p][ee]) | (~acc & W[p]);
+                    for (int p = 0; p < B; ++p) W[p] = (a & q_prop[p][ee]) | (~a & W[p]);
                     store_planes<BP>(own, W);
                 }
             }
