@@ -158,11 +158,17 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
     const long long units = pa::colour_words(L);
     int rpb = rpb_req;
     if (rpb <= 0) {
-        int rpb_mem = (int)(81920 / RB);
+        // 96 KB of lattices per block: two blocks of 512 threads per SM
+        int rpb_mem = (int)(98304 / RB);
         if (rpb_mem < 1) rpb_mem = 1;
         int rpb_fill = c->cfg.R / (4 * c->sms);
         if (rpb_fill < 1) rpb_fill = 1;
         rpb = rpb_mem < rpb_fill ? rpb_mem : rpb_fill;
+        // a group spanning several passes of 512 threads over its site words
+        // fills each pass: q = 10, L = 64 takes 48 replicas (6 words per
+        // thread), not 44 (5.5)
+        const long long per_pass = 512 / units;
+        if (per_pass >= 1 && rpb > per_pass) rpb = (int)(rpb / per_pass * per_pass);
         // at least one warp of work items per block
         const int rpb_warp = (int)((32 + units - 1) / units);
         if (rpb < rpb_warp) rpb = rpb_warp < rpb_mem ? rpb_warp : rpb_mem;

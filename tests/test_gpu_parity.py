@@ -293,11 +293,12 @@ def test_full_size_step_one_sampled(w):
 
 def test_plain_at_scale_launch_shape_reduced_population():
     """Three full steps at L = 64, q = 10, theta = 10 with R = 3000 in the
-    block shape the benchmark picks for R = 100000 (16 replicas x 512 threads)."""
+    block shape the default launch picks for R = 100000 (48 replicas x 512
+    threads, six site words per thread and half sweep)."""
     w = wl.C2
     b = w.betas()[:4]
     R = 3000
-    g = _gpu_run(w.q, w.L, R, w.seed, w.theta, b, launch=(16, 512))
+    g = _gpu_run(w.q, w.L, R, w.seed, w.theta, b, launch=(48, 512))
     o = _oracle_run(w.q, w.L, R, w.seed, w.theta, b)
     _compare(g, o)
 
