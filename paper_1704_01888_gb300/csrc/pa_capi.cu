@@ -85,6 +85,7 @@ struct pa_ctx {
     long long n_obs = 0;  // estimator records written so far
     uint8_t *stage = nullptr;
     size_t stage_bytes = 0;
+    uint8_t *host_stage = nullptr;  // pinned: device state, one record, the histogram
     double *aux = nullptr;  // small device outputs (Newton step)
 
     int step = 0;          // last completed temperature step
@@ -148,7 +149,13 @@ void release(pa_ctx *c)
                     c->stage, c->aux};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->host_stage) cudaFreeHost(c->host_stage);
 }
+
+// Offsets in the pinned host staging area of pa_observables.
+constexpr size_t kStageObs = 256;
+constexpr size_t kStageHist = 512;
+static_assert(sizeof(pa::DevState) <= kStageObs && sizeof(pa_obs) <= kStageHist - kStageObs, "staging layout");
 
 pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
 {
@@ -363,6 +370,11 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
     const size_t canon_bytes = (size_t)c->R_cap * c->N;
     c->stage_bytes = canon_bytes < (64u << 20) ? canon_bytes : (64u << 20);
     if ((s = dev_alloc(&c->stage, c->stage_bytes))) return fail(s);
+    e = cudaHostAlloc((void **)&c->host_stage, kStageHist + sizeof(int32_t) * c->nbins, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        c->host_stage = nullptr;
+        return fail(cuda_fail(e));
+    }
     if ((s = choose_launch(c, 0, 0))) return fail(s);
     *out = c;
     return PA_OK;
@@ -652,14 +664,24 @@ pa_status pa_observables(pa_ctx *c, pa_obs *out, int32_t *hist_out, int32_t hist
 {
     if (!c || !out) return PA_ERR_INVALID;
     if (hist_out && hist_len < c->nbins) return PA_ERR_INVALID;
-    pa_status s = sync_state(c, nullptr);
-    if (s) return s;
+    // one round trip: the device state, the latest record and the histogram
+    // into pinned staging, a single synchronisation, then the error check
+    pa::DevState *h = reinterpret_cast<pa::DevState *>(c->host_stage);
+    pa_obs *rec = reinterpret_cast<pa_obs *>(c->host_stage + kStageObs);
+    int32_t *hist = reinterpret_cast<int32_t *>(c->host_stage + kStageHist);
     const pa::DevObs *slot = c->obs + ((c->n_obs - 1) % c->obs_cap);
     static_assert(sizeof(pa::DevObs) == sizeof(pa_obs), "pa_obs layout");
-    PA_CK(cudaMemcpyAsync(out, slot, sizeof(pa_obs), cudaMemcpyDeviceToHost, c->stream));
+    PA_CK(cudaMemcpyAsync(h, c->st, sizeof(pa::DevState), cudaMemcpyDeviceToHost, c->stream));
+    PA_CK(cudaMemcpyAsync(rec, slot, sizeof(pa_obs), cudaMemcpyDeviceToHost, c->stream));
     if (hist_out)
-        PA_CK(cudaMemcpyAsync(hist_out, c->hist, sizeof(int32_t) * c->nbins, cudaMemcpyDeviceToHost, c->stream));
+        PA_CK(cudaMemcpyAsync(hist, c->hist, sizeof(int32_t) * c->nbins, cudaMemcpyDeviceToHost, c->stream));
     PA_CK(cudaStreamSynchronize(c->stream));
+    if (h->err != 0) {
+        c->failed = true;
+        return (pa_status)h->err;
+    }
+    *out = *rec;
+    if (hist_out) std::memcpy(hist_out, hist, sizeof(int32_t) * c->nbins);
     return PA_OK;
 }
 
