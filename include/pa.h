@@ -116,9 +116,11 @@ typedef struct pa_ctx pa_ctx;
  * replica: a state takes B = ceil(log2 q) bits, stored as P bit planes (B
  * rounded up to 1, 2, 4 or 8); the sites of each colour ((x + y) mod 2) are
  * packed 32 to a 32-bit word per plane (row-major over the colour's sites
- * when L/2 divides 32, else each row padded to whole words), so a replica
- * takes 2 W P 4 bytes, W = L^2/64 or L ceil(L/64) words per colour: L <= 640
- * for q <= 16 and L <= 448 for q <= 128.  PA_ERR_NOMEM or
+ * when L/2 divides 32; when L is a multiple of 16 but not of 64 and L > 32,
+ * a word holds one 8-column segment of four rows L/4 apart; else each row is
+ * padded to whole words), so a replica takes 2 W P 4 bytes, W = L^2/64 (the
+ * first two cases) or L ceil(L/64) words per colour: L <= 640 for q <= 16
+ * and L <= 448 for q <= 128.  PA_ERR_NOMEM or
  * PA_ERR_CUDA if allocation or a launch fails (nothing is leaked; *out = NULL). */
 pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 
@@ -327,7 +329,7 @@ void pa_batch_destroy(pa_batch *b);
  * run resumed with pa_load continues bit for bit as the uninterrupted run.
  * Synchronises.  PA_ERR_STATE with a resample pending or a failed context;
  * PA_ERR_INVALID if the file cannot be written.  Spins are stored in the
- * device layout (format version 2); files are read back by this library on
+ * device layout (format version 3); files are read back by this library on
  * machines of the same byte order. */
 pa_status pa_save(pa_ctx *ctx, const char *path);
 

@@ -228,9 +228,14 @@ static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
  * mod 2), with column index m = x >> 1, are grouped 32 to a "site word".  When
  * a whole number of that colour's rows fills 32 columns (L = 8, 16, 32, 64,
  * i.e. L/2 divides 32), the colour's sites in row-major order, h = y L/2 + m,
- * fill the words in turn: word w = h >> 5, bit b = h & 31.  Otherwise each row
- * starts a new word: word t = m >> 5 of the row, bit b = m & 31, word index
- * w = y ceil(L / 64) + t.  (At L = 64 both rules coincide.)  In sweep k,
+ * fill the words in turn: word w = h >> 5, bit b = h & 31.  When L is a
+ * multiple of 16 but not of 64 and larger than 32 (L = 48, 80, 96, 112, ...),
+ * the rows fall into four bands of L/4 rows and each row into L/16 segments
+ * of 8 columns; word w = k (L/16) + j holds segment j of rows k, k + L/4,
+ * k + L/2 and k + 3L/4, the site of band a (row y = k + a L/4) and column
+ * m = 8j + t at bit b = 8a + t.  Otherwise each row starts a new word: word
+ * t = m >> 5 of the row, bit b = m & 31, word index w = y ceil(L / 64) + t.
+ * (At L = 64 the first and last rules coincide.)  In sweep k,
  * colour c, temperature step `step`, the word draws a stream Z_0, Z_1, ... of
  * 32-bit numbers, Z_{4n+i} being word i of the Philox call with counter
  * (w, SWEEP | ((2k + c) << 8) | n, step, slot | stream << 24), and the site at
@@ -242,6 +247,11 @@ static void orc_neighbours(int L, const uint8_t *s, int x, int y, int nb[4])
 static int orc_rows_packed(int L)
 {
     return L >= 8 && 64 % L == 0;
+}
+
+static int orc_rows_banded(int L)
+{
+    return L > 32 && L % 16 == 0 && L % 64 != 0;
 }
 
 struct orc_word_stream {
@@ -321,6 +331,17 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], in
                     for (int b = 0; b < 32; ++b) {
                         int h = 32 * w + b;
                         int y = h / half, m = h % half;
+                        orc_attempt(q, B, L, s, 2 * m + ((colour + y) & 1), y, &st, b, T);
+                    }
+                }
+            } else if (orc_rows_banded(L)) {
+                int segs = L / 16, band_rows = L / 4;
+                for (int w = 0; w < band_rows * segs; ++w) {
+                    st.w = (uint32_t)w;
+                    st.have = 0;
+                    int k = w / segs, j = w % segs;
+                    for (int b = 0; b < 32; ++b) {
+                        int y = k + (b >> 3) * band_rows, m = 8 * j + (b & 7);
                         orc_attempt(q, B, L, s, 2 * m + ((colour + y) & 1), y, &st, b, T);
                     }
                 }

@@ -216,6 +216,8 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
             batch_body<1>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         else if (rows_packed(r.L))
             batch_body<3>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
+        else if (rows_banded(r.L))
+            batch_body<4>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         else
             batch_body<2>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
         if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(r.acc, sE, sE2, sM);

@@ -383,7 +383,7 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
 // Checkpoint file: a fixed header, the population's arrays, and an FNV-1a
 // checksum of everything before it.
 constexpr char kMagic[8] = {'P', 'A', 'G', 'B', '3', '0', '0', '\x01'};
-constexpr uint32_t kVersion = 2;  // 2: multi-spin-coded spin arrays
+constexpr uint32_t kVersion = 3;  // 2: multi-spin-coded spin arrays; 3: banded rows at L = 48, 80, 96, ...
 
 struct CkptHeader {
     char magic[8];

@@ -8,6 +8,10 @@
 //   word index (c * IPC + w) * BP + p,   IPC = site words per colour.
 // When L/2 divides 32 (L = 8, 16, 32, 64) the colour's sites in row-major order
 // h = y L/2 + m fill the words in turn (w = h >> 5, bit h & 31; IPC = L^2/64).
+// When L is a multiple of 16 but not of 64 and L > 32 (L = 48, 80, 96, ...)
+// the rows form four bands of L/4 rows and each row L/16 segments of 8
+// columns: word w = k L/16 + j holds segment j of rows k + a L/4, a = 0..3,
+// the site of band a and column m = 8j + t at bit 8a + t (IPC = L^2/64).
 // Otherwise each row starts a new word: w = y WPR + (m >> 5), bit m & 31,
 // WPR = ceil(L / 64), IPC = L WPR, and columns >= L/2 of a row's last word are
 // always zero.  Planes >= B are always zero.  One replica takes RW = 2 IPC BP
@@ -45,7 +49,12 @@ __host__ __device__ constexpr int row_words(int L) { return (L + 63) / 64; }
 // Rows packed several to a word: L/2 divides 32 (L = 8, 16, 32; at L = 64 both
 // layouts coincide).
 __host__ __device__ constexpr bool rows_packed(int L) { return L >= 8 && 64 % L == 0; }
-__host__ __device__ constexpr int colour_words(int L) { return rows_packed(L) ? L * L / 64 : L * row_words(L); }
+// Rows in four bands of 8-column segments: L = 48, 80, 96, 112, 144, ...
+__host__ __device__ constexpr bool rows_banded(int L) { return L > 32 && L % 16 == 0 && L % 64 != 0; }
+__host__ __device__ constexpr int colour_words(int L)
+{
+    return (rows_packed(L) || rows_banded(L)) ? L * L / 64 : L * row_words(L);
+}
 // Words of one replica, padded to whole 16-byte vectors (the gather moves uint4).
 __host__ __device__ constexpr int replica_words_of(int B, int L) { return (2 * colour_words(L) * plane_stride(B) + 3) & ~3; }
 __host__ __device__ constexpr int replica_words(int q, int L) { return replica_words_of(state_bits(q), L); }

@@ -135,13 +135,41 @@ __device__ __forceinline__ constexpr uint32_t odd_segments()
 // The four neighbour words of site word `it` (its index within its colour) of
 // colour c: up, down and same-row words of the other colour (oth) and the
 // same-row word shifted by one column.  Returns the mask of the word's valid
-// columns.  MODE as for shifted_row, or 3 for packed rows.
+// columns.  MODE as for shifted_row, 3 for packed rows, 4 for banded rows.
 template <int B, int MODE, int BP>
 __device__ __forceinline__ uint32_t neighbour_planes(const uint32_t *oth, int L, int IPC, int WPR, int nb_last,
                                                      int it, int c, uint32_t (&U)[BP], uint32_t (&D)[BP],
                                                      uint32_t (&H)[BP], uint32_t (&X)[BP])
 {
-    if constexpr (MODE == 3) {
+    if constexpr (MODE == 4) {
+        // word (k, j): segment j of rows k + a L/4 in byte a.  The rows above
+        // and below are the same bytes of words (k -+ 1, j), except across the
+        // band edges: above row 0 of a band lies the last row of the band
+        // before (byte a - 1 of word (L/4 - 1, j), cyclically), below its last
+        // row the first row of the next band (byte a + 1 of word (0, j)).
+        const int segs = L >> 4, band_rows = L >> 2;
+        const int k = it / segs, j = it - k * segs;
+        const int ku = k == 0 ? band_rows - 1 : k - 1;
+        const int kd = k == band_rows - 1 ? 0 : k + 1;
+        const int par = (k + c) & 1;  // band heights are even: one parity per word
+        const int je = par ? (j + 1 == segs ? 0 : j + 1) : (j == 0 ? segs - 1 : j - 1);
+        uint32_t Uw[BP], Dw[BP], Eg[BP];
+        load_planes<BP>(H, oth + it * BP);
+        load_planes<BP>(Uw, oth + (ku * segs + j) * BP);
+        load_planes<BP>(Dw, oth + (kd * segs + j) * BP);
+        load_planes<BP>(Eg, oth + (k * segs + je) * BP);
+        const uint32_t ru = k == 0 ? 8u : 0u, rd = k == band_rows - 1 ? 8u : 0u;
+#pragma unroll
+        for (int p = 0; p < B; ++p) {
+            U[p] = __funnelshift_l(Uw[p], Uw[p], ru);
+            D[p] = __funnelshift_r(Dw[p], Dw[p], rd);
+            // column m + 1 (par = 1) or m - 1 (par = 0) within each 8-column
+            // byte, the edge column from the adjacent segment Eg
+            X[p] = par ? (((H[p] >> 1) & 0x7F7F7F7Fu) | ((Eg[p] << 7) & 0x80808080u))
+                       : (((H[p] << 1) & 0xFEFEFEFEu) | ((Eg[p] >> 7) & 0x01010101u));
+        }
+        return 0xFFFFFFFFu;
+    } else if constexpr (MODE == 3) {
         const int wu = it == 0 ? IPC - 1 : it - 1;
         const int wd = it == IPC - 1 ? 0 : it + 1;
         uint32_t Hu[BP], Hd[BP];
@@ -581,7 +609,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     uint32_t W[BP];
                     load_planes<BP>(W, rep + it * BP);
                     const uint32_t vmask =
-                        (MODE == 0 || MODE == 3) ? 0xFFFFFFFFu : valid_mask(it % WPR, WPR, nb_last);
+                        (MODE == 0 || MODE == 3 || MODE == 4) ? 0xFFFFFFFFu : valid_mask(it % WPR, WPR, nb_last);
                     cnt += __popc(vmask & equal_state<B, BP>(W, s));
                 }
             }
@@ -709,8 +737,8 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
     const int rem = (int)(i - (long long)slot * IPR);
     const int c = rem / IPC;
     const int it = rem - c * IPC;
-    const bool packed = rows_packed(L);
-    const int nb = packed ? 32 : ((it % WPR) == WPR - 1 ? nb_last : 32);
+    const bool packed = rows_packed(L), banded = rows_banded(L);
+    const int nb = (packed || banded) ? 32 : ((it % WPR) == WPR - 1 ? nb_last : 32);
     uint32_t planes[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     if (ground) {
         const uint4 w = philox10(make_uint4((uint32_t)slot >> 2, DOM_GROUND, 0u, stream_hi), k0, k1);
@@ -726,6 +754,10 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
                 const int h = 32 * it + b;
                 y = h / (L / 2);
                 m = h - y * (L / 2);
+            } else if (banded) {
+                const int k = it / (L / 16);
+                y = k + (b >> 3) * (L / 4);
+                m = 8 * (it - k * (L / 16)) + (b & 7);
             } else {
                 y = it / WPR;
                 m = 32 * (it - y * WPR) + b;
@@ -762,6 +794,10 @@ __device__ __forceinline__ uint8_t canonical_state(const uint32_t *spins, int q,
         const int h = y * (L / 2) + m;
         it = h >> 5;
         b = h & 31;
+    } else if (rows_banded(L)) {
+        const int a = y / (L / 4), k = y - a * (L / 4);
+        it = k * (L / 16) + (m >> 3);
+        b = 8 * a + (m & 7);
     } else {
         it = y * row_words(L) + (m >> 5);
         b = m & 31;

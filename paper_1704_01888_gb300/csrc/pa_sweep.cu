@@ -53,8 +53,8 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
 // colour) replicas, the number that fills one pass of the block's threads
 // over the site words, so that no block and no pass is left part-empty.
 // B: bits per state; MODE: 0 for L = 64, 1 for L a multiple of 64, 3 for
-// L = 8, 16, 32 (rows packed several to a word), 2 otherwise (rows padded to
-// whole words).
+// L = 8, 16, 32 (rows packed several to a word), 4 for L = 48, 80, 96, ...
+// (banded 8-column segments), 2 otherwise (rows padded to whole words).
 template <int B, int MODE, int Q>
 __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
 {
@@ -125,6 +125,7 @@ KernelFnPtr pick_kernel(int q, int L)
     if (L == 64) return pick_q<0>(q);
     if (L % 64 == 0) return pick_q<1>(q);
     if (rows_packed(L)) return pick_q<3>(q);
+    if (rows_banded(L)) return pick_q<4>(q);
     return pick_q<2>(q);
 }
 

@@ -65,6 +65,8 @@ def test_bench_helpers_and_global_names():
     assert bench.replica_bytes(10, 16) == 128
     assert bench.replica_bytes(20, 256) == 65536
     assert bench.replica_bytes(2, 8) == 16        # 2 words padded to 4
+    assert bench.replica_bytes(10, 48) == 1152    # banded: 36 words per colour
+    assert bench.replica_bytes(10, 24) == 768     # padded rows: 24 words per colour
     # q = 10 (B = 4), 6 acceptance planes: Philox 50, proposal 32, dE class 49,
     # acceptance 18, merge 5
     assert bench.ops_per_word(10) == 154

@@ -119,8 +119,9 @@ def test_step_api_graph_and_launch_shapes_agree():
 
 # ---------------------------------------------------------------------------
 # Edge cases: every row geometry of the multi-spin-coded kernel (L = 64; rows
-# of whole words; rows packed several to a word at L = 8, 16, 32; rows padded
-# to whole words, one or several words per row),
+# of whole words; rows packed several to a word at L = 8, 16, 32; four bands
+# of 8-column segments at L = 48, 80, 96, 112; rows padded to whole words, one
+# or several words per row),
 # bit-plane counts B = 1..7 (q = 2 .. 128), R = 1, theta = 0, rounding modes.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("q,L,R,theta,K,extra", [
@@ -134,10 +135,14 @@ def test_step_api_graph_and_launch_shapes_agree():
     (128, 16, 100, 2, 6, {}),           # largest q (B = 7)
     (40, 16, 120, 2, 6, {}),            # B = 6
     (10, 24, 90, 2, 6, {}),             # 12 columns in a 32-bit word
+    (10, 48, 150, 3, 6, {}),            # banded rows: 3 segments of 8 columns, bands of 12 rows
+    (2, 48, 120, 3, 6, {}),             # banded rows, q = 2 (one plane)
+    (20, 80, 30, 2, 4, {}),             # banded rows: 5 segments, B = 5
+    (3, 112, 12, 2, 3, {}),             # banded rows: 7 segments, B = 2
     (9, 64, 200, 3, 6, {}),             # one full word per row; q - 1 = 8 uniform
     (10, 128, 30, 2, 4, {}),            # rows of two full words
     (20, 66, 40, 2, 4, {}),             # 33 columns: a full word and one column (B = 5)
-    (17, 96, 30, 2, 4, {}),             # 48 columns: a full and a half word; q - 1 = 16 uniform
+    (17, 96, 30, 2, 4, {}),             # banded rows: 6 segments; q - 1 = 16 uniform
     (2, 130, 8, 2, 3, {}),              # 65 columns: three words per row, q = 2
     (10, 16, 1, 3, 10, {}),             # one replica
     (6, 16, 500, 0, 8, {}),             # resampling only

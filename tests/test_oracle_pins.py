@@ -228,13 +228,14 @@ def test_bitwise_comparison_equals_integer_comparison():
             assert oracle.below_value(v, T) == (v < T), (v, T)
 
 
-@pytest.mark.parametrize("L", [2, 4, 6, 8, 16, 32, 48, 64, 66, 128])
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 16, 24, 32, 48, 64, 66, 80, 96, 128, 144])
 def test_sweep_attempts_every_site_exactly_once(L):
     """At beta = 0 every move is accepted, and for q = 2 a move flips the spin,
     so one sweep flips a site an odd number of times exactly when it is
     attempted an odd number of times: every site flipped means the site words
-    (packed rows for L = 8, 16, 32, padded rows otherwise) cover each site of
-    each colour once.  With q = 3 every site must also have changed."""
+    (packed rows for L = 8, 16, 32, banded 8-column segments for L = 48, 80,
+    96, 144, padded rows otherwise) cover each site of each colour once.  With
+    q = 3 every site must also have changed."""
     rng = np.random.default_rng(L)
     s = rng.integers(0, 2, size=(L, L)).astype(np.uint8)
     out = oracle.sweep_replica(2, s, 0.0, 1, step=1, slot=3, seed=5)
