@@ -80,6 +80,13 @@ __device__ __forceinline__ uint32_t equal_state(const uint32_t (&a)[BP], int s)
     return ~d;
 }
 
+// Division by a divisor d fixed for a replica group (d < 2^15) of x < 2^16,
+// without a division instruction sequence per use: with inv = ceil(2^31 / d)
+// = (2^31 + e) / d, 0 <= e < d, floor(x inv / 2^31) = floor(x / d) because
+// x e < x d < 2^31.
+__device__ __forceinline__ uint32_t div_inverse(uint32_t d) { return (uint32_t)((0x80000000ull + d - 1u) / d); }
+__device__ __forceinline__ int div_by(int x, uint32_t inv) { return (int)__umulhi((uint32_t)x << 1, inv); }
+
 __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum, uint32_t &carry)
 {
     sum = a ^ b ^ c;
@@ -135,11 +142,13 @@ __device__ __forceinline__ constexpr uint32_t odd_segments()
 // The four neighbour words of site word `it` (its index within its colour) of
 // colour c: up, down and same-row words of the other colour (oth) and the
 // same-row word shifted by one column.  Returns the mask of the word's valid
-// columns.  MODE as for shifted_row, 3 for packed rows, 4 for banded rows.
+// columns.  MODE as for shifted_row, 3 for packed rows, 4 for banded rows;
+// inv_row = div_inverse of the words per row (MODE 1, 2) or of the segments
+// per row (MODE 4).
 template <int B, int MODE, int BP>
 __device__ __forceinline__ uint32_t neighbour_planes(const uint32_t *oth, int L, int IPC, int WPR, int nb_last,
-                                                     int it, int c, uint32_t (&U)[BP], uint32_t (&D)[BP],
-                                                     uint32_t (&H)[BP], uint32_t (&X)[BP])
+                                                     uint32_t inv_row, int it, int c, uint32_t (&U)[BP],
+                                                     uint32_t (&D)[BP], uint32_t (&H)[BP], uint32_t (&X)[BP])
 {
     if constexpr (MODE == 4) {
         // word (k, j): segment j of rows k + a L/4 in byte a.  The rows above
@@ -148,7 +157,7 @@ __device__ __forceinline__ uint32_t neighbour_planes(const uint32_t *oth, int L,
         // before (byte a - 1 of word (L/4 - 1, j), cyclically), below its last
         // row the first row of the next band (byte a + 1 of word (0, j)).
         const int segs = L >> 4, band_rows = L >> 2;
-        const int k = it / segs, j = it - k * segs;
+        const int k = div_by(it, inv_row), j = it - k * segs;
         const int ku = k == 0 ? band_rows - 1 : k - 1;
         const int kd = k == band_rows - 1 ? 0 : k + 1;
         const int par = (k + c) & 1;  // band heights are even: one parity per word
@@ -191,7 +200,7 @@ __device__ __forceinline__ uint32_t neighbour_planes(const uint32_t *oth, int L,
         else body(std::integral_constant<int, 16>{});
         return 0xFFFFFFFFu;
     } else {
-        const int y = MODE == 0 ? it : it / WPR;
+        const int y = MODE == 0 ? it : div_by(it, inv_row);
         const int t = MODE == 0 ? 0 : it - y * WPR;
         const int yu = (y == 0) ? L - 1 : y - 1;
         const int yd = (y == L - 1) ? 0 : y + 1;
@@ -374,7 +383,7 @@ __device__ __forceinline__ void acceptance_calls(int ch_begin, int ch_end, uint3
 // indicator bits (neighbours equal to s, neighbours different from s'), summed
 // by a carry-save tree; moves with dE > 0 compare v with T[dE] bit by bit, and
 // the warp draws further acceptance words only while some site is undecided.
-template <int B, int MODE, int Q = 0>
+template <int B, int MODE, int Q = 0, bool HOIST = false>
 __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32_t *sw, const uint4 *s_tab,
                                                  uint32_t *qbuf, const uint32_t *rk0, const uint32_t *rk1,
                                                  long long &sE, long long &sE2, long long &sM)
@@ -424,24 +433,37 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
     if (tid < 2) q_count[tid] = 0;
     __syncthreads();
     int half = 0;
+    // HOIST: when each pass of the block's threads covers whole replicas and
+    // a warp stays within one replica (IPC a multiple of 32 dividing the
+    // threads), a thread keeps one site word index through all passes: its
+    // row, neighbour offsets and counter word are computed once instead of per
+    // word.  (The batched kernel, one function over every body, leaves it out:
+    // a second copy of each first pass doubles its size and build time.)
+    const bool whole_passes = HOIST && IPC % 32 == 0 && (nwarps * 32) % IPC == 0;
+    const int it_fixed = (warp * 32 + lane) % IPC;
+    const int r_first = (warp * 32) / IPC;
+    const int r_step = (nwarps * 32) / IPC;
+    // replica of a block-wide word index, and row (segment row) of a word
+    const uint32_t inv_ipc = div_inverse(IPC);
+    const uint32_t inv_row = div_inverse(MODE == 4 ? L >> 4 : WPR);
+    auto replica_of = [&](int x) { return MODE == 0 ? x / IPC : div_by(x, inv_ipc); };
 
     for (int k = 0; k < G.theta; ++k) {
         for (int c = 0; c < 2; ++c, ++half) {
             const uint32_t ctr1 = DOM_SWEEP | ((uint32_t)(2 * k + c) << 8);
             if (tid == 0) q_count[(half + 1) & 1] = 0;
             int *qc = q_count + (half & 1);
-            for (int base = warp * 32; base < total; base += nwarps * 32) {
-                const int i = base + lane;
-                const bool live = i < total;
-                const int ii = live ? i : total - 1;
-                const int r = ii / IPC;
-                const int it = ii - r * IPC;  // site word within the colour = its counter word w
+            // one site word: replica r, word it within the colour (its counter
+            // word w); lanes that are not live run along for the warp votes
+            auto site_word = [&](const int r, const int it, const bool live) {
+                const int ii = r * IPC + it;
                 uint32_t *rep = sw + r * RW;
                 uint32_t *own = rep + (c * IPC + it) * BP;
                 const uint32_t *oth = rep + (c ^ 1) * IPC * BP;
                 uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
                 load_planes<BP>(W, own);
-                const uint32_t vmask = neighbour_planes<B, MODE, BP>(oth, L, IPC, WPR, nb_last, it, c, U, D, H, X);
+                const uint32_t vmask =
+                    neighbour_planes<B, MODE, BP>(oth, L, IPC, WPR, nb_last, inv_row, it, c, U, D, H, X);
 
                 // proposal: direction sigma = Z_0, offset bits u = Z_1..Z_{B-1}
                 const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
@@ -544,6 +566,17 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     for (int p = 0; p < B; ++p) W[p] = (a & P[p]) | (~a & W[p]);
                     store_planes<BP>(own, W);
                 }
+            };
+            if (HOIST && whole_passes) {
+                for (int r = r_first; r < nrep; r += r_step) site_word(r, it_fixed, true);
+            } else {
+                for (int base = warp * 32; base < total; base += nwarps * 32) {
+                    const int i = base + lane;
+                    const bool live = i < total;
+                    const int ii = live ? i : total - 1;
+                    const int r = replica_of(ii);
+                    site_word(r, ii - r * IPC, live);
+                }
             }
             __syncthreads();
             // second pass: the queued site words, 32 to a warp
@@ -553,7 +586,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 const bool live = e < nq;
                 const int ee = live ? e : nq - 1;
                 const int ii = q_item[ee];
-                const int r = ii / IPC;
+                const int r = replica_of(ii);
                 const int it = ii - r * IPC;
                 uint32_t acc = q_mask[0][ee];
                 uint32_t und = live ? q_mask[1][ee] : 0u;
@@ -595,7 +628,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
                 load_planes<BP>(W, rep + it * BP);
                 const uint32_t vmask =
-                    neighbour_planes<B, MODE, BP>(rep + IPC * BP, L, IPC, WPR, nb_last, it, 0, U, D, H, X);
+                    neighbour_planes<B, MODE, BP>(rep + IPC * BP, L, IPC, WPR, nb_last, inv_row, it, 0, U, D, H, X);
                 agree += __popc(vmask & ~differ<B, BP>(W, U)) + __popc(vmask & ~differ<B, BP>(W, D)) +
                          __popc(vmask & ~differ<B, BP>(W, H)) + __popc(vmask & ~differ<B, BP>(W, X));
             }
@@ -609,7 +642,9 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     uint32_t W[BP];
                     load_planes<BP>(W, rep + it * BP);
                     const uint32_t vmask =
-                        (MODE == 0 || MODE == 3 || MODE == 4) ? 0xFFFFFFFFu : valid_mask(it % WPR, WPR, nb_last);
+                        (MODE == 0 || MODE == 3 || MODE == 4)
+                            ? 0xFFFFFFFFu
+                            : valid_mask(it - div_by(it, inv_row) * WPR, WPR, nb_last);
                     cnt += __popc(vmask & equal_state<B, BP>(W, s));
                 }
             }
