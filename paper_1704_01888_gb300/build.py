@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpa_gb300.so")
-SOURCES = ["pa_sweep.cu", "pa_resample.cu", "pa_capi.cu", "pa_reweight.cu", "pa_batch.cu", "pa_noalloc.cu"]
+SOURCES = ["pa_sweep.cu", "pa_resample.cu", "pa_capi.cu", "pa_reweight.cu", "pa_batch.cu", "pa_batch_hi.cu",
+           "pa_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,8 +1,9 @@
 // pa_batch.cu -- M independent population-annealing runs (Barash, Weigel,
 // Shchur & Janke, arXiv:1704.01888, Sec. 2 steps 1-5), possibly with
 // different q, L, R and schedules, advanced together: every temperature step
-// is six launches that each cover all runs (weights, copy numbers, parent
-// map, one persistent sweep kernel over every run's replica groups,
+// is six or seven launches that each cover all runs (weights, copy numbers,
+// parent map, a persistent sweep kernel over every run's replica groups -- one
+// for the runs with q <= 16 and one for the others, pa_batch.cuh --,
 // estimators, step counter).  Because the step index lives in device memory,
 // one captured CUDA graph of a step is replayed for the whole schedule.
 //
@@ -19,46 +20,11 @@
 #include <vector>
 
 #include "../../include/pa.h"
-#include "pa_kernels.cuh"
+#include "pa_batch.cuh"
 
 namespace pa {
 
 namespace {
-
-constexpr int kB = 1024;
-constexpr int kMaxRuns = 1024;
-
-struct RunDev {
-    uint32_t *buf[2];
-    int32_t *anc[2];
-    int32_t *parent, *E, *Mt, *hist, *fam, *counts, *local_off, *blocksum;
-    double *wtab;
-    unsigned long long *acc;
-    DevState *st;
-    DevObs *obs;  // K + 1 records
-    int32_t q, L, N, nbins, R0, R_cap, mode, rpb, chunk0, nchunks, K, ground;
-    uint32_t stream_hi;
-    long long item0;  // first site word of this run in the flattened init index
-};
-
-struct StepDev {  // one per (step, run)
-    Thresholds thr;
-    double beta, dbeta;
-    int32_t theta, active;
-};
-
-struct BatchArgs {
-    const RunDev *runs;
-    const StepDev *steps;  // (K_max + 1) x M
-    const int32_t *step_counter;
-    int32_t *work;         // per step: next replica group to hand out (zeroed at start)
-    const int32_t *order;  // runs by decreasing estimated cost of one group
-    int32_t M, total_chunks;
-    long long total_items;
-    uint32_t k0, k1;
-    uint32_t rk0[10], rk1[10];
-    int32_t gather;  // 0 for the measurement at step 0
-};
 
 __device__ __forceinline__ int run_of_chunk(const RunDev *runs, int M, int chunk)
 {
@@ -81,32 +47,6 @@ __global__ void k_batch_init(const BatchArgs b)
         }
         const RunDev &r = b.runs[lo];
         dev::init_item(r.buf[0], r.anc[0], r.q, r.L, i - r.item0, b.k0, b.k1, r.stream_hi, r.ground);
-    }
-}
-
-// The sweep body for a run's q (q = 5, 6, 8, 10 fixed at compile time, so
-// that the reduction mod q uses constant masks), else its bits per state, and
-// its row geometry.
-template <int MODE>
-__device__ __forceinline__ void batch_body(int qv, int B, const dev::Group &G, int L, uint32_t *sw,
-                                           const uint4 *s_tab, uint32_t *q, const BatchArgs &b, long long &sE,
-                                           long long &sE2, long long &sM)
-{
-    switch (qv) {
-    case 5: dev::sweep_group_bits<3, MODE, 5>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
-    case 6: dev::sweep_group_bits<3, MODE, 6>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
-    case 8: dev::sweep_group_bits<3, MODE, 8>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
-    case 10: dev::sweep_group_bits<4, MODE, 10>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); return;
-    default: break;
-    }
-    switch (B) {
-    case 1: dev::sweep_group_bits<1, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 2: dev::sweep_group_bits<2, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 3: dev::sweep_group_bits<3, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 4: dev::sweep_group_bits<4, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 5: dev::sweep_group_bits<5, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
-    case 6: dev::sweep_group_bits<6, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
-    default: dev::sweep_group_bits<7, MODE>(G, L, sw, s_tab, q, b.rk0, b.rk1, sE, sE2, sM); break;
     }
 }
 
@@ -144,86 +84,6 @@ __global__ void __launch_bounds__(kB) k_batch_scatter(const BatchArgs b)
                       r.nbins, r.st, s_l);
 }
 
-// One persistent launch over the replica groups of every active run.  Blocks
-// take groups from a shared counter, the groups of the costliest runs first,
-// so that the heterogeneous groups of different runs balance over the SMs.
-__global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
-{
-    extern __shared__ uint4 smem4[];
-    __shared__ uint4 s_tab[dev::kThresholdEntries];
-    __shared__ int s_prefix[kMaxRuns + 1];
-    __shared__ int s_group;
-    __shared__ uint32_t s_queue[dev::queue_words(7)];
-    const int i = *b.step_counter;
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int k = 0; k < b.M; ++k) {
-            s_prefix[k] = acc;
-            const int m = b.order[k];
-            const RunDev &r = b.runs[m];
-            const StepDev &sp = b.steps[(size_t)i * b.M + m];
-            if (sp.active && !r.st->err) {
-                const int R = b.gather ? r.st->pop_next : r.st->pop;
-                acc += (R + r.rpb - 1) / r.rpb;
-            }
-        }
-        s_prefix[b.M] = acc;
-    }
-    __syncthreads();
-    const int total = s_prefix[b.M];
-    for (;;) {
-        if (threadIdx.x == 0) s_group = atomicAdd(b.work + i, 1);
-        __syncthreads();
-        const int g = s_group;
-        __syncthreads();
-        if (g >= total) break;
-        int lo = 0, hi = b.M - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (s_prefix[mid] <= g) lo = mid; else hi = mid - 1;
-        }
-        const int m = b.order[lo];
-        const RunDev &r = b.runs[m];
-        const StepDev &sp = b.steps[(size_t)i * b.M + m];
-        const int parity = r.st->parity;
-        const int R = b.gather ? r.st->pop_next : r.st->pop;
-        const int first = (g - s_prefix[lo]) * r.rpb;
-        dev::Group G;
-        G.in = r.buf[parity];
-        G.out = b.gather ? r.buf[parity ^ 1] : r.buf[parity];
-        G.parent = r.parent;
-        G.anc_in = r.anc[parity];
-        G.anc_out = b.gather ? r.anc[parity ^ 1] : r.anc[parity];
-        G.fam = r.fam;
-        G.E = r.E;
-        G.Mt = r.Mt;
-        G.hist = r.hist;
-        G.first = first;
-        G.nrep = min(r.rpb, R - first);
-        G.q = r.q;
-        G.theta = sp.theta;
-        G.step = i;
-        G.stream_hi = r.stream_hi;
-        G.gather = b.gather != 0;
-        G.write_back = b.gather || sp.theta > 0;
-        dev::build_threshold_table(s_tab, sp.thr);
-        long long sE = 0, sE2 = 0, sM = 0;
-        uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);
-        const int B = state_bits(r.q);
-        if (r.L == 64)
-            batch_body<0>(r.q, B, G, 64, sw, s_tab, s_queue, b, sE, sE2, sM);
-        else if (r.L % 64 == 0)
-            batch_body<1>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
-        else if (rows_packed(r.L))
-            batch_body<3>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
-        else if (rows_banded(r.L))
-            batch_body<4>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
-        else
-            batch_body<2>(r.q, B, G, r.L, sw, s_tab, s_queue, b, sE, sE2, sM);
-        if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(r.acc, sE, sE2, sM);
-    }
-}
-
 __global__ void __launch_bounds__(kB) k_batch_finalize(const BatchArgs b)
 {
     __shared__ double s_d[32];
@@ -256,11 +116,14 @@ struct pa_batch {
     uint8_t *stage = nullptr;  // canonical-layout staging for pa_batch_get_spins
     size_t stage_bytes = 0;
     int32_t *counter_d = nullptr;
-    int32_t *work_d = nullptr;   // (Kmax + 1) group counters of the sweep kernel
+    int32_t *work_d = nullptr;   // 2 x (Kmax + 1) group counters of the sweep kernel's two parts
     int32_t *order_d = nullptr;  // run order of the sweep kernel's groups
     std::vector<void *> allocs;
     pa::BatchArgs args{};
     int smem_budget = 65536, threads = 512, grid = 0, sms = 0;
+    bool has_part[2] = {false, false};  // runs with q <= 16 / q > 16
+    int grid_part[2] = {0, 0};
+    int n_parts = 0;
     bool ran = false;
 };
 
@@ -299,6 +162,16 @@ void batch_release(pa_batch *b)
     b->capture_stream = nullptr;
 }
 
+// The sweep kernel of part 0 (q <= 16, this file) or part 1 (q > 16).
+pa::BatchSweepFn sweep_kernel(int part) { return part == 0 ? pa::k_batch_sweep<0> : pa::batch_sweep_kernel_hi(); }
+
+// The sweep kernels of the parts the batch's runs need, one after the other.
+void launch_sweeps(const pa_batch *b, const pa::BatchArgs &a, cudaStream_t s)
+{
+    for (int part = 0; part < 2; ++part)
+        if (b->has_part[part]) sweep_kernel(part)<<<b->grid_part[part], b->threads, b->smem_budget, s>>>(a);
+}
+
 // Replicas per block for each run and the persistent grid for a shared-memory
 // budget and a block size.
 pa_status apply_launch(pa_batch *b, int budget, int threads)
@@ -307,10 +180,12 @@ pa_status apply_launch(pa_batch *b, int budget, int threads)
     PB_CK(cudaGetDevice(&dev));
     PB_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa;
-    PB_CK(cudaFuncGetAttributes(&fa, pa::k_batch_sweep));
-    const int static_smem = (int)fa.sharedSizeBytes;
     if (budget < 1024 || threads < 64 || threads > 1024 || threads % 32) return PA_ERR_INVALID;
-    if (budget + static_smem > optin) return PA_ERR_INVALID;
+    for (int part = 0; part < 2; ++part) {
+        if (!b->has_part[part]) continue;
+        PB_CK(cudaFuncGetAttributes(&fa, sweep_kernel(part)));
+        if (budget + (int)fa.sharedSizeBytes > optin) return PA_ERR_INVALID;
+    }
     for (int m = 0; m < b->M; ++m) {
         const size_t padded = pa::replica_bytes(b->cfg[m].q, b->cfg[m].L);
         if (padded > (size_t)budget) return PA_ERR_INVALID;
@@ -320,13 +195,19 @@ pa_status apply_launch(pa_batch *b, int budget, int threads)
         b->rpb[m] = r;
         b->runs_h[m].rpb = r;
     }
-    PB_CK(cudaFuncSetAttribute(pa::k_batch_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - static_smem));
-    int per_sm = 0;
-    PB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pa::k_batch_sweep, threads, (size_t)budget));
-    if (per_sm < 1) return PA_ERR_INVALID;
+    for (int part = 0; part < 2; ++part) {
+        if (!b->has_part[part]) continue;
+        const pa::BatchSweepFn k = sweep_kernel(part);
+        PB_CK(cudaFuncGetAttributes(&fa, k));
+        PB_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+        int per_sm = 0;
+        PB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, (size_t)budget));
+        if (per_sm < 1) return PA_ERR_INVALID;
+        b->grid_part[part] = per_sm * b->sms;
+    }
     b->smem_budget = budget;
     b->threads = threads;
-    b->grid = per_sm * b->sms;
+    b->grid = b->grid_part[b->has_part[0] ? 0 : 1];
     // groups of the costliest runs first: cost ~ replicas x sites x sweeps x (4 + bits per state)
     std::vector<int32_t> order(b->M);
     std::vector<double> cost(b->M);
@@ -346,7 +227,7 @@ pa_status apply_launch(pa_batch *b, int budget, int threads)
 pa_status enqueue_start(pa_batch *b)
 {
     PB_CK(cudaMemsetAsync(b->counter_d, 0, sizeof(int32_t), b->stream));
-    PB_CK(cudaMemsetAsync(b->work_d, 0, sizeof(int32_t) * (size_t)(b->Kmax + 1), b->stream));
+    PB_CK(cudaMemsetAsync(b->work_d, 0, sizeof(int32_t) * 2 * (size_t)(b->Kmax + 1), b->stream));
     for (int m = 0; m < b->M; ++m) {
         const pa::RunDev &r = b->runs_h[m];
         pa::DevState h{};
@@ -364,10 +245,10 @@ pa_status enqueue_start(pa_batch *b)
     pa::k_batch_init<<<grid, 256, 0, b->stream>>>(b->args);
     pa::BatchArgs a0 = b->args;
     a0.gather = 0;
-    pa::k_batch_sweep<<<b->grid, b->threads, b->smem_budget, b->stream>>>(a0);
+    launch_sweeps(b, a0, b->stream);
     pa::k_batch_finalize<<<b->M, pa::kB, 0, b->stream>>>(a0);
     pa::k_batch_advance<<<1, 1, 0, b->stream>>>(b->counter_d);
-    pa::bump_launch_count(4);
+    pa::bump_launch_count(3 + b->n_parts);
     PB_CK(cudaGetLastError());
     return PA_OK;
 }
@@ -378,10 +259,10 @@ pa_status enqueue_step(pa_batch *b, cudaStream_t s)
     pa::k_batch_weights<<<b->M, pa::kB, 0, s>>>(b->args);
     pa::k_batch_counts<<<b->args.total_chunks, pa::kB, 0, s>>>(b->args);
     pa::k_batch_scatter<<<b->args.total_chunks, pa::kB, 0, s>>>(b->args);
-    pa::k_batch_sweep<<<b->grid, b->threads, b->smem_budget, s>>>(b->args);
+    launch_sweeps(b, b->args, s);
     pa::k_batch_finalize<<<b->M, pa::kB, 0, s>>>(b->args);
     pa::k_batch_advance<<<1, 1, 0, s>>>(b->counter_d);
-    pa::bump_launch_count(6);
+    pa::bump_launch_count(5 + b->n_parts);
     PB_CK(cudaGetLastError());
     return PA_OK;
 }
@@ -464,6 +345,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         g.R_cap = (int32_t)cap;
         b->cfg[m] = g;
         b->K[m] = d.K;
+        b->has_part[pa::batch_part(g.q)] = true;
         b->theta[m] = d.theta;
         b->Kmax = std::max(b->Kmax, d.K);
         pa::RunDev &r = b->runs_h[m];
@@ -500,6 +382,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
                 return fail(s);
         }
     }
+    b->n_parts = (int)b->has_part[0] + (int)b->has_part[1];
     // per-step parameters (step 0 = the initial measurement)
     std::vector<pa::StepDev> steps((size_t)(b->Kmax + 1) * M);
     for (int i = 0; i <= b->Kmax; ++i) {
@@ -516,7 +399,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         }
     }
     if ((s = balloc(b, &b->runs_d, M)) || (s = balloc(b, &b->steps_d, steps.size())) ||
-        (s = balloc(b, &b->counter_d, 1)) || (s = balloc(b, &b->work_d, (size_t)b->Kmax + 1)) ||
+        (s = balloc(b, &b->counter_d, 1)) || (s = balloc(b, &b->work_d, 2 * ((size_t)b->Kmax + 1))) ||
         (s = balloc(b, &b->order_d, M)))
         return fail(s);
     e = cudaMemcpy(b->steps_d, steps.data(), sizeof(pa::StepDev) * steps.size(), cudaMemcpyHostToDevice);
@@ -527,6 +410,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
     a.runs = b->runs_d;
     a.step_counter = b->counter_d;
     a.work = b->work_d;
+    a.work_stride = b->Kmax + 1;
     a.order = b->order_d;
     a.M = M;
     a.total_chunks = chunk0;
@@ -593,7 +477,7 @@ pa_status pa_batch_run(pa_batch *b, int32_t use_graph)
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) return bfail(e);
-        pa::bump_launch_count(6LL * (b->Kmax - 1));
+        pa::bump_launch_count((5LL + b->n_parts) * (b->Kmax - 1));
     }
     PB_CK(cudaStreamSynchronize(b->stream));
     return check_runs(b);

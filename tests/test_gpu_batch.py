@@ -20,11 +20,13 @@ def _built():
 
 
 def _mixed_runs():
-    """Mixed q (B = 1..5 bit planes), L (every row geometry: padded single
-    words, one full word at L = 64, two full words at L = 128), R, K, theta."""
+    """Mixed q (B = 1..6 bit planes: both parts of the sweep kernel, q <= 16
+    and q > 16), L (every row geometry: padded single words, packed rows,
+    banded rows at L = 48, one full word at L = 64, two full words at
+    L = 128), R, K, theta."""
     spec = [(5, 16, 700, 6, 3), (10, 8, 400, 9, 2), (8, 6, 300, 5, 2), (6, 32, 500, 4, 3),
             (10, 24, 350, 7, 2), (3, 40, 200, 3, 1), (20, 16, 900, 8, 0), (2, 64, 150, 2, 2),
-            (12, 128, 60, 3, 2)]
+            (12, 128, 60, 3, 2), (40, 48, 120, 4, 2), (7, 48, 300, 5, 2)]
     runs = []
     for m, (q, L, R, K, theta) in enumerate(spec):
         p = pa.PAParams(q=q, L=L, R=R, seed=9, stream=m)
