@@ -46,7 +46,7 @@ class Obs(ctypes.Structure):
         ("meanE", ctypes.c_double), ("meanE2", ctypes.c_double), ("C", ctypes.c_double),
         ("meanM", ctypes.c_double), ("S_f", ctypes.c_double),
         ("R", ctypes.c_int64), ("n_families", ctypes.c_int64), ("sumE", ctypes.c_int64),
-        ("sumE2", ctypes.c_int64), ("sumMt", ctypes.c_int64),
+        ("sumE2", ctypes.c_int64), ("sumMt", ctypes.c_int64), ("n_near_ties", ctypes.c_int64),
     ]
 
 
@@ -77,8 +77,16 @@ def lib():
         L.orc_sweep_replica.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, u32, u32, u64, u32]
         L.orc_init_random.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
         L.orc_init_ground.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
-        L.orc_copy_numbers.argtypes = [i64, P, f64, i64, ctypes.c_int, u32, u64, u32, P, P, P]
+        L.orc_copy_numbers.argtypes = [i64, P, f64, i64, ctypes.c_int, u32, u64, u32, P, P, P, P, P]
         L.orc_copy_numbers.restype = i64
+        L.orc_round_copies.argtypes = [ctypes.c_int, f64, u32, P]
+        L.orc_round_copies.restype = i32
+        L.orc_exact_sum.argtypes = [i64, P]
+        L.orc_exact_sum.restype = f64
+        L.orc_colour_words.argtypes = [ctypes.c_int]
+        L.orc_colour_words.restype = ctypes.c_int
+        L.orc_word_site.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+        L.orc_word_site.restype = ctypes.c_int
         L.orc_parents.argtypes = [i64, P, P]
         L.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, ctypes.c_int, ctypes.c_int, P,
                               ctypes.c_int, ctypes.c_int, P, P, P, P, P]
@@ -96,7 +104,6 @@ def lib():
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P]
         L.orc_run_adaptive.restype = ctypes.c_int
         assert L.orc_obs_size() == ctypes.sizeof(Obs)
-        del i32
     return _lib
 
 
@@ -169,15 +176,47 @@ def init_ground(q: int, L: int, slot_begin: int, count: int, seed: int, stream: 
     return out
 
 
-def copy_numbers(E: np.ndarray, dbeta: float, R_target: int, mode: int, step: int, seed: int, stream: int = 0):
-    """Returns (r, lnQ, R_new, rho)."""
+def copy_numbers(E: np.ndarray, dbeta: float, R_target: int, mode: int, step: int, seed: int, stream: int = 0,
+                 with_ties: bool = False):
+    """Returns (r, lnQ, R_new, rho), with the per-replica near-tie flags
+    appended when with_ties."""
     e = np.ascontiguousarray(E, dtype=np.int32)
     r = np.zeros(e.size, dtype=np.int32)
     rho = np.zeros(e.size, dtype=np.float64)
+    ties = np.zeros(e.size, dtype=np.int32)
+    n_ties = ctypes.c_int64()
     lnq = ctypes.c_double()
     Rn = lib().orc_copy_numbers(e.size, _p(e), float(dbeta), R_target, mode, step, seed, stream, _p(r),
-                                ctypes.byref(lnq), _p(rho))
+                                ctypes.byref(lnq), _p(rho), _p(ties), ctypes.byref(n_ties))
+    if with_ties:
+        return r, lnq.value, int(Rn), rho, ties
     return r, lnq.value, int(Rn), rho
+
+
+def round_copies(mode: int, rho: float, u: int = 0):
+    """(r, near_tie) of the nearest-integer (uniform word u) or ROUND rule."""
+    tie = ctypes.c_int()
+    r = lib().orc_round_copies(mode, float(rho), int(u), ctypes.byref(tie))
+    return int(r), bool(tie.value)
+
+
+def exact_sum(x) -> float:
+    """The exact sum of non-negative finite doubles, rounded once to the
+    nearest double (ties to even)."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().orc_exact_sum(a.size, _p(a)))
+
+
+def colour_words(L: int) -> int:
+    """Site words of one colour per replica (the sweep's random-number rule)."""
+    return int(lib().orc_colour_words(L))
+
+
+def word_site(L: int, colour: int, w: int, b: int):
+    """(x, y) of the site at bit b of site word w of colour `colour`, or None."""
+    x, y = ctypes.c_int(), ctypes.c_int()
+    ok = lib().orc_word_site(L, colour, w, b, ctypes.byref(x), ctypes.byref(y))
+    return (x.value, y.value) if ok else None
 
 
 def parents(r: np.ndarray) -> np.ndarray:

@@ -254,6 +254,38 @@ static int orc_rows_banded(int L)
     return L > 32 && L % 16 == 0 && L % 64 != 0;
 }
 
+/* Site words of one colour per replica. */
+ORC_API int orc_colour_words(int L)
+{
+    return (orc_rows_packed(L) || orc_rows_banded(L)) ? L * L / 64 : L * ((L + 63) / 64);
+}
+
+/* The site that bit b of site word w of colour c holds, by the rule above:
+ * returns 1 and sets (x, y), or 0 where that bit holds no site (the columns
+ * past L/2 of a row's last word when rows are padded). */
+ORC_API int orc_word_site(int L, int colour, int w, int b, int *x, int *y)
+{
+    int m, row;
+    if (orc_rows_packed(L)) {
+        int h = 32 * w + b;
+        row = h / (L / 2);
+        m = h % (L / 2);
+    } else if (orc_rows_banded(L)) {
+        int segs = L / 16, band_rows = L / 4;
+        row = w / segs + (b >> 3) * band_rows;
+        m = 8 * (w % segs) + (b & 7);
+    } else {
+        int words_per_row = (L + 63) / 64;
+        row = w / words_per_row;
+        m = 32 * (w % words_per_row) + b;
+    }
+    int col = 2 * m + ((colour + row) & 1);
+    if (col >= L) return 0; /* (odd L, accepted by the oracle alone, ends rows early too) */
+    *y = row;
+    *x = col;
+    return 1;
+}
+
 struct orc_word_stream {
     uint64_t seed;
     uint32_t w, c1base, step, c3;
@@ -315,7 +347,7 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], in
                                uint32_t step, uint32_t slot, uint64_t seed, uint32_t stream)
 {
     int B = orc_state_bits(q);
-    int words_per_row = (L + 63) / 64;
+    int words = orc_colour_words(L);
     for (int k = 0; k < theta; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
             struct orc_word_stream st;
@@ -323,40 +355,12 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], in
             st.c1base = ORC_DOM_SWEEP | ((uint32_t)(2 * k + colour) << 8);
             st.step = step;
             st.c3 = slot | (stream << 24);
-            if (orc_rows_packed(L)) {
-                int half = L / 2;
-                for (int w = 0; w < L * half / 32; ++w) {
-                    st.w = (uint32_t)w;
-                    st.have = 0;
-                    for (int b = 0; b < 32; ++b) {
-                        int h = 32 * w + b;
-                        int y = h / half, m = h % half;
-                        orc_attempt(q, B, L, s, 2 * m + ((colour + y) & 1), y, &st, b, T);
-                    }
-                }
-            } else if (orc_rows_banded(L)) {
-                int segs = L / 16, band_rows = L / 4;
-                for (int w = 0; w < band_rows * segs; ++w) {
-                    st.w = (uint32_t)w;
-                    st.have = 0;
-                    int k = w / segs, j = w % segs;
-                    for (int b = 0; b < 32; ++b) {
-                        int y = k + (b >> 3) * band_rows, m = 8 * j + (b & 7);
-                        orc_attempt(q, B, L, s, 2 * m + ((colour + y) & 1), y, &st, b, T);
-                    }
-                }
-            } else {
-                for (int y = 0; y < L; ++y) {
-                    int x0 = (colour + y) & 1;  /* first column of this colour in row y */
-                    for (int t = 0; t < words_per_row; ++t) {
-                        st.w = (uint32_t)(y * words_per_row + t);
-                        st.have = 0;
-                        for (int b = 0; b < 32; ++b) {
-                            int x = 2 * (32 * t + b) + x0;
-                            if (x >= L) break;
-                            orc_attempt(q, B, L, s, x, y, &st, b, T);
-                        }
-                    }
+            for (int w = 0; w < words; ++w) {
+                st.w = (uint32_t)w;
+                st.have = 0;
+                for (int b = 0; b < 32; ++b) {
+                    int x, y;
+                    if (orc_word_site(L, colour, w, b, &x, &y)) orc_attempt(q, B, L, s, x, y, &st, b, T);
                 }
             }
         }
@@ -404,14 +408,122 @@ ORC_API void orc_init_ground(int q, int L, int64_t slot_begin, int64_t count, ui
 /* ------------------------------------------------------------------------- */
 enum { ORC_NEAREST_INT = 0, ORC_ROUND = 1, ORC_POISSON = 2, ORC_OFF = 3 };
 
+/* reading (the normaliser): Q_i = sum_j w_j / R_{i-1} is a sum of positive
+ * doubles whose value the paper defines exactly.  S = sum_j w_j is taken as
+ * that exact sum rounded once to the nearest double (ties to even), so it does
+ * not depend on any summation order.  The accumulator below holds a sum of
+ * non-negative finite doubles as an integer count of 2^-1074 (the smallest
+ * positive double) in 32-bit limbs; limb k holds bits 32k .. 32k + 31. */
+#define ORC_ACC_LIMBS 72
+
+typedef struct {
+    uint32_t limb[ORC_ACC_LIMBS];
+} orc_acc;
+
+/* adds v * 2^(32 k) with carry propagation */
+static void orc_acc_add_word(orc_acc *a, int k, uint64_t v)
+{
+    while (v != 0) {
+        uint64_t s = (uint64_t)a->limb[k] + (v & 0xFFFFFFFFu);
+        a->limb[k] = (uint32_t)s;
+        v = (v >> 32) + (s >> 32);
+        k += 1;
+    }
+}
+
+/* adds x (finite, >= 0): x = m 2^(pos - 1074) with m an integer below 2^53 */
+static void orc_acc_add(orc_acc *a, double x)
+{
+    uint64_t m;
+    int pos;
+    if (x == 0.0) return;
+    if (x < 2.2250738585072014e-308) { /* subnormal: a multiple of 2^-1074 */
+        m = (uint64_t)ldexp(x, 1074);
+        pos = 0;
+    } else {
+        int e;
+        double f = frexp(x, &e); /* x = f 2^e, 1/2 <= f < 1 */
+        m = (uint64_t)ldexp(f, 53);
+        pos = e - 53 + 1074;
+    }
+    int k = pos / 32, sh = pos % 32;
+    orc_acc_add_word(a, k, (m & 0xFFFFFFFFu) << sh);
+    orc_acc_add_word(a, k + 1, (m >> 32) << sh);
+}
+
+static int orc_acc_bit(const orc_acc *a, int i)
+{
+    return (int)(a->limb[i / 32] >> (i % 32)) & 1;
+}
+
+/* The accumulated value rounded to the nearest double, ties to even. */
+static double orc_acc_round(const orc_acc *a)
+{
+    int top = -1;
+    for (int i = 32 * ORC_ACC_LIMBS - 1; i >= 0; --i) {
+        if (orc_acc_bit(a, i)) {
+            top = i;
+            break;
+        }
+    }
+    if (top < 0) return 0.0;
+    uint64_t m = 0;
+    if (top < 53) { /* at most 53 significant bits: exact */
+        for (int i = top; i >= 0; --i) m = 2 * m + (uint64_t)orc_acc_bit(a, i);
+        return ldexp((double)m, -1074);
+    }
+    for (int i = top; i > top - 53; --i) m = 2 * m + (uint64_t)orc_acc_bit(a, i);
+    int round = orc_acc_bit(a, top - 53), sticky = 0;
+    for (int i = top - 54; i >= 0 && !sticky; --i) sticky = orc_acc_bit(a, i);
+    if (round && (sticky || (m & 1))) m += 1; /* m = 2^53 is still exact */
+    return ldexp((double)m, top - 52 - 1074);
+}
+
+/* sum_j x[j] exact, rounded once (x[j] finite and >= 0). */
+ORC_API double orc_exact_sum(int64_t n, const double *x)
+{
+    orc_acc a;
+    memset(&a, 0, sizeof(a));
+    for (int64_t j = 0; j < n; ++j) orc_acc_add(&a, x[j]);
+    return orc_acc_round(&a);
+}
+
+/* reading (near ties): a copy number is flagged as a near tie when the
+ * quantity its rule compares lies closer to the decision boundary than
+ * delta = 2^-48 max(1, rho_j), a bound well above the rounding error rho_j can
+ * carry (a few units in the last place): for nearest-integer copy numbers when
+ * frac(rho_j) lies within delta of u_j / 2^32, for ROUND when it lies within
+ * delta of 1/2, for Poisson draws when a uniform of the inversion lies within
+ * 2^-40 of the cumulative probability it is compared with.  (A last-place
+ * change that moves rho_j across an integer changes floor(rho_j) and frac
+ * together and leaves r_j as it is, except through u_j = 0, which the first
+ * test covers.)  The flag changes nothing; it counts the draws whose outcome a
+ * last-place difference in rho_j could change. */
+
+/* One copy number with mean rho, nearest-integer (u the replica's uniform
+ * word) or ROUND; *tie receives the near-tie flag. */
+ORC_API int32_t orc_round_copies(int mode, double rho, uint32_t u, int *tie)
+{
+    double n = floor(rho);
+    double frac = rho - n;
+    double delta = 0x1p-48 * (rho > 1.0 ? rho : 1.0);
+    if (mode == ORC_ROUND) {
+        *tie = fabs(frac - 0.5) < delta;
+        return (int32_t)n + (frac >= 0.5);
+    }
+    *tie = fabs(frac - (double)u * 0x1p-32) < delta;
+    return (int32_t)n + ((double)u < frac * 4294967296.0);
+}
+
 /* A Poisson draw with mean rho for replica j (Sec. 2, Eq. 1), by inversion of
  * the cumulative distribution, the mean split into pieces of at most 64 (a
  * sum of independent Poisson variables is Poisson with the summed mean, and
  * exp(-64) is far from underflow).  The k-th uniform, (U_k + 1/2) / 2^32, is
  * word k & 3 of counter (j, RESAMPLE | (1 + k / 4), step, stream << 24). */
-static int32_t orc_poisson(double rho, int64_t j, uint32_t step, uint64_t seed, uint32_t stream)
+static int32_t orc_poisson(double rho, int64_t j, uint32_t step, uint64_t seed, uint32_t stream, int *tie)
 {
     int32_t r = 0;
+    *tie = 0;
     double remaining = rho;
     uint32_t k = 0;
     uint32_t w[4] = {0, 0, 0, 0};
@@ -424,7 +536,9 @@ static int32_t orc_poisson(double rho, int64_t j, uint32_t step, uint64_t seed, 
         double p = exp(-mu);
         double F = p;
         int32_t n = 0;
-        while (u > F && n < 1000) {
+        for (;;) {
+            if (fabs(u - F) < 0x1p-40) *tie = 1;
+            if (!(u > F && n < 1000)) break;
             n += 1;
             p = p * mu / (double)n;
             F = F + p;
@@ -439,55 +553,52 @@ static int32_t orc_poisson(double rho, int64_t j, uint32_t step, uint64_t seed, 
  *
  * The Boltzmann factors are evaluated relative to E_ref, the lowest energy for
  * dbeta >= 0 and the highest for dbeta < 0, so that no factor overflows:
- *   w_j = exp(-dbeta (E_j - E_ref)),  S = sum_j w_j (ascending j),
+ *   w_j = exp(-dbeta (E_j - E_ref)),  S = sum_j w_j (exact, rounded once),
  *   ln Q_i = -dbeta E_ref + ln(S / R_prev)          (= ln of the paper's Q_i),
  *   rho_j = (R w_j) / S                              (= (R/R_{i-1}) tau_i(E_j)).
  * reading: "nearest-integer" copy numbers draw r_j from the two integers
  * nearest to rho_j with the mean kept exact: r_j = floor(rho_j) + [u_j <
- * frac(rho_j) 2^32], u_j = word (j & 3) of counter (j >> 2, RESAMPLE, step, 0).
- * ORC_ROUND instead takes the nearest integer, halves rounded up;
- * ORC_POISSON draws r_j ~ Pois(rho_j), the paper's Eq. 1; ORC_OFF keeps every
- * replica once (the resampling-off comparison of Sec. 5, Fig. 2 right).
- * rho_out (optional) receives rho_j.  Returns the new population size. */
+ * frac(rho_j) 2^32], u_j = word (j & 3) of counter (j >> 2, RESAMPLE, step,
+ * stream << 24).  ORC_ROUND instead takes the nearest integer, halves rounded
+ * up; ORC_POISSON draws r_j ~ Pois(rho_j), the paper's Eq. 1; ORC_OFF keeps
+ * every replica once (the resampling-off comparison of Sec. 5, Fig. 2 right).
+ * rho_out and tie_out (optional) receive rho_j and the near-tie flag of each
+ * replica, n_ties (optional) the number of flagged replicas.  Returns the new
+ * population size. */
 ORC_API int64_t orc_copy_numbers(int64_t R_prev, const int32_t *E, double dbeta, int64_t R_target,
                                  int mode, uint32_t step, uint64_t seed, uint32_t stream, int32_t *r,
-                                 double *lnQ, double *rho_out)
+                                 double *lnQ, double *rho_out, int32_t *tie_out, int64_t *n_ties)
 {
     int32_t E_ref = E[0];
     for (int64_t j = 1; j < R_prev; ++j) {
         if (dbeta >= 0.0 ? (E[j] < E_ref) : (E[j] > E_ref)) E_ref = E[j];
     }
-    double S = 0.0;
-    for (int64_t j = 0; j < R_prev; ++j) S += exp(-dbeta * (double)(E[j] - E_ref));
+    double *w = (double *)calloc((size_t)(R_prev > 0 ? R_prev : 1), sizeof(double));
+    for (int64_t j = 0; j < R_prev; ++j) w[j] = exp(-dbeta * (double)(E[j] - E_ref));
+    double S = orc_exact_sum(R_prev, w);
     *lnQ = -dbeta * (double)E_ref + log(S / (double)R_prev);
-    int64_t total = 0;
+    int64_t total = 0, ties = 0;
     for (int64_t j = 0; j < R_prev; ++j) {
-        double w = exp(-dbeta * (double)(E[j] - E_ref));
-        double rho = ((double)R_target * w) / S;
+        double rho = ((double)R_target * w[j]) / S;
         if (rho_out) rho_out[j] = rho;
-        double n = floor(rho);
-        double frac = rho - n;
-        int32_t up;
+        int tie = 0;
         if (mode == ORC_POISSON) {
-            r[j] = orc_poisson(rho, j, step, seed, stream);
-            total += r[j];
-            continue;
-        }
-        if (mode == ORC_OFF) {
+            r[j] = orc_poisson(rho, j, step, seed, stream, &tie);
+        } else if (mode == ORC_OFF) {
             r[j] = 1;
-            total += 1;
-            continue;
-        }
-        if (mode == ORC_ROUND) {
-            up = frac >= 0.5;
+        } else if (mode == ORC_ROUND) {
+            r[j] = orc_round_copies(ORC_ROUND, rho, 0u, &tie);
         } else {
             uint32_t u[4];
             orc_draw(seed, (uint32_t)(j >> 2), ORC_DOM_RESAMPLE, step, stream << 24, u);
-            up = (double)u[j & 3] < frac * 4294967296.0;
+            r[j] = orc_round_copies(ORC_NEAREST_INT, rho, u[j & 3], &tie);
         }
-        r[j] = (int32_t)n + up;
+        if (tie_out) tie_out[j] = tie;
+        ties += tie;
         total += r[j];
     }
+    free(w);
+    if (n_ties) *n_ties = ties;
     return total;
 }
 
@@ -504,7 +615,7 @@ ORC_API void orc_parents(int64_t R_prev, const int32_t *r, int32_t *parent)
 /* ------------------------------------------------------------------------- */
 typedef struct {
     double beta, lnQ, lnZ, meanE, meanE2, C, meanM, S_f;
-    int64_t R, n_families, sumE, sumE2, sumMt;
+    int64_t R, n_families, sumE, sumE2, sumMt, n_near_ties;
 } orc_obs;
 
 /* Population averages over R replicas with energies E and largest-state
@@ -533,6 +644,7 @@ static void orc_measure(int q, int N, int64_t R, const int32_t *E, const int32_t
     o->meanM = (double)((int64_t)q * sM - (int64_t)N * R) / ((double)(q - 1) * (double)R);
     o->S_f = 0.0;
     o->n_families = 0;
+    o->n_near_ties = 0;
     if (anc) {
         int64_t *count = (int64_t *)calloc((size_t)R0, sizeof(int64_t));
         for (int64_t j = 0; j < R; ++j) count[anc[j]] += 1;
@@ -604,7 +716,8 @@ ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, u
     for (int i = 1; i <= K; ++i) {
         double dbeta = betas[i] - betas[i - 1];
         double lnQ;
-        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, stream, r, &lnQ, NULL);
+        int64_t ties = 0;
+        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, stream, r, &lnQ, NULL, NULL, &ties);
         if (Rn > R_cap || Rn <= 0) {
             result = -1;
             break;
@@ -629,6 +742,7 @@ ORC_API int64_t orc_run(int q, int L, int64_t R, int64_t R_cap, uint64_t seed, u
         orc_measure(q, N, Rc, E, Mt, betas[i], anc, R, &obs[i]);
         obs[i].lnQ = lnQ;
         obs[i].lnZ = lnZ;
+        obs[i].n_near_ties = ties;
         if (hist) {
             int32_t *h = hist + (int64_t)i * (2 * N + 1);
             memset(h, 0, sizeof(int32_t) * (size_t)(2 * N + 1));
@@ -863,7 +977,8 @@ ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t se
         double nb = (dbeta == room) ? beta_end : beta + dbeta;
         int i = K + 1;
         double lnQ;
-        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, stream, r, &lnQ, NULL);
+        int64_t ties = 0;
+        int64_t Rn = orc_copy_numbers(Rc, E, dbeta, R, mode, (uint32_t)i, seed, stream, r, &lnQ, NULL, NULL, &ties);
         if (Rn > R_cap || Rn <= 0) {
             K = -1;
             break;
@@ -883,6 +998,7 @@ ORC_API int orc_run_adaptive(int q, int L, int64_t R, int64_t R_cap, uint64_t se
         orc_measure(q, N, Rc, E, Mt, nb, NULL, R, &obs[i]);
         obs[i].lnQ = lnQ;
         obs[i].lnZ = lnZ;
+        obs[i].n_near_ties = ties;
         betas[i] = nb;
         beta = nb;
         K = i;

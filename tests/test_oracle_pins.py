@@ -547,3 +547,188 @@ def test_resampling_off_keeps_every_replica():
     assert np.all(r == 1) and Rn == 40
     out = oracle.run(6, 8, 300, 1, 2, np.linspace(0, 1.5, 11), mode=oracle.OFF)
     assert np.all(out["R"] == 300) and np.all(out["n_families"] == 300)  # no family is lost
+
+
+# --------------------------------------------------------------------------
+# The normaliser S: the exact sum of the weights, rounded once (Sec. 2 step 2)
+# --------------------------------------------------------------------------
+def _correctly_rounded_sum(xs):
+    """Python's rational arithmetic: the exact sum, then one correctly rounded
+    conversion (int / int true division rounds correctly)."""
+    from fractions import Fraction
+
+    return float(sum((Fraction(float(x)) for x in xs), Fraction(0)))
+
+
+def test_exact_sum_is_the_correctly_rounded_sum():
+    rng = np.random.default_rng(11)
+    eps = 2.0 ** -52
+    cases = [
+        rng.random(2000),
+        np.exp(-0.008 * rng.integers(0, 8193, size=5000)),      # PA weights at dbeta = 0.008
+        np.exp(-0.7 * rng.integers(0, 300, size=3000)),         # down to 1e-91
+        np.array([1.0] + [2.0 ** -60] * 5000),                  # naive summation drops every small term
+        np.array([1.0, 2.0 ** -53]),                            # exactly halfway: ties to even (down)
+        np.array([1.0, 2.0 ** -53, 2.0 ** -300]),               # just above halfway: up
+        np.array([1.0 + eps, 2.0 ** -53]),                      # halfway from an odd mantissa: up
+        np.array([5e-324, 5e-324, 3 * 5e-324, 2.0 ** -1022]),   # subnormals
+        np.array([0.0, 0.0]),
+        np.array([2.0 ** 52, 0.5, 0.5, 0.25]),
+        np.array([1e300, 1e300, 1e-300]),
+        rng.random(7) * 2.0 ** rng.integers(-1070, 1000, size=7),
+    ]
+    for xs in cases:
+        want = _correctly_rounded_sum(xs)
+        got = oracle.exact_sum(xs)
+        assert got == want, (xs[:4], got, want)
+        assert oracle.exact_sum(rng.permutation(xs)) == got  # no summation order
+        assert got == math.fsum(xs)
+    assert oracle.exact_sum(np.array([1.0, 2.0 ** -53])) == 1.0
+    assert oracle.exact_sum(np.array([1.0 + eps, 2.0 ** -53])) == 1.0 + 2 * eps
+
+
+def test_copy_number_normaliser_is_exact_and_order_free():
+    """S enters ln Q and every rho_j; with the exact sum, the oracle's ln Q
+    equals -dbeta E_ref + ln(S/R) for the correctly rounded S, and a permuted
+    population gives bit-identical rho (as a multiset)."""
+    rng = np.random.default_rng(3)
+    E = rng.integers(-700, -400, size=3000).astype(np.int32)
+    dbeta = 0.0123
+    r, lnq, Rn, rho = oracle.copy_numbers(E, dbeta, 3000, oracle.NEAREST_INT, 4, 9)
+    # the C library's exp, as the oracle uses (numpy's exp rounds differently)
+    w = np.array([math.exp(-dbeta * float(e - E.min())) for e in E])
+    S = _correctly_rounded_sum(w)
+    assert lnq == -dbeta * float(E.min()) + math.log(S / E.size)
+    assert np.array_equal(rho, (3000.0 * w) / S)
+    perm = rng.permutation(E.size)
+    _, lnq2, _, rho2 = oracle.copy_numbers(E[perm], dbeta, 3000, oracle.NEAREST_INT, 4, 9)
+    assert lnq2 == lnq
+    assert np.array_equal(np.sort(rho2), np.sort(rho))
+
+
+# --------------------------------------------------------------------------
+# Near-tie flags of the copy-number rules
+# --------------------------------------------------------------------------
+def _nudged(rho, k):
+    x = rho
+    for _ in range(abs(k)):
+        x = np.nextafter(x, math.inf if k > 0 else -math.inf)
+    return x
+
+
+def test_near_tie_flag_marks_every_draw_a_last_place_change_could_flip():
+    """Unflagged draws keep their copy number when rho moves by up to eight
+    units in the last place; draws placed exactly on a boundary are flagged;
+    the flag fires for a fraction of random draws close to 2 delta 2^32."""
+    rng = np.random.default_rng(5)
+    flagged = 0
+    n = 20000
+    for _ in range(n):
+        rho = float(rng.exponential(1.5))
+        u = int(rng.integers(0, 2**32))
+        for mode in (oracle.NEAREST_INT, oracle.ROUND):
+            r, tie = oracle.round_copies(mode, rho, u)
+            assert r in (math.floor(rho), math.floor(rho) + 1)
+            flagged += tie
+            if not tie:
+                for k in (-8, -3, -1, 1, 3, 8):
+                    assert oracle.round_copies(mode, _nudged(rho, k), u)[0] == r, (mode, rho, u, k)
+    assert flagged <= 3  # expected about 2 n 2^-48 2^32 ~ 6e-4
+    # on the boundary: frac(rho) = u / 2^32, or 1/2 for ROUND
+    for n0 in (0, 1, 3, 17):
+        for u in (1, 12345, 2**31, 2**32 - 7):
+            rho = n0 + u * 2.0 ** -32
+            assert oracle.round_copies(oracle.NEAREST_INT, rho, u)[1]
+            r_lo = oracle.round_copies(oracle.NEAREST_INT, _nudged(rho, -1), u)[0]
+            r_hi = oracle.round_copies(oracle.NEAREST_INT, _nudged(rho, 1), u)[0]
+            assert (r_lo, r_hi) == (n0, n0 + 1)
+        assert oracle.round_copies(oracle.ROUND, n0 + 0.5)[1]
+        assert oracle.round_copies(oracle.ROUND, _nudged(n0 + 0.5, -1))[0] == n0
+
+
+def test_near_tie_count_of_a_run_matches_the_flags():
+    q, L, R = 6, 8, 1500
+    betas = np.linspace(0.0, 1.2, 9)
+    out = oracle.run(q, L, R, 4, 2, betas, want_state=False)
+    assert out["n_near_ties"][0] == 0
+    assert np.all(out["n_near_ties"] >= 0) and out["n_near_ties"].sum() <= 2
+
+
+# --------------------------------------------------------------------------
+# Magnetisation and specific heat (Sec. 3, Eqs. 4-5; fluctuation formula)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("q,L", [(3, 4), (10, 6)])
+def test_ground_state_population_has_full_magnetisation(q, L):
+    """A replica in a ground state has m = 1 (Eq. 5, every site in one state),
+    so a population of ground states has <M> = N exactly; a wrong (q - 1)
+    normalisation would not give N."""
+    N = L * L
+    out = oracle.run(q, L, 500, 2, 3, np.array([2.5]), init_mode=oracle.INIT_GROUND, want_state=False)
+    assert out["meanM"][0] == N
+    assert out["sumMt"][0] == 500 * N
+
+
+def test_infinite_temperature_magnetisation_matches_enumeration():
+    """<M> at beta = 0 over q^N equally likely configurations (exact, by
+    enumeration of the largest occupation) against the oracle's population of
+    independent uniform replicas, within 5 standard errors."""
+    import itertools
+
+    q, L = 3, 2
+    N = L * L
+    Mt = np.array([max(np.bincount(c, minlength=q)) for c in itertools.product(range(q), repeat=N)], dtype=float)
+    M = (q * Mt - N) / (q - 1)
+    R = 40000
+    out = oracle.run(q, L, R, 8, 1, np.array([0.0]), want_state=False)
+    assert abs(out["meanM"][0] - M.mean()) < 5 * M.std() / math.sqrt(R)
+
+
+def _var_E_from_dos(g, N, beta):
+    E = np.arange(-2 * N, 1, dtype=np.float64)
+    gg = g.astype(np.float64)
+    a = np.where(gg > 0, np.log(np.maximum(gg, 1)) - beta * E, -np.inf)
+    w = np.exp(a - a.max())
+    m1 = (w * E).sum() / w.sum()
+    return float((w * (E - m1) ** 2).sum() / w.sum())
+
+
+def test_specific_heat_matches_exact_enumeration():
+    """The oracle's C = beta^2 (<E^2> - <E>^2) / N from PA populations against
+    beta^2 var(E) / N from the exact density of states (4 x 4, q = 3), within
+    5 standard errors over seeds."""
+    q, L = 3, 4
+    N = L * L
+    g = oracle.density_of_states(q, L)
+    betas = np.linspace(0.0, 1.6, 17)
+    C = np.array([oracle.run(q, L, 6000, s, 5, betas, want_state=False)["C"] for s in range(1, 7)])
+    for i in (4, 8, 10, 12, 16):
+        ex = betas[i] ** 2 * _var_E_from_dos(g, N, betas[i]) / N
+        se = C[:, i].std(ddof=1) / math.sqrt(C.shape[0])
+        assert abs(C[:, i].mean() - ex) < 5 * se + 5e-3 * ex, (i, C[:, i].mean(), ex, se)
+
+
+# --------------------------------------------------------------------------
+# The sweep's random-number rule: site words of each colour (Sec. 2 step 3 reading)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 16, 24, 32, 48, 64, 66, 80, 96, 112, 128, 130, 144, 160, 192, 256])
+def test_site_words_are_a_bijection_onto_each_colour(L):
+    """For each colour the valid (word, bit) pairs map one to one onto that
+    colour's L^2/2 sites; with packed rows (L = 8, 16, 32, 64) and banded rows
+    (L = 48, 80, 96, ...) every bit of every word holds a site."""
+    words = oracle.colour_words(L)
+    full = (L >= 8 and 64 % L == 0) or (L > 32 and L % 16 == 0 and L % 64 != 0)
+    for c in (0, 1):
+        seen = {}
+        for w in range(words):
+            for b in range(32):
+                xy = oracle.word_site(L, c, w, b)
+                if xy is None:
+                    assert not full, (L, c, w, b)
+                    continue
+                x, y = xy
+                assert 0 <= x < L and 0 <= y < L and (x + y) % 2 == c
+                assert (x, y) not in seen, (L, c, w, b, seen.get((x, y)))
+                seen[(x, y)] = (w, b)
+        assert len(seen) == L * L // 2
+    if full:
+        assert words == L * L // 64
