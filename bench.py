@@ -81,7 +81,7 @@ def replica_bytes(q: int, L: int) -> int:
 # ALU pipe: 4 schedulers x 16 lanes per SM and clock (ncu counts its peak as half a
 # warp instruction per scheduler and cycle)
 LANES_PER_SM_PER_CLK = 64
-PA_OBS_BYTES = 104
+PA_OBS_BYTES = 112
 DEVSTATE_BYTES = 48
 
 

@@ -49,7 +49,9 @@ typedef enum {
     PA_ERR_INVALID = 1,  /* an argument is out of range, see each call         */
     PA_ERR_CAPACITY = 2, /* a resampled population would exceed R_cap          */
     PA_ERR_CUDA = 3,     /* a CUDA runtime call failed; see pa_last_cuda_error */
-    PA_ERR_TIMEOUT = 4,  /* a bounded device wait gave up                      */
+    PA_ERR_TIMEOUT = 4,  /* reserved for bounded device waits; no call of this
+                            version returns it (its kernels do not wait on one
+                            another)                                          */
     PA_ERR_STATE = 5,    /* calls in the wrong order, or a failed context      */
     PA_ERR_NOMEM = 6,    /* device or host allocation failed                   */
     PA_ERR_TOO_LARGE = 7 /* a replica larger than one block's shared memory
@@ -96,10 +98,17 @@ typedef struct {
  *   S_f   = -sum_f nu_f ln nu_f, nu_f the fraction of replicas descending from
  *           initial replica f (family entropy; the paper does not define it),
  *           n_families the number of such f with nu_f > 0.  Both 0 unless
- *           track_families. */
+ *           track_families;
+ *   n_near_ties = copy numbers of the resampling into this step whose outcome
+ *           a change of rho_j in its last places could have changed: for
+ *           NEAREST_INT frac(rho_j) within 2^-48 max(1, rho_j) of u_j / 2^32,
+ *           for ROUND within that distance of 1/2, for POISSON a uniform of
+ *           the inversion within 2^-40 of the cumulative probability it is
+ *           compared with (0 at step 0 and for OFF).  A diagnostic only: it
+ *           changes no outcome. */
 typedef struct {
     double beta, lnQ, lnZ, meanE, meanE2, C, meanM, S_f;
-    int64_t R, n_families, sumE, sumE2, sumMt;
+    int64_t R, n_families, sumE, sumE2, sumMt, n_near_ties;
 } pa_obs;
 
 typedef struct pa_ctx pa_ctx;
@@ -128,6 +137,12 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
  * computes ln Q_i from the current energy histogram, the copy numbers r_j
  * (per resample_mode), their exclusive scan and the parent map of the new
  * population.  The replica gather itself is fused into the next pa_sweep.
+ * Arithmetic: with E_ref the lowest energy (highest for dbeta < 0), the
+ * weights w = exp(-dbeta (E - E_ref)) come from a table the host computes
+ * with the C library's exp (once per distinct dbeta, then kept on the device);
+ * S = sum_j w_j is summed exactly and rounded once to the nearest double;
+ * rho_j = (R w_j) / S; ln Q_i = -dbeta E_ref + ln(S / R_{i-1}).  So S, rho_j
+ * and the copy numbers do not depend on the device's summation order.
  * `step` is the temperature-step index i >= 1 (part of the random key) and
  * must exceed the previous step's.  dbeta may be negative (heating, Sec. 5).
  * If lnQ_out or R_out is non-NULL the call synchronises and writes ln Q_i and
@@ -190,6 +205,14 @@ pa_status pa_get_spins(pa_ctx *ctx, int64_t slot_begin, int64_t count, uint8_t *
 /* Initial-replica (family) ids of the current population, host int32[R_i]
  * (synchronises).  PA_ERR_STATE unless track_families. */
 pa_status pa_get_ancestors(pa_ctx *ctx, int32_t *host);
+
+/* Parent map of the latest resampling step (Sec. 2 step 2): out[k] = the slot,
+ * in the population before that step, of the replica that new slot k copies;
+ * children of one parent are consecutive and parents ascend.  R_i int32
+ * values (R_i the size after that step, pending or swept).  on_device = 0:
+ * out is host memory (the call synchronises); 1: a device pointer (the copy is
+ * enqueued).  PA_ERR_STATE before the first resample. */
+pa_status pa_get_parents(pa_ctx *ctx, int32_t *out, int32_t on_device);
 
 /* Runs the temperature schedule betas[1..K] from the context's current step:
  * for i = 1..K, resample by betas[i] - betas[i-1] then theta sweeps at
@@ -379,28 +402,34 @@ pa_status pa_profile_read(pa_ctx *ctx, double *ms_out2, int64_t *launches_out2);
  * device or fail under memory pressure in the middle of their work).
  *
  * It computes, for the R_prev energies E[0..R_prev) (device int32, each in
- * [-2N, 0], N = L*L) of a population, the same quantities as pa_resample: ln Q
- * for the step dbeta, the copy numbers under `mode` (random words keyed by
- * seed and step) and the parent map of the new population,
+ * [-2N, 0], N = L*L) of a population, the same quantities as pa_resample
+ * (same arithmetic, bit for bit): ln Q for the step dbeta, the copy numbers
+ * under `mode` (random words keyed by seed, step and rng_stream, 0..255, the
+ * pa_config stream of the run) and the parent map of the new population,
  * parent[0..R_i) (device int32, capacity parent_cap >= R_prev), with the new
  * size in *R_out and ln Q in *lnQ_out (both device pointers).  The work is
  * only enqueued on cuda_stream; read the outputs after synchronising.  If an
  * energy lies outside [-2N, 0] *R_out becomes -PA_ERR_INVALID, and if R_i would
- * exceed parent_cap, -PA_ERR_CAPACITY; parent is then unspecified.
+ * exceed parent_cap, -PA_ERR_CAPACITY; parent is then unspecified.  The
+ * Boltzmann factors are computed on the host and copied from host memory into
+ * the working memory (skipped when the previous call on that device used the
+ * same dbeta); that copy may wait for earlier work on cuda_stream.
  *
  * Working memory: one fixed array of about 3.6 MB inside the library's device
  * image, held by every GPU that loads the library until the process exits.
- * Limits: L <= 256, R_prev <= 262144, parent_cap <= 262144; larger sizes
- * return PA_ERR_TOO_LARGE.  The first call on each device looks up that
- * array's device address (cudaGetSymbolAddress, with the device current); make
- * that first call before any stream capture.  All calls share the array and
- * overwrite it: calls whose work overlaps on the GPU race, calls ordered on
- * one stream do not.  Returns PA_ERR_INVALID for null pointers, odd L, R_prev
- * < 1, R_target < 1, parent_cap < R_prev, an unknown mode or a non-finite
- * dbeta, and PA_ERR_CUDA if a launch fails. */
+ * Limits: L <= 256 and R_prev <= 262144 (larger sizes return
+ * PA_ERR_TOO_LARGE); parent_cap is the caller's and is not limited.  The first
+ * call on each device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call before
+ * any stream capture.  All calls share the array and overwrite it: calls whose
+ * work overlaps on the GPU race, calls ordered on one stream do not.  Returns
+ * PA_ERR_INVALID for null pointers, odd L, R_prev < 1, R_target < 1,
+ * parent_cap < R_prev, an unknown mode, rng_stream outside 0..255 or a
+ * non-finite dbeta, and PA_ERR_CUDA if a launch fails or if a CUDA error is
+ * already pending on the calling thread (left pending for its owner). */
 pa_status pa_resample_noalloc(const int32_t *E, int32_t R_prev, int32_t L, double dbeta, int32_t R_target,
-                              int32_t mode, int32_t step, uint64_t seed, int32_t *parent, int32_t parent_cap,
-                              double *lnQ_out, int32_t *R_out, void *cuda_stream);
+                              int32_t mode, int32_t step, uint64_t seed, int32_t rng_stream, int32_t *parent,
+                              int32_t parent_cap, double *lnQ_out, int32_t *R_out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

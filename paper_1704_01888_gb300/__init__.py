@@ -41,6 +41,7 @@ EXPORTED = (
     "pa_overlap", "pa_next_dbeta", "pa_run_adaptive", "pa_batch_create", "pa_batch_autotune", "pa_batch_set_launch",
     "pa_batch_get_launch", "pa_batch_run", "pa_batch_observables", "pa_batch_get_spins", "pa_batch_destroy",
     "pa_batch_population_size", "pa_save", "pa_load", "pa_occupations", "pa_batch_measurements",
+    "pa_get_parents",
 )
 
 
@@ -68,7 +69,7 @@ class Obs(ctypes.Structure):
         ("meanE", ctypes.c_double), ("meanE2", ctypes.c_double), ("C", ctypes.c_double),
         ("meanM", ctypes.c_double), ("S_f", ctypes.c_double),
         ("R", ctypes.c_int64), ("n_families", ctypes.c_int64), ("sumE", ctypes.c_int64),
-        ("sumE2", ctypes.c_int64), ("sumMt", ctypes.c_int64),
+        ("sumE2", ctypes.c_int64), ("sumMt", ctypes.c_int64), ("n_near_ties", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -99,6 +100,7 @@ def load_library(path: str | None = None):
         "pa_population_size": ([P, P], st),
         "pa_get_spins": ([P, i64, i64, P], st),
         "pa_get_ancestors": ([P, P], st),
+        "pa_get_parents": ([P, P, i32], st),
         "pa_run": ([P, P, i32, i32, P, P, i32, P, i32], st),
         "pa_destroy": ([P], None),
         "pa_status_str": ([st], ctypes.c_char_p),
@@ -109,7 +111,7 @@ def load_library(path: str | None = None):
         "pa_profile_read": ([P, P, P], st),
         "pa_observables_history": ([P, i32, P], st),
         "pa_get_launch": ([P, P, P, P], st),
-        "pa_resample_noalloc": ([P, i32, i32, f64, i32, i32, i32, ctypes.c_uint64, P, i32, P, P, P], st),
+        "pa_resample_noalloc": ([P, i32, i32, f64, i32, i32, i32, ctypes.c_uint64, i32, P, i32, P, P, P], st),
         "pa_reweight_forward": ([P, P, i32, P, P, P], st),
         "pa_reweight_scale": ([P, i32, f64, P, P, P], st),
         "pa_reweight_grad_O": ([P, i32, P, P, P, P, P], st),
@@ -160,13 +162,15 @@ def _current_stream() -> int:
 
 
 def resample_noalloc(E_ptr: int, R_prev: int, L: int, dbeta: float, R_target: int, mode: int, step: int,
-                     seed: int, parent_ptr: int, parent_cap: int, lnQ_ptr: int, R_ptr: int, stream: int) -> None:
+                     seed: int, parent_ptr: int, parent_cap: int, lnQ_ptr: int, R_ptr: int, stream: int,
+                     rng_stream: int = 0) -> None:
     """pa_resample_noalloc on device pointers (see include/pa.h): resampling
     for callers that may not allocate device memory.  Raises PAError on a
     rejected call; the results land in the device outputs."""
     _check(load_library().pa_resample_noalloc(
-        ctypes.c_void_p(E_ptr), R_prev, L, float(dbeta), R_target, mode, step, seed, ctypes.c_void_p(parent_ptr),
-        parent_cap, ctypes.c_void_p(lnQ_ptr), ctypes.c_void_p(R_ptr), ctypes.c_void_p(stream)), "pa_resample_noalloc")
+        ctypes.c_void_p(E_ptr), R_prev, L, float(dbeta), R_target, mode, step, seed, int(rng_stream),
+        ctypes.c_void_p(parent_ptr), parent_cap, ctypes.c_void_p(lnQ_ptr), ctypes.c_void_p(R_ptr),
+        ctypes.c_void_p(stream)), "pa_resample_noalloc")
 
 
 def kernel_launch_count() -> int:
@@ -319,6 +323,15 @@ class Population:
     def ancestors(self) -> np.ndarray:
         out = np.zeros(self.size(), dtype=np.int32)
         _check(self.lib.pa_get_ancestors(self._ctx, _ptr(out)), "pa_get_ancestors")
+        return out
+
+    def parents(self, count: int | None = None) -> np.ndarray:
+        """Parent map of the latest resampling step (Sec. 2 step 2): entry k is
+        the previous-population slot that new slot k copies.  `count` is the
+        new size R_i (the current size once the step has been swept)."""
+        n = self.size() if count is None else int(count)
+        out = np.zeros(n, dtype=np.int32)
+        _check(self.lib.pa_get_parents(self._ctx, _ptr(out), 0), "pa_get_parents")
         return out
 
     def set_launch(self, replicas_per_block: int = 0, threads_per_block: int = 0):

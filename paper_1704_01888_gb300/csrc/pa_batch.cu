@@ -52,14 +52,14 @@ __global__ void k_batch_init(const BatchArgs b)
 
 __global__ void __launch_bounds__(kB) k_batch_weights(const BatchArgs b)
 {
-    __shared__ double s_d[32];
+    __shared__ unsigned long long s_acc[dev::kSumLimbs];
     __shared__ long long s_l[32];
     const int m = blockIdx.x;
     const int i = *b.step_counter;
     const StepDev sp = b.steps[(size_t)i * b.M + m];
     if (!sp.active) return;
     const RunDev &r = b.runs[m];
-    dev::weights_body(r.hist, r.nbins, sp.dbeta, r.st, r.wtab, s_d, s_l);
+    dev::weights_body(r.hist, r.nbins, sp.dbeta, sp.wtab, r.st, s_acc, s_l);
 }
 
 __global__ void __launch_bounds__(kB) k_batch_counts(const BatchArgs b)
@@ -67,9 +67,10 @@ __global__ void __launch_bounds__(kB) k_batch_counts(const BatchArgs b)
     __shared__ int s_i[32];
     const int m = run_of_chunk(b.runs, b.M, blockIdx.x);
     const int i = *b.step_counter;
-    if (!b.steps[(size_t)i * b.M + m].active) return;
+    const StepDev &sp = b.steps[(size_t)i * b.M + m];
+    if (!sp.active) return;
     const RunDev &r = b.runs[m];
-    dev::counts_body(blockIdx.x - r.chunk0, r.E, r.nbins - 1, r.R0, r.mode, i, r.stream_hi, b.k0, b.k1, r.wtab,
+    dev::counts_body(blockIdx.x - r.chunk0, r.E, r.nbins - 1, r.R0, r.mode, i, r.stream_hi, b.k0, b.k1, sp.wtab,
                      r.counts, r.local_off, r.blocksum, r.st, s_i);
 }
 
@@ -373,7 +374,7 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
             (s = balloc(b, &r.E, r.R_cap)) || (s = balloc(b, &r.Mt, r.R_cap)) || (s = balloc(b, &r.hist, r.nbins)) ||
             (s = balloc(b, &r.counts, r.R_cap)) || (s = balloc(b, &r.local_off, r.R_cap)) ||
             (s = balloc(b, &r.blocksum, nc)) || (s = balloc(b, &r.parent, r.R_cap)) ||
-            (s = balloc(b, &r.wtab, r.nbins)) || (s = balloc(b, &r.acc, 3)) || (s = balloc(b, &r.st, 1)) ||
+            (s = balloc(b, &r.acc, 3)) || (s = balloc(b, &r.st, 1)) ||
             (s = balloc(b, &r.obs, (size_t)d.K + 1)))
             return fail(s);
         if (g.track_families) {
@@ -383,6 +384,30 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
         }
     }
     b->n_parts = (int)b->has_part[0] + (int)b->has_part[1];
+    // weight tables: one per run and distinct dbeta of its schedule (a
+    // constant schedule has a handful), all in one device array
+    std::vector<std::map<uint64_t, size_t>> wt_at(M);
+    size_t wt_total = 0;
+    for (int m = 0; m < M; ++m) {
+        for (int i = 1; i <= b->K[m]; ++i) {
+            const double dbeta = runs[m].betas[i] - runs[m].betas[i - 1];
+            uint64_t key;
+            std::memcpy(&key, &dbeta, sizeof(key));
+            if (wt_at[m].emplace(key, wt_total).second) wt_total += (size_t)b->runs_h[m].nbins;
+        }
+    }
+    std::vector<double> wt_host(wt_total);
+    for (int m = 0; m < M; ++m) {
+        for (const auto &kv : wt_at[m]) {
+            double dbeta;
+            std::memcpy(&dbeta, &kv.first, sizeof(dbeta));
+            pa::weight_table(dbeta, b->runs_h[m].nbins, wt_host.data() + kv.second);
+        }
+    }
+    double *wt_dev = nullptr;
+    if ((s = balloc(b, &wt_dev, wt_total))) return fail(s);
+    e = cudaMemcpy(wt_dev, wt_host.data(), sizeof(double) * wt_total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(bfail(e));
     // per-step parameters (step 0 = the initial measurement)
     std::vector<pa::StepDev> steps((size_t)(b->Kmax + 1) * M);
     for (int i = 0; i <= b->Kmax; ++i) {
@@ -394,6 +419,11 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
             const double beta = runs[m].betas[i];
             sp.beta = beta;
             sp.dbeta = i > 0 ? beta - runs[m].betas[i - 1] : 0.0;
+            if (i > 0) {
+                uint64_t key;
+                std::memcpy(&key, &sp.dbeta, sizeof(key));
+                sp.wtab = wt_dev + wt_at[m].at(key);
+            }
             sp.theta = i > 0 ? b->theta[m] : 0;
             sp.thr = pa::acceptance_thresholds(beta);
         }

@@ -19,7 +19,6 @@ struct RunDev {
     uint32_t *buf[2];
     int32_t *anc[2];
     int32_t *parent, *E, *Mt, *hist, *fam, *counts, *local_off, *blocksum;
-    double *wtab;
     unsigned long long *acc;
     DevState *st;
     DevObs *obs;  // K + 1 records
@@ -31,6 +30,7 @@ struct RunDev {
 struct StepDev {  // one per (step, run)
     Thresholds thr;
     double beta, dbeta;
+    const double *wtab;  // weight table of dbeta (pa::weight_table), 2N + 1 entries
     int32_t theta, active;
 };
 

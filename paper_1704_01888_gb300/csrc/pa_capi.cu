@@ -46,6 +46,14 @@ Thresholds acceptance_thresholds(double beta)
     return th;
 }
 
+void weight_table(double dbeta, int n, double *out)
+{
+    for (int t = 0; t < n; ++t) {
+        const double d = dbeta >= 0.0 ? (double)t : -(double)t;
+        out[t] = std::exp(-dbeta * d);
+    }
+}
+
 }  // namespace pa
 
 namespace {
@@ -77,7 +85,17 @@ struct pa_ctx {
     int32_t *anc[2] = {nullptr, nullptr};
     int32_t *E = nullptr, *Mt = nullptr, *hist = nullptr, *fam = nullptr;
     int32_t *counts = nullptr, *local_off = nullptr, *blocksum = nullptr, *parent = nullptr;
-    double *wtab = nullptr;
+    // Weight tables of the resampling steps (pa::weight_table), one per
+    // distinct dbeta, most recently used last; a constant schedule has a
+    // handful of distinct steps, so tables are computed once and reused.
+    struct WTable {
+        uint64_t key;  // bit pattern of dbeta
+        double *dev;
+        double *host;  // pinned source of the upload, kept with the table
+    };
+    std::vector<WTable> wtabs;
+    bool wtab_hold = false;  // no eviction while a schedule's tables are in use
+    bool resampled = false;  // parent holds the map of a resample
     unsigned long long *acc = nullptr;
     pa::DevState *st = nullptr;
     pa::DevObs *obs = nullptr;
@@ -140,12 +158,63 @@ pa_status profile_mark(pa_ctx *c, int k, bool first)
     return PA_OK;
 }
 
+void release_wtables(pa_ctx *c, size_t keep)
+{
+    while (c->wtabs.size() > keep) {
+        pa_ctx::WTable &t = c->wtabs.front();
+        if (t.dev) cudaFree(t.dev);
+        if (t.host) cudaFreeHost(t.host);
+        c->wtabs.erase(c->wtabs.begin());
+    }
+}
+
+constexpr size_t kWTableCache = 64;
+
+// The device weight table of dbeta: from the cache, or computed on the host
+// and uploaded on the context's stream.
+pa_status get_wtable(pa_ctx *c, double dbeta, const double **out)
+{
+    uint64_t key;
+    std::memcpy(&key, &dbeta, sizeof(key));
+    for (size_t i = 0; i < c->wtabs.size(); ++i) {
+        if (c->wtabs[i].key == key) {
+            pa_ctx::WTable t = c->wtabs[i];
+            c->wtabs.erase(c->wtabs.begin() + (long)i);
+            c->wtabs.push_back(t);
+            *out = t.dev;
+            return PA_OK;
+        }
+    }
+    if (!c->wtab_hold && c->wtabs.size() >= kWTableCache) {
+        // the least recently used table may still have readers in the stream
+        PA_CK(cudaStreamSynchronize(c->stream));
+        release_wtables(c, kWTableCache - 1);
+    }
+    pa_ctx::WTable t{key, nullptr, nullptr};
+    const size_t bytes = sizeof(double) * (size_t)c->nbins;
+    cudaError_t e = cudaMalloc((void **)&t.dev, bytes);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&t.host, bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) {
+        pa::weight_table(dbeta, c->nbins, t.host);
+        e = cudaMemcpyAsync(t.dev, t.host, bytes, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e != cudaSuccess) {
+        if (t.dev) cudaFree(t.dev);
+        if (t.host) cudaFreeHost(t.host);
+        return cuda_fail(e);
+    }
+    c->wtabs.push_back(t);
+    *out = t.dev;
+    return PA_OK;
+}
+
 void release(pa_ctx *c)
 {
     release_events(c);
+    release_wtables(c, 0);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     void *ptrs[] = {c->spins[0], c->spins[1], c->anc[0], c->anc[1], c->E, c->Mt, c->hist, c->fam,
-                    c->counts, c->local_off, c->blocksum, c->parent, c->wtab, c->acc, c->st, c->obs,
+                    c->counts, c->local_off, c->blocksum, c->parent, c->acc, c->st, c->obs,
                     c->stage, c->aux};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -262,13 +331,16 @@ pa_status enqueue_sweep(pa_ctx *c, double beta, int theta, int step)
 
 pa_status enqueue_resample(pa_ctx *c, double dbeta, int step)
 {
-    pa_status s = profile_mark(c, 1, true);
+    const double *wtab = nullptr;
+    pa_status s = get_wtable(c, dbeta, &wtab);
     if (s) return s;
+    if ((s = profile_mark(c, 1, true))) return s;
     PA_CK(pa::launch_resample(c->hist, c->nbins, c->E, dbeta, c->cfg.R, c->R_cap, c->cfg.resample_mode, step,
-                              (uint32_t)c->cfg.stream << 24, c->k0, c->k1, c->wtab, c->counts, c->local_off, c->blocksum, c->parent,
-                              c->hist, c->st, c->stream));
+                              (uint32_t)c->cfg.stream << 24, c->k0, c->k1, wtab, c->counts, c->local_off,
+                              c->blocksum, c->parent, c->hist, c->st, c->stream));
     if ((s = profile_mark(c, 1, false))) return s;
     c->pending_step = step;
+    c->resampled = true;
     return PA_OK;
 }
 
@@ -356,8 +428,7 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
         (s = dev_alloc(&c->E, c->R_cap)) || (s = dev_alloc(&c->Mt, c->R_cap)) ||
         (s = dev_alloc(&c->hist, c->nbins)) || (s = dev_alloc(&c->counts, c->R_cap)) ||
         (s = dev_alloc(&c->local_off, c->R_cap)) || (s = dev_alloc(&c->blocksum, nb)) ||
-        (s = dev_alloc(&c->parent, c->R_cap)) || (s = dev_alloc(&c->wtab, c->nbins)) ||
-        (s = dev_alloc(&c->acc, 3)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
+        (s = dev_alloc(&c->parent, c->R_cap)) || (s = dev_alloc(&c->acc, 3)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
         return fail(s);
     if (g.track_families) {
         if ((s = dev_alloc(&c->anc[0], c->R_cap)) || (s = dev_alloc(&c->anc[1], c->R_cap)) ||
@@ -577,6 +648,7 @@ pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, in
     if (!c) return PA_ERR_INVALID;
     if (c->failed || c->pending_step != 0 || step <= c->step) return PA_ERR_STATE;
     if (!std::isfinite(dbeta) || !(c->beta + dbeta >= 0.0)) return PA_ERR_INVALID;
+    const bool had_parents = c->resampled;
     pa_status s = enqueue_resample(c, dbeta, step);
     if (s) return s;
     if (lnQ_out || R_out) {
@@ -590,6 +662,7 @@ pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, in
             PA_CK(cudaStreamSynchronize(c->stream));
             c->failed = false;
             c->pending_step = 0;
+            c->resampled = had_parents;  // the scatter stopped before writing parents
             return PA_ERR_CAPACITY;
         }
         if (s) return s;
@@ -717,6 +790,20 @@ pa_status pa_get_ancestors(pa_ctx *c, int32_t *host)
     return PA_OK;
 }
 
+pa_status pa_get_parents(pa_ctx *c, int32_t *out, int32_t on_device)
+{
+    if (!c || !out) return PA_ERR_INVALID;
+    if (!c->resampled) return PA_ERR_STATE;
+    pa::DevState h;
+    pa_status s = sync_state(c, &h);
+    if (s) return s;
+    const int n = c->pending_step != 0 ? h.pop_next : h.pop;
+    PA_CK(cudaMemcpyAsync(out, c->parent, sizeof(int32_t) * (size_t)n,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) PA_CK(cudaStreamSynchronize(c->stream));
+    return PA_OK;
+}
+
 pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_obs *obs_out,
                  const int32_t *hist_steps, int32_t n_hist, int32_t *hist_out, int32_t use_graph)
 {
@@ -747,6 +834,18 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
     }
     const long long first_obs = c->n_obs;
     const int step0 = c->step;
+    // every weight table of the schedule before any capture begins; none is
+    // evicted until the run has finished
+    c->wtab_hold = true;
+    for (int i = 1; i <= K; ++i) {
+        const double *w = nullptr;
+        pa_status s = get_wtable(c, betas[i] - betas[i - 1], &w);
+        if (s) {
+            c->wtab_hold = false;
+            if (hstore) cudaFree(hstore);
+            return s;
+        }
+    }
 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -762,6 +861,7 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
         if (e == cudaSuccess) e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             c->profiling = was_profiling;
+            c->wtab_hold = false;
             if (hstore) cudaFree(hstore);
             return cuda_fail(e);
         }
@@ -789,6 +889,9 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
     if (s == PA_OK) s = sync_state(c, nullptr);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    cudaStreamSynchronize(c->stream);
+    c->wtab_hold = false;
+    if (c->wtabs.size() > kWTableCache) release_wtables(c, kWTableCache);
     if (s == PA_OK && obs_out) {
         for (int i = 0; i < K; ++i) {
             const pa::DevObs *slot = c->obs + ((first_obs + i) % c->obs_cap);

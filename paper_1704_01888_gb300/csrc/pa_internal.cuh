@@ -75,7 +75,7 @@ struct DevState {
     int32_t err;       // 0, or a pa_status code set by a kernel
     int32_t parity;    // spin / ancestor buffer holding the current population
     int32_t E_ref;     // reference energy of the pending resample
-    int32_t pad0;
+    int32_t ties;      // copy numbers of the pending resample flagged as near ties
     double S;          // sum of shifted Boltzmann factors of the pending resample
     double lnQ;        // ln Q of the pending resample
     double lnZ;        // running ln Z (Eq. 2)
@@ -84,7 +84,7 @@ struct DevState {
 // Per-step estimators; field order matches pa_obs in include/pa.h.
 struct DevObs {
     double beta, lnQ, lnZ, meanE, meanE2, C, meanM, S_f;
-    int64_t R, n_families, sumE, sumE2, sumMt;
+    int64_t R, n_families, sumE, sumE2, sumMt, n_near_ties;
 };
 
 struct SweepArgs {
@@ -114,10 +114,11 @@ int sweep_max_blocks_per_sm(int q, int L, int rpb, int threads);
 // Launchers (pa_resample.cu)
 cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
                         uint32_t stream_hi, int ground, cudaStream_t s);
+// wtab: the weight table of dbeta (weight_table below), 2N + 1 entries.
 cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, double dbeta, int R_target,
-                            int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1, double *wtab,
-                            int32_t *counts, int32_t *local_off, int32_t *blocksum, int32_t *parent,
-                            int32_t *hist_zero, DevState *st, cudaStream_t s);
+                            int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1,
+                            const double *wtab, int32_t *counts, int32_t *local_off, int32_t *blocksum,
+                            int32_t *parent, int32_t *hist_zero, DevState *st, cudaStream_t s);
 cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,
                             double beta, int q, int N, int gathered, int resampled, cudaStream_t s);
 cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count,
@@ -125,6 +126,13 @@ cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int 
 
 // Host: the thresholds of inverse temperature beta.
 Thresholds acceptance_thresholds(double beta);
+
+// Host: the Boltzmann factors of a resampling step dbeta by energy distance
+// t = |E - E_ref| from the reference energy, t = 0..n-1:
+// out[t] = exp(-dbeta d) with d = t (dbeta >= 0, E_ref the lowest energy) or
+// d = -t (dbeta < 0, E_ref the highest), using the C library's exp, so the
+// factors do not depend on the device.
+void weight_table(double dbeta, int n, double *out);
 
 // Launchers (pa_reweight.cu)
 cudaError_t launch_newton(const int32_t *hist, int nbins, const DevState *st, double target, double cap, int iters,

@@ -847,9 +847,78 @@ __device__ __forceinline__ uint8_t canonical_state(const uint32_t *spins, int q,
 // Resampling bodies (Sec. 2 step 2, Eq. 2)
 // ===========================================================================
 
-// One block: reference bin, weight table, S and ln Q of the pending resample.
-__device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, double dbeta, DevState *st, double *wtab,
-                                             double *s_d, long long *s_l)
+// Exact sum of the weights.  S = sum_k h_k w_k over the occupied energy bins
+// (h_k < 2^24 replicas, w_k a double in [0, 1]) is accumulated exactly and
+// rounded once to the nearest double, ties to even, so that S -- and with it
+// every rho_j -- does not depend on which lane, warp or block adds which term.
+// The accumulator counts units of 2^-1074 (the smallest positive double): a
+// term h m 2^(pos - 1074) (m the 53-bit significand) is the integer h m < 2^77
+// placed at bit pos <= 1022.  Limb i of the shared array collects bits
+// 32 i .. 32 i + 31 in a 64-bit counter, so the carries of up to 2^32
+// additions fit and are propagated once, at the end.  The sum is below
+// R_cap < 2^24, i.e. below bit 1098: 36 limbs.
+constexpr int kSumLimbs = 36;
+
+__device__ __forceinline__ void exact_add(unsigned long long *acc, uint32_t h, double w)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
+    const int ef = (int)(bits >> 52) & 0x7FF;
+    if (bits == 0ull) return;
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
+    const int pos = ef ? ef - 1 : 0;
+    const unsigned long long lo = m * (unsigned long long)h;
+    const unsigned long long hi = __umul64hi(m, (unsigned long long)h);
+    const int li = pos >> 5, sh = pos & 31;
+    const unsigned long long lo_s = lo << sh;
+    const unsigned long long hi_s = (hi << sh) | (sh ? lo >> (64 - sh) : 0ull);
+    const uint32_t c[4] = {(uint32_t)lo_s, (uint32_t)(lo_s >> 32), (uint32_t)hi_s, (uint32_t)(hi_s >> 32)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (c[k]) atomicAdd(acc + li + k, (unsigned long long)c[k]);
+}
+
+// Bits lowpos .. lowpos + 63 of normalised 32-bit limbs (lowpos >= 0).
+__device__ __forceinline__ unsigned long long limb_bits64(const unsigned long long *acc, int lowpos)
+{
+    const int li = lowpos >> 5, sh = lowpos & 31;
+    auto limb = [&](int i) -> unsigned long long { return i < kSumLimbs ? acc[i] : 0ull; };
+    const unsigned long long lo64 = limb(li) | (limb(li + 1) << 32);
+    return sh ? (lo64 >> sh) | (limb(li + 2) << (64 - sh)) : lo64;
+}
+
+// Propagates the carries and rounds the accumulated value to the nearest
+// double (one thread; the value must be at least 1, i.e. bit 1074 or above).
+__device__ __forceinline__ double exact_round(unsigned long long *acc)
+{
+    unsigned long long carry = 0ull;
+    for (int i = 0; i < kSumLimbs; ++i) {
+        const unsigned long long v = acc[i] + carry;
+        acc[i] = v & 0xFFFFFFFFull;
+        carry = v >> 32;
+    }
+    int t = kSumLimbs - 1;
+    while (t > 0 && acc[t] == 0ull) --t;
+    int p = 32 * t + 31 - __clz((uint32_t)acc[t]);  // top bit
+    const unsigned long long x = limb_bits64(acc, p - 63);  // bit 63 = top bit
+    unsigned long long mant = x >> 11;
+    const bool round = (x >> 10) & 1ull;
+    bool sticky = (x & 0x3FFull) != 0ull;
+    const int low = p - 63;  // bits below it
+    for (int i = 0; i < (low >> 5) && !sticky; ++i) sticky = acc[i] != 0ull;
+    if (!sticky && (low & 31)) sticky = (acc[low >> 5] & ((1ull << (low & 31)) - 1ull)) != 0ull;
+    if (round && (sticky || (mant & 1ull))) mant += 1ull;
+    if (mant >> 53) {
+        mant >>= 1;
+        p += 1;
+    }
+    // value = mant 2^(p - 52 - 1074): biased exponent p - 1074 + 1023
+    return __longlong_as_double((long long)(((unsigned long long)(p - 51) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// One block: reference bin, S (exact sum of h_k w_k, weights from the host
+// table wtab by distance |k - k_ref|) and ln Q of the pending resample.
+__device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, double dbeta, const double *wtab,
+                                             DevState *st, unsigned long long *s_acc, long long *s_l)
 {
     if (st->err) return;
     const int tid = threadIdx.x;
@@ -865,6 +934,7 @@ __device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, dou
     }
     const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0) s_l[warp] = best;
+    for (int i = tid; i < kSumLimbs; i += blockDim.x) s_acc[i] = 0ull;
     __syncthreads();
     if (warp == 0) {
         long long v = (lane < (int)(blockDim.x >> 5)) ? s_l[lane] : (dbeta >= 0.0 ? (long long)INT_MAX : -1);
@@ -877,33 +947,31 @@ __device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, dou
     }
     __syncthreads();
     const int kref = (int)s_l[0];
-
-    // only occupied bins: an empty bin on the far side of E_ref could hold an
-    // overflowing factor, and 0 * inf would poison the sum
-    double part = 0.0;
     for (int k = tid; k < nbins; k += blockDim.x) {
         const int h = hist[k];
-        if (h == 0) continue;
-        const double w = exp(__dmul_rn(-dbeta, (double)(k - kref)));
-        wtab[k] = w;
-        part = __dadd_rn(part, __dmul_rn((double)h, w));
+        if (h > 0) exact_add(s_acc, (uint32_t)h, wtab[k >= kref ? k - kref : kref - k]);
     }
-    const double S = block_sum_fixed(part, s_d);
+    __syncthreads();
     if (tid == 0) {
+        const double S = exact_round(s_acc);
         const int E_ref = kref - (nbins - 1);
         st->S = S;
         st->E_ref = E_ref;
+        st->ties = 0;
         st->lnQ = __dadd_rn(__dmul_rn(-dbeta, (double)E_ref), log(S / (double)st->pop));
     }
+    __syncthreads();
 }
 
 // A Poisson draw with mean rho for replica j (Sec. 2, Eq. 1): inversion of
 // the cumulative distribution with the mean split into pieces of at most 64;
 // the k-th uniform (U_k + 1/2) / 2^32 is word k & 3 of counter
 // (j, RESAMPLE | (1 + k / 4), step, stream).
-__device__ __forceinline__ int poisson_draw(double rho, int j, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1)
+__device__ __forceinline__ int poisson_draw(double rho, int j, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1,
+                                            bool &tie)
 {
     int r = 0;
+    tie = false;
     double remaining = rho;
     uint32_t k = 0;
     uint4 w = make_uint4(0u, 0u, 0u, 0u);
@@ -917,7 +985,9 @@ __device__ __forceinline__ int poisson_draw(double rho, int j, int step, uint32_
         double p = exp(-mu);
         double F = p;
         int n = 0;
-        while (u > F && n < 1000) {
+        for (;;) {
+            if (fabs(__dsub_rn(u, F)) < 0x1p-40) tie = true;
+            if (!(u > F && n < 1000)) break;
             n += 1;
             p = __ddiv_rn(__dmul_rn(p, mu), (double)n);
             F = __dadd_rn(F, p);
@@ -927,7 +997,16 @@ __device__ __forceinline__ int poisson_draw(double rho, int j, int step, uint32_
     return r;
 }
 
+// Near-tie flag of a rounded copy number: frac(rho) within 2^-48 max(1, rho)
+// of the rule's boundary (u / 2^32 for nearest-integer copy numbers, 1/2 for
+// ROUND), where a last-place change of rho could change the outcome.
+__device__ __forceinline__ bool round_tie(double rho, double frac, double boundary)
+{
+    return fabs(__dsub_rn(frac, boundary)) < __dmul_rn(0x1p-48, fmax(1.0, rho));
+}
+
 // One block of 1024 old replicas (chunk): copy numbers and their block scan.
+// w(E_j) comes from the host table wtab by distance |E_j - E_ref|.
 __device__ __forceinline__ void counts_body(int chunk, const int32_t *E, int twoN, int R_target, int mode, int step,
                                             uint32_t stream_hi, uint32_t k0, uint32_t k1, const double *wtab,
                                             int32_t *counts, int32_t *local_off, int32_t *blocksum, DevState *st,
@@ -938,27 +1017,30 @@ __device__ __forceinline__ void counts_body(int chunk, const int32_t *E, int two
     if (chunk * (int)blockDim.x >= R_prev) return;
     const int j = chunk * blockDim.x + threadIdx.x;
     int r = 0;
+    bool tie = false;
     if (j < R_prev) {
-        const double w = wtab[E[j] + twoN];
+        const int d = E[j] - st->E_ref;
+        const double w = wtab[d >= 0 ? d : -d];
         const double rho = __ddiv_rn(__dmul_rn((double)R_target, w), st->S);
         const double n = floor(rho);
         const double frac = __dsub_rn(rho, n);
         if (mode == 2) {
-            r = poisson_draw(rho, j, step, stream_hi, k0, k1);
+            r = poisson_draw(rho, j, step, stream_hi, k0, k1, tie);
         } else if (mode == 3) {
             r = 1;
+        } else if (mode == 1) {
+            r = (int)n + (frac >= 0.5);
+            tie = round_tie(rho, frac, 0.5);
         } else {
-            int up;
-            if (mode == 1) {
-                up = frac >= 0.5;
-            } else {
-                const uint4 u = philox10(make_uint4((uint32_t)j >> 2, DOM_RESAMPLE, (uint32_t)step, stream_hi), k0, k1);
-                up = (double)pick_word(u, j & 3) < __dmul_rn(frac, 4294967296.0);
-            }
-            r = (int)n + up;
+            const uint4 u = philox10(make_uint4((uint32_t)j >> 2, DOM_RESAMPLE, (uint32_t)step, stream_hi), k0, k1);
+            const uint32_t uj = pick_word(u, j & 3);
+            r = (int)n + ((double)uj < __dmul_rn(frac, 4294967296.0));
+            tie = round_tie(rho, frac, __dmul_rn((double)uj, 0x1p-32));
         }
         counts[j] = r;
     }
+    const unsigned nt = __popc(__ballot_sync(0xFFFFFFFFu, tie));
+    if ((threadIdx.x & 31) == 0 && nt) atomicAdd(&st->ties, (int)nt);
     int total;
     const int before = block_exclusive_scan(r, s_i, &total);
     if (j < R_prev) local_off[j] = before;
@@ -1048,6 +1130,7 @@ __device__ __forceinline__ void finalize_body(DevState *st, unsigned long long *
         o.S_f = fam ? Sf : 0.0;
         o.R = R;
         o.n_families = fam ? nf : 0;
+        o.n_near_ties = resampled ? st->ties : 0;
         o.sumE = sE;
         o.sumE2 = sE2;
         o.sumMt = sM;

@@ -5,9 +5,11 @@
 //   k_init      Sec. 2 step 1 (uniform spins at beta_0 = 0) or Sec. 5 Eq. 6
 //               (a uniformly chosen ground state per replica), written in the
 //               multi-spin-coded layout.
-//   k_weights   Sec. 2 step 2: reference energy, Boltzmann factors
-//               w_k = exp(-dbeta (E_k - E_ref)) per energy bin, their
-//               histogram-weighted sum S and ln Q_i = -dbeta E_ref + ln(S/R_{i-1}).
+//   k_weights   Sec. 2 step 2: reference energy, the histogram-weighted sum
+//               S of the Boltzmann factors w = exp(-dbeta (E - E_ref)) (taken
+//               from a table the host computes with the C library's exp;
+//               summed exactly and rounded once) and
+//               ln Q_i = -dbeta E_ref + ln(S/R_{i-1}).
 //   k_counts    copy numbers r_j from rho_j = R w(E_j) / S and their
 //               block-local exclusive scan (warp shuffles).
 //   k_scatter   block offsets, the new population size R_i (checked against
@@ -36,12 +38,12 @@ __global__ void k_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint3
         dev::init_item(spins, anc, q, L, i, k0, k1, stream_hi, ground);
 }
 
-__global__ void __launch_bounds__(kBlock) k_weights(const int32_t *hist, int nbins, double dbeta, DevState *st,
-                                                    double *wtab)
+__global__ void __launch_bounds__(kBlock) k_weights(const int32_t *hist, int nbins, double dbeta, const double *wtab,
+                                                    DevState *st)
 {
-    __shared__ double s_d[32];
+    __shared__ unsigned long long s_acc[dev::kSumLimbs];
     __shared__ long long s_l[32];
-    dev::weights_body(hist, nbins, dbeta, st, wtab, s_d, s_l);
+    dev::weights_body(hist, nbins, dbeta, wtab, st, s_acc, s_l);
 }
 
 __global__ void __launch_bounds__(kBlock) k_counts(const int32_t *E, int twoN, int R_target, int mode, int step,
@@ -70,14 +72,15 @@ constexpr int kSmallResample = 4 * kBlock;
 
 __global__ void __launch_bounds__(kBlock) k_resample_small(const int32_t *hist, int nbins, const int32_t *E,
                                                            double dbeta, int R_target, int R_cap, int mode, int step,
-                                                           uint32_t stream_hi, uint32_t k0, uint32_t k1, double *wtab,
-                                                           int32_t *counts, int32_t *local_off, int32_t *blocksum,
-                                                           int32_t *parent, int32_t *hist_zero, DevState *st)
+                                                           uint32_t stream_hi, uint32_t k0, uint32_t k1,
+                                                           const double *wtab, int32_t *counts, int32_t *local_off,
+                                                           int32_t *blocksum, int32_t *parent, int32_t *hist_zero,
+                                                           DevState *st)
 {
-    __shared__ double s_d[32];
+    __shared__ unsigned long long s_acc[dev::kSumLimbs];
     __shared__ long long s_l[32];
     __shared__ int s_i[32];
-    dev::weights_body(hist, nbins, dbeta, st, wtab, s_d, s_l);
+    dev::weights_body(hist, nbins, dbeta, wtab, st, s_acc, s_l);
     __syncthreads();
     const int nb = (R_cap + kBlock - 1) / kBlock;
     for (int chunk = 0; chunk < nb; ++chunk) {
@@ -129,9 +132,9 @@ cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint
 }
 
 cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, double dbeta, int R_target,
-                            int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1, double *wtab,
-                            int32_t *counts, int32_t *local_off, int32_t *blocksum, int32_t *parent,
-                            int32_t *hist_zero, DevState *st, cudaStream_t s)
+                            int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1,
+                            const double *wtab, int32_t *counts, int32_t *local_off, int32_t *blocksum,
+                            int32_t *parent, int32_t *hist_zero, DevState *st, cudaStream_t s)
 {
     if (R_cap <= kSmallResample) {
         k_resample_small<<<1, kBlock, 0, s>>>(hist, nbins, E, dbeta, R_target, R_cap, mode, step, stream_hi, k0, k1,
@@ -140,7 +143,7 @@ cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, do
         return cudaGetLastError();
     }
     const int nb = (R_cap + kBlock - 1) / kBlock;
-    k_weights<<<1, kBlock, 0, s>>>(hist, nbins, dbeta, st, wtab);
+    k_weights<<<1, kBlock, 0, s>>>(hist, nbins, dbeta, wtab, st);
     k_counts<<<nb, kBlock, 0, s>>>(E, nbins - 1, R_target, mode, step, stream_hi, k0, k1, wtab, counts, local_off,
                                    blocksum, st);
     const int nb2 = nb > (nbins + kBlock - 1) / kBlock ? nb : (nbins + kBlock - 1) / kBlock;

@@ -1,9 +1,9 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
 the same seeded inputs.
 
-Bar: spins, energies, largest-state occupations, histograms, population sizes
-and family ids bit-exact; <E>, <E^2>, C and <M> bit-exact (they come from
-exact integer sums through the same IEEE operations); ln Q and ln Z within
+Bar: spins, energies, largest-state occupations, histograms, population sizes,
+near-tie counts and family ids bit-exact; <E>, <E^2>, C and <M> bit-exact
+(they come from exact integer sums through the same IEEE operations); ln Q and ln Z within
 1e-10 relative (the device evaluates exp/log with CUDA's libm, the oracle
 with the C library's); family entropy within 1e-12 relative.
 """
@@ -75,6 +75,7 @@ def _compare(g, o, fam=False, check_hists=True):
         assert go["lnZ"] == pytest.approx(o["lnZ"][i], rel=LNZ_RTOL, abs=1e-12), ("lnZ", i)
         if i > 0:
             assert go["lnQ"] == pytest.approx(o["lnQ"][i], rel=LNZ_RTOL, abs=1e-12), ("lnQ", i)
+        assert go["n_near_ties"] == o["n_near_ties"][i], ("n_near_ties", i)
         if fam:
             assert go["n_families"] == o["n_families"][i], ("n_families", i)
             assert go["S_f"] == pytest.approx(o["S_f"][i], rel=SF_RTOL, abs=1e-14), ("S_f", i)
