@@ -394,6 +394,90 @@ pa_status pa_profile(pa_ctx *ctx, int32_t enable);
  * resampling kernels.  Any pointer may be NULL. */
 pa_status pa_profile_read(pa_ctx *ctx, double *ms_out2, int64_t *launches_out2);
 
+/* ---- One population spread over several GPUs (Sec. 2: the replicas are
+ * independent between resampling steps; a step couples them only through
+ * the normaliser Q_i and the copy-number offsets) ------------------------
+ * Rank g of `world` holds a contiguous range of global slots, about R/world
+ * replicas.  Random numbers are keyed by global slot and global replica
+ * index, and S is an exact sum of the histogram-weighted Boltzmann factors, so
+ * any number of ranks gives the population, energies, estimators and ln Z of
+ * one GPU (pa_init) bit for bit.  The caller moves data between the calls
+ * (the library calls no collective):
+ *   pa_shard_init                                  (each rank)
+ *   sum hist, sums, fam over ranks; pa_shard_finalize(beta_0)
+ *   for each step i:
+ *     pa_shard_counts(dbeta_i, i, &T)              (needs the summed hist)
+ *     gather T of every rank into totals[world]
+ *     pa_shard_pack(totals, send_counts, recv_counts)
+ *     exchange: send[sum of send_counts before d ..][send_counts[d] replicas]
+ *       to rank d; receive recv_counts[g] replicas from rank g into recv,
+ *       sources in rank order (replica_words 32-bit words per replica, and
+ *       send_anc -> recv_anc with families)
+ *     pa_shard_accept; pa_sweep(beta_i, theta, i)
+ *     sum hist, sums, fam over ranks; pa_shard_finalize(beta_i)
+ * Device buffers the caller reads or writes (owned by the context; recv and
+ * recv_anc change with every step: query them after pa_shard_pack). */
+typedef struct {
+    int32_t *hist;          /* [n_bins] energy histogram (this rank's, to be summed in place) */
+    int64_t *sums;          /* [4] sum E, sum E^2, sum Mt, near ties (this rank's, to be summed in place) */
+    int32_t *fam;           /* [R] family counts (this rank's, to be summed); NULL without families */
+    uint32_t *send;         /* [capacity x replica_words] children packed by pa_shard_pack */
+    int32_t *send_anc;      /* [capacity] their family ids; NULL without families */
+    uint32_t *recv;         /* [capacity x replica_words] where this rank's new replicas arrive */
+    int32_t *recv_anc;      /* [capacity]; NULL without families */
+    int64_t replica_words;  /* 32-bit words per replica in the device layout */
+    int64_t capacity;       /* replicas this rank can hold */
+    int64_t n_bins;         /* 2N + 1 */
+} pa_shard_buffers;
+
+/* The exchange plan of one step (host only; no GPU needed): totals[g] = the
+ * number of children rank g's replicas have after resampling.  The new
+ * population has R_new = sum totals replicas; rank g's children are the new
+ * global slots [O_g, O_g + totals[g]), O_g = sum_{h<g} totals[h], and rank d
+ * holds the new slots [floor(d R_new / world), floor((d+1) R_new / world)).
+ * Writes R_new, this rank's new range [lo, hi), send_counts[d] (replicas it
+ * sends to rank d) and recv_counts[g] (replicas it receives from rank g); any
+ * output pointer may be NULL.  PA_ERR_INVALID for a bad rank or world or a
+ * negative total, PA_ERR_CAPACITY for R_new outside 1 .. 2^24 - 1. */
+pa_status pa_shard_plan(const int64_t *totals, int32_t world, int32_t rank, int64_t *R_new, int64_t *lo, int64_t *hi,
+                        int64_t *send_counts, int64_t *recv_counts);
+
+/* Rank `rank` of `world` (2..1024) of the population cfg describes (cfg->R
+ * and cfg->R_cap are the whole population's): initial replicas of the global
+ * slots [floor(rank R / world), floor((rank+1) R / world)) with their
+ * measurements (synchronises).  Errors as pa_init. */
+pa_status pa_shard_init(const pa_config *cfg, int32_t rank, int32_t world, void *cuda_stream, pa_ctx **out);
+
+/* The device buffers of the exchange (see above).  PA_ERR_STATE unless the
+ * context came from pa_shard_init. */
+pa_status pa_shard_get_buffers(pa_ctx *ctx, pa_shard_buffers *out);
+
+/* Resampling of this rank's replicas from the summed histogram (Sec. 2 step 2,
+ * Eq. 2; arithmetic as pa_resample): ln Q_i, copy numbers keyed by global
+ * replica index, their scan and the local parent map.  Synchronises and writes
+ * the number of this rank's children to *local_total.  PA_ERR_STATE out of
+ * order, PA_ERR_CAPACITY if the children exceed this rank's capacity (the
+ * population stays at step i-1). */
+pa_status pa_shard_counts(pa_ctx *ctx, double dbeta, int32_t step, int64_t *local_total);
+
+/* Plans the exchange (pa_shard_plan with every rank's total) and enqueues the
+ * packing of this rank's children, in new-slot order, into send / send_anc.
+ * send_counts / recv_counts: host int64[world] (may be NULL).
+ * PA_ERR_CAPACITY if the new local range exceeds the capacity. */
+pa_status pa_shard_pack(pa_ctx *ctx, const int64_t *totals, int64_t *send_counts, int64_t *recv_counts);
+
+/* After the exchange has filled recv (and recv_anc): they become this rank's
+ * population, global slots [lo, hi) of the plan; then call pa_sweep. */
+pa_status pa_shard_accept(pa_ctx *ctx);
+
+/* Estimators of the step (Sec. 2 step 4) from the summed sums, family counts
+ * and histogram; ln Z_i = ln Z_{i-1} + ln Q_i.  Read them with pa_observables. */
+pa_status pa_shard_finalize(pa_ctx *ctx, double beta);
+
+/* This rank's current global slot range [slot0, slot0 + count) and the size
+ * of the whole population (synchronises). */
+pa_status pa_shard_range(pa_ctx *ctx, int64_t *slot0, int64_t *count, int64_t *R_all);
+
 /* Resampling without any device allocation.  This call has no counterpart in
  * the paper: it exists for callers that may not allocate device memory --
  * plug-ins whose host framework owns every device allocation (a cudaMalloc

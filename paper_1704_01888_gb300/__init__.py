@@ -41,7 +41,8 @@ EXPORTED = (
     "pa_overlap", "pa_next_dbeta", "pa_run_adaptive", "pa_batch_create", "pa_batch_autotune", "pa_batch_set_launch",
     "pa_batch_get_launch", "pa_batch_run", "pa_batch_observables", "pa_batch_get_spins", "pa_batch_destroy",
     "pa_batch_population_size", "pa_save", "pa_load", "pa_occupations", "pa_batch_measurements",
-    "pa_get_parents",
+    "pa_get_parents", "pa_shard_plan", "pa_shard_init", "pa_shard_get_buffers", "pa_shard_counts", "pa_shard_pack",
+    "pa_shard_accept", "pa_shard_finalize", "pa_shard_range",
 )
 
 
@@ -61,6 +62,14 @@ class Config(ctypes.Structure):
 
 class RunDesc(ctypes.Structure):
     _fields_ = [("cfg", Config), ("betas", ctypes.c_void_p), ("K", ctypes.c_int32), ("theta", ctypes.c_int32)]
+
+
+class ShardBuffers(ctypes.Structure):
+    _fields_ = [
+        ("hist", ctypes.c_void_p), ("sums", ctypes.c_void_p), ("fam", ctypes.c_void_p), ("send", ctypes.c_void_p),
+        ("send_anc", ctypes.c_void_p), ("recv", ctypes.c_void_p), ("recv_anc", ctypes.c_void_p),
+        ("replica_words", ctypes.c_int64), ("capacity", ctypes.c_int64), ("n_bins", ctypes.c_int64),
+    ]
 
 
 class Obs(ctypes.Structure):
@@ -101,6 +110,14 @@ def load_library(path: str | None = None):
         "pa_get_spins": ([P, i64, i64, P], st),
         "pa_get_ancestors": ([P, P], st),
         "pa_get_parents": ([P, P, i32], st),
+        "pa_shard_plan": ([P, i32, i32, P, P, P, P, P], st),
+        "pa_shard_init": ([ctypes.POINTER(Config), i32, i32, P, ctypes.POINTER(P)], st),
+        "pa_shard_get_buffers": ([P, ctypes.POINTER(ShardBuffers)], st),
+        "pa_shard_counts": ([P, f64, i32, P], st),
+        "pa_shard_pack": ([P, P, P, P], st),
+        "pa_shard_accept": ([P], st),
+        "pa_shard_finalize": ([P, f64], st),
+        "pa_shard_range": ([P, P, P, P], st),
         "pa_run": ([P, P, i32, i32, P, P, i32, P, i32], st),
         "pa_destroy": ([P], None),
         "pa_status_str": ([st], ctypes.c_char_p),
@@ -171,6 +188,21 @@ def resample_noalloc(E_ptr: int, R_prev: int, L: int, dbeta: float, R_target: in
         ctypes.c_void_p(E_ptr), R_prev, L, float(dbeta), R_target, mode, step, seed, int(rng_stream),
         ctypes.c_void_p(parent_ptr), parent_cap, ctypes.c_void_p(lnQ_ptr), ctypes.c_void_p(R_ptr),
         ctypes.c_void_p(stream)), "pa_resample_noalloc")
+
+
+def shard_plan(totals, world: int, rank: int):
+    """The exchange plan of one step of a population spread over `world`
+    ranks (pa_shard_plan; host only): (R_new, lo, hi, send_counts,
+    recv_counts)."""
+    t = np.ascontiguousarray(totals, dtype=np.int64)
+    if t.size != world:
+        raise ValueError("one total per rank")
+    send = np.zeros(world, dtype=np.int64)
+    recv = np.zeros(world, dtype=np.int64)
+    R_new, lo, hi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().pa_shard_plan(_ptr(t), world, rank, ctypes.byref(R_new), ctypes.byref(lo), ctypes.byref(hi),
+                                        _ptr(send), _ptr(recv)), "pa_shard_plan")
+    return R_new.value, lo.value, hi.value, send, recv
 
 
 def kernel_launch_count() -> int:

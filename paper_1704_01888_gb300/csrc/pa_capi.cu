@@ -9,6 +9,7 @@
 // without host round trips.  The host computes only the per-beta acceptance
 // thresholds (four 32-bit integers, passed as kernel arguments), using the C
 // library's exp so that they are reproducible bit for bit on the host.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
@@ -86,15 +87,21 @@ struct pa_ctx {
     int32_t *E = nullptr, *Mt = nullptr, *hist = nullptr, *fam = nullptr;
     int32_t *counts = nullptr, *local_off = nullptr, *blocksum = nullptr, *parent = nullptr;
     // Weight tables of the resampling steps (pa::weight_table), one per
-    // distinct dbeta, most recently used last; a constant schedule has a
-    // handful of distinct steps, so tables are computed once and reused.
-    struct WTable {
-        uint64_t key;  // bit pattern of dbeta
-        double *dev;
-        double *host;  // pinned source of the upload, kept with the table
-    };
-    std::vector<WTable> wtabs;
-    bool wtab_hold = false;  // no eviction while a schedule's tables are in use
+    // distinct dbeta, in a device arena of kWTableSlots tables reused least
+    // recently used first; a constant schedule has a handful of distinct
+    // steps, so each table is computed once.  A new table is computed on the
+    // host into one of kWStage pinned staging slots and uploaded on the
+    // context's stream, which orders the upload after every earlier reader of
+    // the arena slot it overwrites.
+    double *wt_arena = nullptr;                 // device, kWTableSlots x nbins
+    double *wt_stage = nullptr;                 // pinned host, kWStage x nbins
+    std::vector<cudaEvent_t> wt_stage_done;     // upload from each staging slot done
+    std::vector<uint64_t> wt_key;               // dbeta bits held by each arena slot
+    std::vector<long long> wt_stamp;            // last use (0: empty)
+    long long wt_clock = 0;
+    int wt_next_stage = 0;
+    double *wt_run = nullptr;                   // tables of a long pa_run schedule
+    std::vector<std::pair<uint64_t, const double *>> wt_run_at;
     bool resampled = false;  // parent holds the map of a resample
     unsigned long long *acc = nullptr;
     pa::DevState *st = nullptr;
@@ -112,6 +119,21 @@ struct pa_ctx {
     bool failed = false;
 
     int rpb = 1, threads = 32, grid = 1;
+
+    // A population spread over several GPUs (pa_shard_init): this context
+    // holds the global slots [slot0, slot0 + R_i(local)) of one population of
+    // R_all replicas; the caller sums the histogram, the integer sums and the
+    // family counts over the ranks and exchanges the children between steps.
+    bool shard = false;
+    int rank = 0, world = 1;
+    int R_fill = 0;           // replicas the launch shape is sized for (R, or R / world)
+    int slot0 = 0, R_all = 0; // current population
+    int slot0_next = 0, n_next = 0, R_all_next = 0, n_pack = 0;
+    int host_parity = 0;      // buffer holding the current population (the device's parity)
+    int shard_stage = 0;      // kShard* below
+    bool shard_resampled = false;
+    uint32_t *send = nullptr;
+    int32_t *send_anc = nullptr;
     cudaStream_t capture_stream = nullptr;  // private stream for graph capture
 
     // event timing (pa_profile)
@@ -158,60 +180,94 @@ pa_status profile_mark(pa_ctx *c, int k, bool first)
     return PA_OK;
 }
 
-void release_wtables(pa_ctx *c, size_t keep)
+constexpr int kWTableSlots = 32;
+constexpr int kWStage = 4;
+
+// Device arena and pinned staging of the weight tables (at context creation).
+pa_status alloc_wtables(pa_ctx *c)
 {
-    while (c->wtabs.size() > keep) {
-        pa_ctx::WTable &t = c->wtabs.front();
-        if (t.dev) cudaFree(t.dev);
-        if (t.host) cudaFreeHost(t.host);
-        c->wtabs.erase(c->wtabs.begin());
+    const size_t n = (size_t)c->nbins;
+    pa_status s = dev_alloc(&c->wt_arena, n * kWTableSlots);
+    if (s) return s;
+    cudaError_t e = cudaHostAlloc((void **)&c->wt_stage, sizeof(double) * n * kWStage, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        c->wt_stage = nullptr;
+        return cuda_fail(e);
     }
+    c->wt_stage_done.assign(kWStage, nullptr);
+    for (cudaEvent_t &ev : c->wt_stage_done)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e);
+    c->wt_key.assign(kWTableSlots, 0);
+    c->wt_stamp.assign(kWTableSlots, 0);
+    return PA_OK;
 }
 
-constexpr size_t kWTableCache = 64;
+void release_wtables(pa_ctx *c)
+{
+    for (cudaEvent_t ev : c->wt_stage_done)
+        if (ev) cudaEventDestroy(ev);
+    c->wt_stage_done.clear();
+    if (c->wt_arena) cudaFree(c->wt_arena);
+    if (c->wt_stage) cudaFreeHost(c->wt_stage);
+    if (c->wt_run) cudaFree(c->wt_run);
+    c->wt_arena = c->wt_run = nullptr;
+    c->wt_stage = nullptr;
+}
 
-// The device weight table of dbeta: from the cache, or computed on the host
-// and uploaded on the context's stream.
+// Frees the tables of a long pa_run schedule (after its work has finished).
+void release_run_tables(pa_ctx *c)
+{
+    if (c->wt_run) cudaFree(c->wt_run);
+    c->wt_run = nullptr;
+    c->wt_run_at.clear();
+}
+
+// The device weight table of dbeta: a schedule's own tables during a long
+// pa_run, else the arena slot holding it, else a new table in the least
+// recently used slot.
 pa_status get_wtable(pa_ctx *c, double dbeta, const double **out)
 {
     uint64_t key;
     std::memcpy(&key, &dbeta, sizeof(key));
-    for (size_t i = 0; i < c->wtabs.size(); ++i) {
-        if (c->wtabs[i].key == key) {
-            pa_ctx::WTable t = c->wtabs[i];
-            c->wtabs.erase(c->wtabs.begin() + (long)i);
-            c->wtabs.push_back(t);
-            *out = t.dev;
+    for (const auto &kv : c->wt_run_at) {
+        if (kv.first == key) {
+            *out = kv.second;
             return PA_OK;
         }
     }
-    if (!c->wtab_hold && c->wtabs.size() >= kWTableCache) {
-        // the least recently used table may still have readers in the stream
-        PA_CK(cudaStreamSynchronize(c->stream));
-        release_wtables(c, kWTableCache - 1);
+    const size_t n = (size_t)c->nbins;
+    int slot = 0;
+    for (int i = 0; i < kWTableSlots; ++i) {
+        if (c->wt_stamp[i] && c->wt_key[i] == key) {
+            c->wt_stamp[i] = ++c->wt_clock;
+            *out = c->wt_arena + n * i;
+            return PA_OK;
+        }
+        if (c->wt_stamp[i] < c->wt_stamp[slot]) slot = i;
     }
-    pa_ctx::WTable t{key, nullptr, nullptr};
-    const size_t bytes = sizeof(double) * (size_t)c->nbins;
-    cudaError_t e = cudaMalloc((void **)&t.dev, bytes);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&t.host, bytes, cudaHostAllocDefault);
-    if (e == cudaSuccess) {
-        pa::weight_table(dbeta, c->nbins, t.host);
-        e = cudaMemcpyAsync(t.dev, t.host, bytes, cudaMemcpyHostToDevice, c->stream);
-    }
-    if (e != cudaSuccess) {
-        if (t.dev) cudaFree(t.dev);
-        if (t.host) cudaFreeHost(t.host);
-        return cuda_fail(e);
-    }
-    c->wtabs.push_back(t);
-    *out = t.dev;
+    const int k = c->wt_next_stage;
+    c->wt_next_stage = (k + 1) % kWStage;
+    double *host = c->wt_stage + n * k;
+    PA_CK(cudaEventSynchronize(c->wt_stage_done[k]));  // its previous upload has left
+    pa::weight_table(dbeta, c->nbins, host);
+    double *dev = c->wt_arena + n * slot;
+    PA_CK(cudaMemcpyAsync(dev, host, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    PA_CK(cudaEventRecord(c->wt_stage_done[k], c->stream));
+    c->wt_key[slot] = key;
+    c->wt_stamp[slot] = ++c->wt_clock;
+    *out = dev;
     return PA_OK;
 }
+
+// Steps of a shard's temperature step, in order.
+enum { kShardMeasured = 1, kShardReady = 2, kShardCounted = 3, kShardPacked = 4, kShardAccepted = 5 };
 
 void release(pa_ctx *c)
 {
     release_events(c);
-    release_wtables(c, 0);
+    release_wtables(c);
+    if (c->send) cudaFree(c->send);
+    if (c->send_anc) cudaFree(c->send_anc);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     void *ptrs[] = {c->spins[0], c->spins[1], c->anc[0], c->anc[1], c->E, c->Mt, c->hist, c->fam,
                     c->counts, c->local_off, c->blocksum, c->parent, c->acc, c->st, c->obs,
@@ -237,7 +293,7 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
         // 96 KB of lattices per block: two blocks of 512 threads per SM
         int rpb_mem = (int)(98304 / RB);
         if (rpb_mem < 1) rpb_mem = 1;
-        int rpb_fill = c->cfg.R / (4 * c->sms);
+        int rpb_fill = c->R_fill / (4 * c->sms);
         if (rpb_fill < 1) rpb_fill = 1;
         rpb = rpb_mem < rpb_fill ? rpb_mem : rpb_fill;
         // a group spanning several passes of 512 threads over its site words
@@ -302,6 +358,7 @@ pa::SweepArgs sweep_args(pa_ctx *c, double beta, int theta, int step, int gather
     a.rpb = c->rpb;
     a.gather = gather;
     a.stream_hi = (uint32_t)c->cfg.stream << 24;
+    a.slot0 = (uint32_t)c->slot0;
     return a;
 }
 
@@ -321,8 +378,9 @@ pa_status enqueue_sweep(pa_ctx *c, double beta, int theta, int step)
     if (s) return s;
     PA_CK(pa::launch_sweep(a, c->threads, c->grid, c->stream));
     if ((s = profile_mark(c, 0, false))) return s;
-    PA_CK(pa::launch_finalize(c->st, c->acc, a.fam, c->cfg.R, next_obs_slot(c), beta, c->cfg.q, c->N,
-                              gather, gather, c->stream));
+    if (!c->shard)
+        PA_CK(pa::launch_finalize(c->st, c->acc, a.fam, c->cfg.R, next_obs_slot(c), beta, c->cfg.q, c->N,
+                                  gather, gather, c->stream));
     c->pending_step = 0;
     c->step = step;
     c->beta = beta;
@@ -387,9 +445,10 @@ namespace {
 
 // Validates a configuration, allocates a context and its device buffers and
 // picks the sweep launch shape; no kernel runs.
-pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
+pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out, int rank = 0, int world = 1)
 {
     *out = nullptr;
+    if (world < 1 || world > 1024 || rank < 0 || rank >= world) return PA_ERR_INVALID;
     if (g.q < 2 || g.q > 128 || g.L < 2 || g.L > 1024 || (g.L & 1) || g.R < 1 || g.stream < 0 || g.stream > 255)
         return PA_ERR_INVALID;
     if (g.resample_mode < PA_RESAMPLE_NEAREST_INT || g.resample_mode > PA_RESAMPLE_OFF) return PA_ERR_INVALID;
@@ -405,7 +464,14 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
     c->cfg.R_cap = (int32_t)R_cap;
     c->N = g.L * g.L;
     c->nbins = 2 * c->N + 1;
-    c->R_cap = (int)R_cap;
+    c->rank = rank;
+    c->world = world;
+    c->shard = world > 1;
+    // a shard holds about R_cap / world replicas; the children it sends in one
+    // step can exceed its share by the spread of the copy numbers, hence the
+    // margin
+    c->R_cap = world > 1 ? (int)((R_cap + world - 1) / world + R_cap / (8 * world) + 1024) : (int)R_cap;
+    c->R_fill = world > 1 ? (g.R + world - 1) / world : g.R;
     c->stream = (cudaStream_t)cuda_stream;
     c->k0 = (uint32_t)(g.seed & 0xFFFFFFFFu);
     c->k1 = (uint32_t)(g.seed >> 32);
@@ -428,11 +494,16 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
         (s = dev_alloc(&c->E, c->R_cap)) || (s = dev_alloc(&c->Mt, c->R_cap)) ||
         (s = dev_alloc(&c->hist, c->nbins)) || (s = dev_alloc(&c->counts, c->R_cap)) ||
         (s = dev_alloc(&c->local_off, c->R_cap)) || (s = dev_alloc(&c->blocksum, nb)) ||
-        (s = dev_alloc(&c->parent, c->R_cap)) || (s = dev_alloc(&c->acc, 3)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
+        (s = dev_alloc(&c->parent, c->R_cap)) || (s = dev_alloc(&c->acc, 4)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
         return fail(s);
     if (g.track_families) {
         if ((s = dev_alloc(&c->anc[0], c->R_cap)) || (s = dev_alloc(&c->anc[1], c->R_cap)) ||
             (s = dev_alloc(&c->fam, g.R)))
+            return fail(s);
+    }
+    if (c->shard) {
+        if ((s = dev_alloc(&c->send, spin_bytes / sizeof(uint32_t))) ||
+            (g.track_families && (s = dev_alloc(&c->send_anc, c->R_cap))))
             return fail(s);
     }
     c->obs_cap = 1024;
@@ -446,6 +517,7 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out)
         c->host_stage = nullptr;
         return fail(cuda_fail(e));
     }
+    if ((s = alloc_wtables(c))) return fail(s);
     if ((s = choose_launch(c, 0, 0))) return fail(s);
     *out = c;
     return PA_OK;
@@ -501,7 +573,7 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
         h.lnZ = (double)c->N * std::log((double)g.q);
     cudaError_t e = cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->hist, 0, sizeof(int32_t) * c->nbins, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 3, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 4, c->stream);
     if (e == cudaSuccess && c->fam) e = cudaMemsetAsync(c->fam, 0, sizeof(int32_t) * g.R, c->stream);
     if (e == cudaSuccess)
         e = pa::launch_init(c->spins[0], c->anc[0], g.q, g.L, g.R, c->k0, c->k1, (uint32_t)g.stream << 24,
@@ -516,6 +588,7 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
 pa_status pa_save(pa_ctx *c, const char *path)
 {
     if (!c || !path) return PA_ERR_INVALID;
+    if (c->shard) return PA_ERR_STATE;
     if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
     pa::DevState st;
     pa_status s = sync_state(c, &st);
@@ -608,7 +681,7 @@ pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out)
     st.pop = h.pop;
     st.lnZ = h.lnZ;
     if (e == cudaSuccess) e = cudaMemcpy(c->st, &st, sizeof(st), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(c->acc, 0, sizeof(unsigned long long) * 3);
+    if (e == cudaSuccess) e = cudaMemset(c->acc, 0, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess && c->fam) e = cudaMemset(c->fam, 0, sizeof(int32_t) * h.cfg.R);
     if (e == cudaSuccess) e = cudaMemcpy(c->obs, &h.last, sizeof(pa_obs), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_fail(e));
@@ -646,6 +719,7 @@ pa_status pa_get_launch(pa_ctx *c, int32_t *rpb, int32_t *threads, int32_t *bloc
 pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, int32_t *R_out)
 {
     if (!c) return PA_ERR_INVALID;
+    if (c->shard) return PA_ERR_STATE;
     if (c->failed || c->pending_step != 0 || step <= c->step) return PA_ERR_STATE;
     if (!std::isfinite(dbeta) || !(c->beta + dbeta >= 0.0)) return PA_ERR_INVALID;
     const bool had_parents = c->resampled;
@@ -677,6 +751,22 @@ pa_status pa_sweep(pa_ctx *c, double beta, int32_t theta, int32_t step)
     if (!c) return PA_ERR_INVALID;
     if (theta < 0 || theta > pa::kMaxTheta || !(beta >= 0.0) || !std::isfinite(beta)) return PA_ERR_INVALID;
     if (c->failed) return PA_ERR_STATE;
+    if (c->shard) {
+        // after pa_shard_accept (the step's own number), or extra sweeps of a
+        // completed step
+        if (c->shard_stage == kShardAccepted ? step != c->pending_step
+                                             : (c->shard_stage != kShardReady || step != c->step))
+            return PA_ERR_STATE;
+        const int pending = c->pending_step;
+        c->pending_step = 0;  // the exchange has placed the new replicas: no gather
+        pa_status s = enqueue_sweep(c, beta, theta, step);
+        if (s) {
+            c->pending_step = pending;
+            return s;
+        }
+        c->shard_stage = kShardMeasured;
+        return PA_OK;
+    }
     if (c->pending_step != 0 ? step != c->pending_step : step != c->step) return PA_ERR_STATE;
     return enqueue_sweep(c, beta, theta, step);
 }
@@ -804,11 +894,191 @@ pa_status pa_get_parents(pa_ctx *c, int32_t *out, int32_t on_device)
     return PA_OK;
 }
 
+pa_status pa_shard_plan(const int64_t *totals, int32_t world, int32_t rank, int64_t *R_new, int64_t *lo, int64_t *hi,
+                        int64_t *send_counts, int64_t *recv_counts)
+{
+    if (!totals || world < 1 || world > 1024 || rank < 0 || rank >= world) return PA_ERR_INVALID;
+    int64_t R = 0;
+    for (int g = 0; g < world; ++g) {
+        if (totals[g] < 0) return PA_ERR_INVALID;
+        R += totals[g];
+    }
+    if (R < 1 || R >= (int64_t)1 << 24) return PA_ERR_CAPACITY;
+    auto bound = [&](int64_t d) { return d * R / world; };
+    auto overlap = [](int64_t a0, int64_t a1, int64_t b0, int64_t b1) {
+        const int64_t x = std::max(a0, b0), y = std::min(a1, b1);
+        return y > x ? y - x : (int64_t)0;
+    };
+    // rank g's children are the new slots [O_g, O_g + T_g), O_g = sum_{h<g} T_h
+    int64_t O = 0, my0 = 0;
+    for (int g = 0; g < rank; ++g) O += totals[g];
+    my0 = O;
+    const int64_t b0 = bound(rank), b1 = bound(rank + 1);
+    int64_t Og = 0;
+    for (int g = 0; g < world; ++g) {
+        if (send_counts) send_counts[g] = overlap(my0, my0 + totals[rank], bound(g), bound(g + 1));
+        if (recv_counts) recv_counts[g] = overlap(Og, Og + totals[g], b0, b1);
+        Og += totals[g];
+    }
+    if (R_new) *R_new = R;
+    if (lo) *lo = b0;
+    if (hi) *hi = b1;
+    return PA_OK;
+}
+
+pa_status pa_shard_init(const pa_config *cfg, int32_t rank, int32_t world, void *cuda_stream, pa_ctx **out)
+{
+    if (!out) return PA_ERR_INVALID;
+    *out = nullptr;
+    if (!cfg || world < 2) return PA_ERR_INVALID;
+    const pa_config &g = *cfg;
+    pa_ctx *c = nullptr;
+    pa_status s = ctx_create(g, cuda_stream, &c, rank, world);
+    if (s) return s;
+    auto fail = [&](pa_status e) {
+        release(c);
+        delete c;
+        return e;
+    };
+    const int lo = (int)((int64_t)rank * g.R / world), hi = (int)((int64_t)(rank + 1) * g.R / world);
+    c->slot0 = lo;
+    c->R_all = g.R;
+    pa::DevState h{};
+    h.pop = hi - lo;
+    if (g.init_mode == PA_INIT_GROUND)
+        h.lnZ = std::log((double)g.q) - g.beta0 * (double)(-2 * c->N);
+    else
+        h.lnZ = (double)c->N * std::log((double)g.q);
+    cudaError_t e = cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->hist, 0, sizeof(int32_t) * c->nbins, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(unsigned long long) * 4, c->stream);
+    if (e == cudaSuccess && c->fam) e = cudaMemsetAsync(c->fam, 0, sizeof(int32_t) * g.R, c->stream);
+    if (e == cudaSuccess && hi > lo)
+        e = pa::launch_init(c->spins[0], c->anc[0], g.q, g.L, hi - lo, c->k0, c->k1, (uint32_t)g.stream << 24,
+                            g.init_mode == PA_INIT_GROUND, c->stream, (uint32_t)lo);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    if ((s = enqueue_sweep(c, g.beta0, 0, 0))) return fail(s);
+    if ((s = sync_state(c, nullptr))) return fail(s);
+    c->shard_stage = kShardMeasured;
+    c->shard_resampled = false;
+    *out = c;
+    return PA_OK;
+}
+
+pa_status pa_shard_get_buffers(pa_ctx *c, pa_shard_buffers *out)
+{
+    if (!c || !out) return PA_ERR_INVALID;
+    if (!c->shard) return PA_ERR_STATE;
+    const int nxt = c->host_parity ^ 1;
+    out->hist = c->hist;
+    out->sums = reinterpret_cast<int64_t *>(c->acc);
+    out->fam = c->fam;
+    out->send = c->send;
+    out->send_anc = c->send_anc;
+    out->recv = c->spins[nxt];
+    out->recv_anc = c->anc[nxt];
+    out->replica_words = pa::replica_words(c->cfg.q, c->cfg.L);
+    out->capacity = c->R_cap;
+    out->n_bins = c->nbins;
+    return PA_OK;
+}
+
+pa_status pa_shard_finalize(pa_ctx *c, double beta)
+{
+    if (!c || !std::isfinite(beta)) return PA_ERR_INVALID;
+    if (!c->shard || c->failed || c->shard_stage != kShardMeasured) return PA_ERR_STATE;
+    PA_CK(pa::launch_finalize(c->st, c->acc, c->fam, c->cfg.R, next_obs_slot(c), beta, c->cfg.q, c->N, 0,
+                              c->shard_resampled ? 1 : 0, c->stream, c->R_all));
+    c->shard_resampled = false;
+    c->shard_stage = kShardReady;
+    return PA_OK;
+}
+
+pa_status pa_shard_counts(pa_ctx *c, double dbeta, int32_t step, int64_t *local_total)
+{
+    if (!c || !local_total) return PA_ERR_INVALID;
+    if (!c->shard || c->failed || c->shard_stage != kShardReady || step <= c->step) return PA_ERR_STATE;
+    if (!std::isfinite(dbeta) || !(c->beta + dbeta >= 0.0)) return PA_ERR_INVALID;
+    const double *wtab = nullptr;
+    pa_status s = get_wtable(c, dbeta, &wtab);
+    if (s) return s;
+    PA_CK(pa::launch_resample(c->hist, c->nbins, c->E, dbeta, c->cfg.R, c->R_cap, c->cfg.resample_mode, step,
+                              (uint32_t)c->cfg.stream << 24, c->k0, c->k1, wtab, c->counts, c->local_off,
+                              c->blocksum, c->parent, c->hist, c->st, c->stream, c->slot0, c->R_all));
+    pa::DevState h;
+    s = sync_state(c, &h);
+    if (s == PA_ERR_CAPACITY) {
+        // this rank's children exceed its buffers: the population stays at step i-1
+        pa::DevState fix = h;
+        fix.err = 0;
+        PA_CK(cudaMemcpyAsync(c->st, &fix, sizeof(fix), cudaMemcpyHostToDevice, c->stream));
+        PA_CK(cudaStreamSynchronize(c->stream));
+        c->failed = false;
+        return PA_ERR_CAPACITY;
+    }
+    if (s) return s;
+    // this rank's near ties join the sums that the caller adds over the ranks
+    const int64_t ties = h.ties;
+    PA_CK(cudaMemcpyAsync(c->acc + 3, &ties, sizeof(ties), cudaMemcpyHostToDevice, c->stream));
+    c->n_pack = h.pop_next;
+    c->pending_step = step;
+    c->resampled = true;
+    c->shard_stage = kShardCounted;
+    *local_total = h.pop_next;
+    return PA_OK;
+}
+
+pa_status pa_shard_pack(pa_ctx *c, const int64_t *totals, int64_t *send_counts, int64_t *recv_counts)
+{
+    if (!c || !totals) return PA_ERR_INVALID;
+    if (!c->shard || c->failed || c->shard_stage != kShardCounted) return PA_ERR_STATE;
+    if (totals[c->rank] != c->n_pack) return PA_ERR_INVALID;
+    int64_t R_new = 0, lo = 0, hi = 0;
+    pa_status s = pa_shard_plan(totals, c->world, c->rank, &R_new, &lo, &hi, send_counts, recv_counts);
+    if (s) return s;
+    if (hi - lo > c->R_cap || R_new > c->cfg.R_cap) return PA_ERR_CAPACITY;
+    PA_CK(pa::launch_shard_pack(c->spins[c->host_parity], c->cfg.track_families ? c->anc[c->host_parity] : nullptr,
+                                c->parent, c->n_pack, pa::replica_words(c->cfg.q, c->cfg.L), c->send,
+                                c->send_anc, c->stream));
+    c->slot0_next = (int)lo;
+    c->n_next = (int)(hi - lo);
+    c->R_all_next = (int)R_new;
+    c->shard_stage = kShardPacked;
+    return PA_OK;
+}
+
+pa_status pa_shard_accept(pa_ctx *c)
+{
+    if (!c) return PA_ERR_INVALID;
+    if (!c->shard || c->failed || c->shard_stage != kShardPacked) return PA_ERR_STATE;
+    PA_CK(pa::launch_shard_accept(c->st, c->n_next, c->stream));
+    c->host_parity ^= 1;
+    c->slot0 = c->slot0_next;
+    c->R_all = c->R_all_next;
+    c->shard_resampled = true;
+    c->shard_stage = kShardAccepted;
+    return PA_OK;
+}
+
+pa_status pa_shard_range(pa_ctx *c, int64_t *slot0, int64_t *count, int64_t *R_all)
+{
+    if (!c) return PA_ERR_INVALID;
+    if (!c->shard) return PA_ERR_STATE;
+    pa::DevState h;
+    pa_status s = sync_state(c, &h);
+    if (s) return s;
+    if (slot0) *slot0 = c->slot0;
+    if (count) *count = h.pop;
+    if (R_all) *R_all = c->R_all;
+    return PA_OK;
+}
+
 pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_obs *obs_out,
                  const int32_t *hist_steps, int32_t n_hist, int32_t *hist_out, int32_t use_graph)
 {
     if (!c || !betas || K < 1 || theta < 0 || theta > pa::kMaxTheta || n_hist < 0 || (n_hist > 0 && (!hist_steps || !hist_out)))
         return PA_ERR_INVALID;
+    if (c->shard) return PA_ERR_STATE;
     if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
     for (int i = 0; i <= K; ++i)
         if (!std::isfinite(betas[i]) || !(betas[i] >= 0.0)) return PA_ERR_INVALID;
@@ -834,14 +1104,44 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
     }
     const long long first_obs = c->n_obs;
     const int step0 = c->step;
-    // every weight table of the schedule before any capture begins; none is
-    // evicted until the run has finished
-    c->wtab_hold = true;
-    for (int i = 1; i <= K; ++i) {
-        const double *w = nullptr;
-        pa_status s = get_wtable(c, betas[i] - betas[i - 1], &w);
+    // every weight table of the schedule is on the device before any capture
+    // begins and stays until the run has finished: in the arena when the
+    // schedule has at most kWTableSlots distinct steps (loaded in turn, none
+    // evicts another), else in tables of the run's own
+    {
+        std::vector<uint64_t> keys;
+        for (int i = 1; i <= K; ++i) {
+            const double d = betas[i] - betas[i - 1];
+            uint64_t key;
+            std::memcpy(&key, &d, sizeof(key));
+            if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+        }
+        pa_status s = PA_OK;
+        if (keys.size() <= (size_t)kWTableSlots) {
+            for (uint64_t key : keys) {
+                double d;
+                std::memcpy(&d, &key, sizeof(d));
+                const double *w = nullptr;
+                if ((s = get_wtable(c, d, &w))) break;
+            }
+        } else {
+            const size_t n = (size_t)c->nbins;
+            std::vector<double> host(n * keys.size());
+            if (!(s = dev_alloc(&c->wt_run, host.size()))) {
+                for (size_t k = 0; k < keys.size(); ++k) {
+                    double d;
+                    std::memcpy(&d, &keys[k], sizeof(d));
+                    pa::weight_table(d, c->nbins, host.data() + n * k);
+                    c->wt_run_at.emplace_back(keys[k], c->wt_run + n * k);
+                }
+                cudaError_t e = cudaMemcpyAsync(c->wt_run, host.data(), sizeof(double) * host.size(),
+                                                cudaMemcpyHostToDevice, c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                if (e != cudaSuccess) s = cuda_fail(e);
+            }
+        }
         if (s) {
-            c->wtab_hold = false;
+            release_run_tables(c);
             if (hstore) cudaFree(hstore);
             return s;
         }
@@ -861,7 +1161,7 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
         if (e == cudaSuccess) e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             c->profiling = was_profiling;
-            c->wtab_hold = false;
+            release_run_tables(c);
             if (hstore) cudaFree(hstore);
             return cuda_fail(e);
         }
@@ -890,8 +1190,7 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     cudaStreamSynchronize(c->stream);
-    c->wtab_hold = false;
-    if (c->wtabs.size() > kWTableCache) release_wtables(c, kWTableCache);
+    release_run_tables(c);
     if (s == PA_OK && obs_out) {
         for (int i = 0; i < K; ++i) {
             const pa::DevObs *slot = c->obs + ((first_obs + i) % c->obs_cap);
@@ -916,6 +1215,7 @@ pa_status pa_next_dbeta(pa_ctx *c, double target, double dbeta_cap, int32_t iter
     if (!c || !dbeta_out || !(target > 0.0 && target < 1.0) || !(dbeta_cap > 0.0) || !std::isfinite(dbeta_cap) ||
         iters < 0 || iters > 200)
         return PA_ERR_INVALID;
+    if (c->shard) return PA_ERR_STATE;
     if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
     PA_CK(pa::launch_newton(c->hist, c->nbins, c->st, target, dbeta_cap, iters, c->aux, c->stream));
     double h[2];

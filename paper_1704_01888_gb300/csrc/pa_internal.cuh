@@ -104,6 +104,7 @@ struct SweepArgs {
     int32_t rpb;               // replicas per block iteration
     int32_t gather;            // 1: read parents from buf[parity], write buf[parity^1]
     uint32_t stream_hi;        // stream number << 24 (top byte of the slot counter word)
+    uint32_t slot0;            // global slot of local slot 0 (0 unless the population spans GPUs)
 };
 
 // Launchers (pa_sweep.cu)
@@ -112,15 +113,27 @@ size_t sweep_smem_bytes(int q, int L, int rpb);
 int sweep_max_blocks_per_sm(int q, int L, int rpb, int threads);
 
 // Launchers (pa_resample.cu)
+// slot0: global slot of local slot 0 (random keys and family ids follow it).
 cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
-                        uint32_t stream_hi, int ground, cudaStream_t s);
+                        uint32_t stream_hi, int ground, cudaStream_t s, uint32_t slot0 = 0u);
 // wtab: the weight table of dbeta (weight_table below), 2N + 1 entries.
+// j0 / R_prev_all: global index of local replica 0 and the size of the whole
+// population when it spans several GPUs (0, 0 otherwise).
 cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, double dbeta, int R_target,
                             int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1,
                             const double *wtab, int32_t *counts, int32_t *local_off, int32_t *blocksum,
-                            int32_t *parent, int32_t *hist_zero, DevState *st, cudaStream_t s);
+                            int32_t *parent, int32_t *hist_zero, DevState *st, cudaStream_t s, int j0 = 0,
+                            int R_prev_all = 0);
+// R_all: size of the whole population when the sums cover several GPUs (0 otherwise).
 cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,
-                            double beta, int q, int N, int gathered, int resampled, cudaStream_t s);
+                            double beta, int q, int N, int gathered, int resampled, cudaStream_t s, int R_all = 0);
+// A population spread over several GPUs: copies the n children of the
+// pending resample (parent map, new-slot order) out of `spins` / `anc` into
+// contiguous send buffers; and, once the exchange has delivered this GPU's
+// new replicas into the other buffer, makes them the current population.
+cudaError_t launch_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent, int n, int RW,
+                             uint32_t *send, int32_t *send_anc, cudaStream_t s);
+cudaError_t launch_shard_accept(DevState *st, int n_local, cudaStream_t s);
 cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count,
                                 cudaStream_t s);
 

@@ -257,6 +257,7 @@ struct Group {
     int32_t *E, *Mt, *hist;  // per-replica energies and occupations, energy histogram
     int first, nrep;         // slots [first, first + nrep)
     int q, theta, step;
+    uint32_t slot0;          // global slot of local slot 0 (a population shared by several GPUs)
     uint32_t stream_hi;      // stream number << 24, or'ed into the slot counter word
     bool gather, write_back;
 };
@@ -466,7 +467,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     neighbour_planes<B, MODE, BP>(oth, L, IPC, WPR, nb_last, inv_row, it, c, U, D, H, X);
 
                 // proposal: direction sigma = Z_0, offset bits u = Z_1..Z_{B-1}
-                const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
+                const uint32_t slot = (G.slot0 + (uint32_t)(first + r)) | G.stream_hi;
                 const uint32_t w = (uint32_t)it;
                 uint32_t Z[8];
                 {
@@ -591,7 +592,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 uint32_t acc = q_mask[0][ee];
                 uint32_t und = live ? q_mask[1][ee] : 0u;
                 const uint32_t c0 = q_mask[2][ee], e1 = q_mask[3][ee];
-                const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
+                const uint32_t slot = (G.slot0 + (uint32_t)(first + r)) | G.stream_hi;
                 const uint32_t w = (uint32_t)it;
                 constexpr int fc = (B + 3) / 4;
                 acceptance_calls<B, true>(fc + kFirstPassCalls, fc + 8, w, ctr1, (uint32_t)G.step, slot, rk0, rk1,
@@ -760,7 +761,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *scratch32, int *
 // in the state floor(Z q / 2^32), Z = word (slot & 3) of counter
 // (slot >> 2, GROUND, 0, stream).
 __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, int L, long long i, uint32_t k0,
-                                          uint32_t k1, uint32_t stream_hi, int ground)
+                                          uint32_t k1, uint32_t stream_hi, int ground, uint32_t slot0 = 0u)
 {
     const int B = state_bits(q);
     const int BP = plane_stride(B);
@@ -775,9 +776,10 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
     const bool packed = rows_packed(L), banded = rows_banded(L);
     const int nb = (packed || banded) ? 32 : ((it % WPR) == WPR - 1 ? nb_last : 32);
     uint32_t planes[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    const uint32_t key_slot = slot0 + (uint32_t)slot;  // the random numbers follow the global slot
     if (ground) {
-        const uint4 w = philox10(make_uint4((uint32_t)slot >> 2, DOM_GROUND, 0u, stream_hi), k0, k1);
-        const uint32_t alpha = __umulhi(pick_word(w, slot & 3), (uint32_t)q);
+        const uint4 w = philox10(make_uint4(key_slot >> 2, DOM_GROUND, 0u, stream_hi), k0, k1);
+        const uint32_t alpha = __umulhi(pick_word(w, key_slot & 3), (uint32_t)q);
         const uint32_t vm = nb == 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
         for (int p = 0; p < B; ++p) planes[p] = ((alpha >> p) & 1u) ? vm : 0u;
     } else {
@@ -801,7 +803,7 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
             const int site = y * L + x;
             if ((site >> 2) != last) {
                 last = site >> 2;
-                w = philox10(make_uint4((uint32_t)last, DOM_INIT, 0u, (uint32_t)slot | stream_hi), k0, k1);
+                w = philox10(make_uint4((uint32_t)last, DOM_INIT, 0u, key_slot | stream_hi), k0, k1);
             }
             const uint32_t s = __umulhi(pick_word(w, site & 3), (uint32_t)q);
             for (int p = 0; p < B; ++p) planes[p] |= ((s >> p) & 1u) << b;
@@ -809,7 +811,7 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
     }
     uint32_t *dst = spins + (size_t)slot * replica_words_of(B, L) + (size_t)rem * BP;
     for (int p = 0; p < BP; ++p) dst[p] = planes[p];
-    if (rem == 0 && anc) anc[slot] = slot;
+    if (rem == 0 && anc) anc[slot] = (int32_t)key_slot;
 }
 
 // State of canonical site i (= r N + y L + x) of a multi-spin-coded population.
@@ -917,8 +919,11 @@ __device__ __forceinline__ double exact_round(unsigned long long *acc)
 
 // One block: reference bin, S (exact sum of h_k w_k, weights from the host
 // table wtab by distance |k - k_ref|) and ln Q of the pending resample.
+// R_prev_all: the population size R_{i-1} when the histogram covers several
+// GPUs' replicas (0: this GPU's own, st->pop).
 __device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, double dbeta, const double *wtab,
-                                             DevState *st, unsigned long long *s_acc, long long *s_l)
+                                             DevState *st, unsigned long long *s_acc, long long *s_l,
+                                             int R_prev_all = 0)
 {
     if (st->err) return;
     const int tid = threadIdx.x;
@@ -958,7 +963,8 @@ __device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, dou
         st->S = S;
         st->E_ref = E_ref;
         st->ties = 0;
-        st->lnQ = __dadd_rn(__dmul_rn(-dbeta, (double)E_ref), log(S / (double)st->pop));
+        const int R_prev = R_prev_all > 0 ? R_prev_all : st->pop;
+        st->lnQ = __dadd_rn(__dmul_rn(-dbeta, (double)E_ref), log(S / (double)R_prev));
     }
     __syncthreads();
 }
@@ -1007,10 +1013,12 @@ __device__ __forceinline__ bool round_tie(double rho, double frac, double bounda
 
 // One block of 1024 old replicas (chunk): copy numbers and their block scan.
 // w(E_j) comes from the host table wtab by distance |E_j - E_ref|.
+// j0: global index of local replica 0 (a population shared by several GPUs):
+// the random numbers of replica j follow j0 + j.
 __device__ __forceinline__ void counts_body(int chunk, const int32_t *E, int twoN, int R_target, int mode, int step,
                                             uint32_t stream_hi, uint32_t k0, uint32_t k1, const double *wtab,
                                             int32_t *counts, int32_t *local_off, int32_t *blocksum, DevState *st,
-                                            int *s_i)
+                                            int *s_i, int j0 = 0)
 {
     if (st->err) return;
     const int R_prev = st->pop;
@@ -1024,16 +1032,17 @@ __device__ __forceinline__ void counts_body(int chunk, const int32_t *E, int two
         const double rho = __ddiv_rn(__dmul_rn((double)R_target, w), st->S);
         const double n = floor(rho);
         const double frac = __dsub_rn(rho, n);
+        const int jg = j0 + j;
         if (mode == 2) {
-            r = poisson_draw(rho, j, step, stream_hi, k0, k1, tie);
+            r = poisson_draw(rho, jg, step, stream_hi, k0, k1, tie);
         } else if (mode == 3) {
             r = 1;
         } else if (mode == 1) {
             r = (int)n + (frac >= 0.5);
             tie = round_tie(rho, frac, 0.5);
         } else {
-            const uint4 u = philox10(make_uint4((uint32_t)j >> 2, DOM_RESAMPLE, (uint32_t)step, stream_hi), k0, k1);
-            const uint32_t uj = pick_word(u, j & 3);
+            const uint4 u = philox10(make_uint4((uint32_t)jg >> 2, DOM_RESAMPLE, (uint32_t)step, stream_hi), k0, k1);
+            const uint32_t uj = pick_word(u, jg & 3);
             r = (int)n + ((double)uj < __dmul_rn(frac, 4294967296.0));
             tie = round_tie(rho, frac, __dmul_rn((double)uj, 0x1p-32));
         }
@@ -1081,12 +1090,15 @@ __device__ __forceinline__ void scatter_body(int chunk, int nchunks, const int32
 
 // One block: estimators of the step (Sec. 2 step 4, Eqs. 4-5), family
 // entropy, ln Z of Eq. 2, buffer parity flip.
+// R_all: the population size when the sums and family counts cover several
+// GPUs' replicas (0: this GPU's own).
 __device__ __forceinline__ void finalize_body(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,
                                               double beta, int q, int N, int gathered, int resampled, double *s_d,
-                                              long long *s_l)
+                                              long long *s_l, int R_all = 0)
 {
     if (st->err) return;
-    const int R = gathered ? st->pop_next : st->pop;
+    const int R_local = gathered ? st->pop_next : st->pop;
+    const int R = R_all > 0 ? R_all : R_local;
     double part = 0.0;
     long long nf = 0;
     if (fam) {
@@ -1116,7 +1128,7 @@ __device__ __forceinline__ void finalize_body(DevState *st, unsigned long long *
             st->lnZ = __dadd_rn(st->lnZ, lnQ);
         }
         if (gathered) {
-            st->pop = R;
+            st->pop = R_local;
             st->parity ^= 1;
         }
         DevObs o;
@@ -1130,7 +1142,9 @@ __device__ __forceinline__ void finalize_body(DevState *st, unsigned long long *
         o.S_f = fam ? Sf : 0.0;
         o.R = R;
         o.n_families = fam ? nf : 0;
-        o.n_near_ties = resampled ? st->ties : 0;
+        // several GPUs: acc[3] holds the near ties summed over them
+        o.n_near_ties = resampled ? (R_all > 0 ? (long long)acc[3] : (long long)st->ties) : 0;
+        if (R_all > 0) acc[3] = 0ull;
         o.sumE = sE;
         o.sumE2 = sE2;
         o.sumMt = sM;

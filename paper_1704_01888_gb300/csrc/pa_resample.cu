@@ -30,30 +30,30 @@ namespace {
 constexpr int kBlock = 1024;
 
 __global__ void k_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
-                       uint32_t stream_hi, int ground)
+                       uint32_t stream_hi, int ground, uint32_t slot0)
 {
     const long long total = (long long)R * (2 * colour_words(L));
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x)
-        dev::init_item(spins, anc, q, L, i, k0, k1, stream_hi, ground);
+        dev::init_item(spins, anc, q, L, i, k0, k1, stream_hi, ground, slot0);
 }
 
 __global__ void __launch_bounds__(kBlock) k_weights(const int32_t *hist, int nbins, double dbeta, const double *wtab,
-                                                    DevState *st)
+                                                    DevState *st, int R_prev_all)
 {
     __shared__ unsigned long long s_acc[dev::kSumLimbs];
     __shared__ long long s_l[32];
-    dev::weights_body(hist, nbins, dbeta, wtab, st, s_acc, s_l);
+    dev::weights_body(hist, nbins, dbeta, wtab, st, s_acc, s_l, R_prev_all);
 }
 
 __global__ void __launch_bounds__(kBlock) k_counts(const int32_t *E, int twoN, int R_target, int mode, int step,
                                                    uint32_t stream_hi, uint32_t k0, uint32_t k1, const double *wtab,
                                                    int32_t *counts, int32_t *local_off, int32_t *blocksum,
-                                                   DevState *st)
+                                                   DevState *st, int j0)
 {
     __shared__ int s_i[32];
     dev::counts_body(blockIdx.x, E, twoN, R_target, mode, step, stream_hi, k0, k1, wtab, counts, local_off, blocksum,
-                     st, s_i);
+                     st, s_i, j0);
 }
 
 __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t *counts, const int32_t *local_off,
@@ -75,17 +75,17 @@ __global__ void __launch_bounds__(kBlock) k_resample_small(const int32_t *hist, 
                                                            uint32_t stream_hi, uint32_t k0, uint32_t k1,
                                                            const double *wtab, int32_t *counts, int32_t *local_off,
                                                            int32_t *blocksum, int32_t *parent, int32_t *hist_zero,
-                                                           DevState *st)
+                                                           DevState *st, int j0, int R_prev_all)
 {
     __shared__ unsigned long long s_acc[dev::kSumLimbs];
     __shared__ long long s_l[32];
     __shared__ int s_i[32];
-    dev::weights_body(hist, nbins, dbeta, wtab, st, s_acc, s_l);
+    dev::weights_body(hist, nbins, dbeta, wtab, st, s_acc, s_l, R_prev_all);
     __syncthreads();
     const int nb = (R_cap + kBlock - 1) / kBlock;
     for (int chunk = 0; chunk < nb; ++chunk) {
         dev::counts_body(chunk, E, nbins - 1, R_target, mode, step, stream_hi, k0, k1, wtab, counts, local_off,
-                         blocksum, st, s_i);
+                         blocksum, st, s_i, j0);
         __syncthreads();
     }
     const int nb2 = nb > (nbins + kBlock - 1) / kBlock ? nb : (nbins + kBlock - 1) / kBlock;
@@ -97,11 +97,37 @@ __global__ void __launch_bounds__(kBlock) k_resample_small(const int32_t *hist, 
 
 __global__ void __launch_bounds__(kBlock) k_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0,
                                                      DevObs *obs, double beta, int q, int N, int gathered,
-                                                     int resampled)
+                                                     int resampled, int R_all)
 {
     __shared__ double s_d[32];
     __shared__ long long s_l[32];
-    dev::finalize_body(st, acc, fam, R0, obs, beta, q, N, gathered, resampled, s_d, s_l);
+    dev::finalize_body(st, acc, fam, R0, obs, beta, q, N, gathered, resampled, s_d, s_l, R_all);
+}
+
+// Children of the pending resample, in new-slot order, copied out of the
+// current population for the exchange between GPUs (one uint4 per thread).
+__global__ void k_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent, int n, int RW,
+                             uint32_t *send, int32_t *send_anc)
+{
+    const int U = RW / 4;
+    const long long total = (long long)n * U;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / U), o = (int)(i - (long long)c * U);
+        const int p = parent[c];
+        reinterpret_cast<uint4 *>(send + (size_t)c * RW)[o] = reinterpret_cast<const uint4 *>(spins + (size_t)p * RW)[o];
+        if (o == 0 && send_anc) send_anc[c] = anc[p];
+    }
+}
+
+// The received replicas (in the buffer not holding the current population)
+// become the current population.
+__global__ void k_shard_accept(DevState *st, int n_local)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !st->err) {
+        st->pop = n_local;
+        st->parity ^= 1;
+    }
 }
 
 __global__ void k_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, long long count)
@@ -123,10 +149,10 @@ int grid_for(long long work, int threads)
 }  // namespace
 
 cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint32_t k0, uint32_t k1,
-                        uint32_t stream_hi, int ground, cudaStream_t s)
+                        uint32_t stream_hi, int ground, cudaStream_t s, uint32_t slot0)
 {
     const long long work = (long long)R * (2 * colour_words(L));
-    k_init<<<grid_for(work, 256), 256, 0, s>>>(spins, anc, q, L, R, k0, k1, stream_hi, ground);
+    k_init<<<grid_for(work, 256), 256, 0, s>>>(spins, anc, q, L, R, k0, k1, stream_hi, ground, slot0);
     bump_launch_count(1);
     return cudaGetLastError();
 }
@@ -134,18 +160,20 @@ cudaError_t launch_init(uint32_t *spins, int32_t *anc, int q, int L, int R, uint
 cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, double dbeta, int R_target,
                             int R_cap, int mode, int step, uint32_t stream_hi, uint32_t k0, uint32_t k1,
                             const double *wtab, int32_t *counts, int32_t *local_off, int32_t *blocksum,
-                            int32_t *parent, int32_t *hist_zero, DevState *st, cudaStream_t s)
+                            int32_t *parent, int32_t *hist_zero, DevState *st, cudaStream_t s, int j0,
+                            int R_prev_all)
 {
     if (R_cap <= kSmallResample) {
         k_resample_small<<<1, kBlock, 0, s>>>(hist, nbins, E, dbeta, R_target, R_cap, mode, step, stream_hi, k0, k1,
-                                              wtab, counts, local_off, blocksum, parent, hist_zero, st);
+                                              wtab, counts, local_off, blocksum, parent, hist_zero, st, j0,
+                                              R_prev_all);
         bump_launch_count(1);
         return cudaGetLastError();
     }
     const int nb = (R_cap + kBlock - 1) / kBlock;
-    k_weights<<<1, kBlock, 0, s>>>(hist, nbins, dbeta, wtab, st);
+    k_weights<<<1, kBlock, 0, s>>>(hist, nbins, dbeta, wtab, st, R_prev_all);
     k_counts<<<nb, kBlock, 0, s>>>(E, nbins - 1, R_target, mode, step, stream_hi, k0, k1, wtab, counts, local_off,
-                                   blocksum, st);
+                                   blocksum, st, j0);
     const int nb2 = nb > (nbins + kBlock - 1) / kBlock ? nb : (nbins + kBlock - 1) / kBlock;
     k_scatter<<<nb2, kBlock, 0, s>>>(counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st);
     bump_launch_count(3);
@@ -153,9 +181,25 @@ cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, do
 }
 
 cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,
-                            double beta, int q, int N, int gathered, int resampled, cudaStream_t s)
+                            double beta, int q, int N, int gathered, int resampled, cudaStream_t s, int R_all)
 {
-    k_finalize<<<1, kBlock, 0, s>>>(st, acc, fam, R0, obs, beta, q, N, gathered, resampled);
+    k_finalize<<<1, kBlock, 0, s>>>(st, acc, fam, R0, obs, beta, q, N, gathered, resampled, R_all);
+    bump_launch_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent, int n, int RW,
+                             uint32_t *send, int32_t *send_anc, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_shard_pack<<<grid_for((long long)n * (RW / 4), 256), 256, 0, s>>>(spins, anc, parent, n, RW, send, send_anc);
+    bump_launch_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_accept(DevState *st, int n_local, cudaStream_t s)
+{
+    k_shard_accept<<<1, 32, 0, s>>>(st, n_local);
     bump_launch_count(1);
     return cudaGetLastError();
 }

@@ -42,6 +42,7 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
     G.theta = a.theta;
     G.step = a.step;
     G.stream_hi = a.stream_hi;
+    G.slot0 = a.slot0;
     G.gather = a.gather != 0;
     G.write_back = a.gather || a.theta > 0;
     return G;
