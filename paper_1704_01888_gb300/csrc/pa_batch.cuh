@@ -156,7 +156,6 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
         G.theta = sp.theta;
         G.step = i;
         G.stream_hi = r.stream_hi;
-        G.slot0 = 0u;
         G.gather = b.gather != 0;
         G.write_back = b.gather || sp.theta > 0;
         dev::build_threshold_table(s_tab, sp.thr);

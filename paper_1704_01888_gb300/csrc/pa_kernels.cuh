@@ -255,9 +255,9 @@ struct Group {
     int32_t *anc_out;
     int32_t *fam;            // family counts (null: no families)
     int32_t *E, *Mt, *hist;  // per-replica energies and occupations, energy histogram
-    int first, nrep;         // slots [first, first + nrep)
+    int first, nrep;         // slots [first, first + nrep): global slots (random keys); the
+                             // arrays above are indexed by them
     int q, theta, step;
-    uint32_t slot0;          // global slot of local slot 0 (a population shared by several GPUs)
     uint32_t stream_hi;      // stream number << 24, or'ed into the slot counter word
     bool gather, write_back;
 };
@@ -467,7 +467,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                     neighbour_planes<B, MODE, BP>(oth, L, IPC, WPR, nb_last, inv_row, it, c, U, D, H, X);
 
                 // proposal: direction sigma = Z_0, offset bits u = Z_1..Z_{B-1}
-                const uint32_t slot = (G.slot0 + (uint32_t)(first + r)) | G.stream_hi;
+                const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
                 const uint32_t w = (uint32_t)it;
                 uint32_t Z[8];
                 {
@@ -592,7 +592,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 uint32_t acc = q_mask[0][ee];
                 uint32_t und = live ? q_mask[1][ee] : 0u;
                 const uint32_t c0 = q_mask[2][ee], e1 = q_mask[3][ee];
-                const uint32_t slot = (G.slot0 + (uint32_t)(first + r)) | G.stream_hi;
+                const uint32_t slot = (uint32_t)(first + r) | G.stream_hi;
                 const uint32_t w = (uint32_t)it;
                 constexpr int fc = (B + 3) / 4;
                 acceptance_calls<B, true>(fc + kFirstPassCalls, fc + 8, w, ctr1, (uint32_t)G.step, slot, rk0, rk1,
@@ -861,22 +861,69 @@ __device__ __forceinline__ uint8_t canonical_state(const uint32_t *spins, int q,
 // R_cap < 2^24, i.e. below bit 1098: 36 limbs.
 constexpr int kSumLimbs = 36;
 
-__device__ __forceinline__ void exact_add(unsigned long long *acc, uint32_t h, double w)
+// The term h w (w > 0) as four 32-bit chunks c[0..3] of limbs li .. li + 3.
+__device__ __forceinline__ int exact_term(uint32_t h, double w, uint32_t (&c)[4])
 {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
     const int ef = (int)(bits >> 52) & 0x7FF;
-    if (bits == 0ull) return;
     const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
     const int pos = ef ? ef - 1 : 0;
     const unsigned long long lo = m * (unsigned long long)h;
     const unsigned long long hi = __umul64hi(m, (unsigned long long)h);
-    const int li = pos >> 5, sh = pos & 31;
+    const int sh = pos & 31;
     const unsigned long long lo_s = lo << sh;
     const unsigned long long hi_s = (hi << sh) | (sh ? lo >> (64 - sh) : 0ull);
-    const uint32_t c[4] = {(uint32_t)lo_s, (uint32_t)(lo_s >> 32), (uint32_t)hi_s, (uint32_t)(hi_s >> 32)};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (c[k]) atomicAdd(acc + li + k, (unsigned long long)c[k]);
+    c[0] = (uint32_t)lo_s;
+    c[1] = (uint32_t)(lo_s >> 32);
+    c[2] = (uint32_t)hi_s;
+    c[3] = (uint32_t)(hi_s >> 32);
+    return pos >> 5;
+}
+
+// Adds the terms of the occupied bins among k_begin .. k_end - 1 to the
+// shared limbs.  Consecutive bins have weights within a few binades of one
+// another, so a thread sums its terms in five register limbs (li - 1 .. li +
+// 3 of the first term) and adds them to the shared array only when a term
+// falls outside them: a handful of shared atomics per thread instead of four
+// per term.
+__device__ __forceinline__ void exact_add_range(unsigned long long *acc, const int32_t *hist, const double *wtab,
+                                                int kref, int k_begin, int k_end)
+{
+    unsigned long long w0 = 0ull, w1 = 0ull, w2 = 0ull, w3 = 0ull, w4 = 0ull;
+    int base = -2;
+    auto flush = [&]() {
+        if (base < 0) return;
+        if (w0) atomicAdd(acc + base, w0);
+        if (w1) atomicAdd(acc + base + 1, w1);
+        if (w2) atomicAdd(acc + base + 2, w2);
+        if (w3) atomicAdd(acc + base + 3, w3);
+        if (w4) atomicAdd(acc + base + 4, w4);
+        w0 = w1 = w2 = w3 = w4 = 0ull;
+    };
+    for (int k = k_begin; k < k_end; ++k) {
+        const int h = hist[k];
+        if (h <= 0) continue;
+        const double w = wtab[k >= kref ? k - kref : kref - k];
+        if (w == 0.0) continue;
+        uint32_t c[4];
+        const int li = exact_term((uint32_t)h, w, c);
+        if (li < base || li > base + 1) {
+            flush();
+            base = li > 0 ? li - 1 : 0;
+        }
+        if (li == base) {
+            w0 += c[0];
+            w1 += c[1];
+            w2 += c[2];
+            w3 += c[3];
+        } else {
+            w1 += c[0];
+            w2 += c[1];
+            w3 += c[2];
+            w4 += c[3];
+        }
+    }
+    flush();
 }
 
 // Bits lowpos .. lowpos + 63 of normalised 32-bit limbs (lowpos >= 0).
@@ -952,10 +999,8 @@ __device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, dou
     }
     __syncthreads();
     const int kref = (int)s_l[0];
-    for (int k = tid; k < nbins; k += blockDim.x) {
-        const int h = hist[k];
-        if (h > 0) exact_add(s_acc, (uint32_t)h, wtab[k >= kref ? k - kref : kref - k]);
-    }
+    const int per = (nbins + (int)blockDim.x - 1) / (int)blockDim.x;  // a contiguous range of bins per thread
+    exact_add_range(s_acc, hist, wtab, kref, min(nbins, tid * per), min(nbins, (tid + 1) * per));
     __syncthreads();
     if (tid == 0) {
         const double S = exact_round(s_acc);
@@ -1058,9 +1103,12 @@ __device__ __forceinline__ void counts_body(int chunk, const int32_t *E, int two
 
 // One block (chunk of nchunks): block offsets, new size (capacity check),
 // parent map; the chunks also clear the histogram for the next sweep.
+// min_total: smallest valid number of children (1; 0 for one GPU's share of
+// a population spread over several, which may receive all its replicas from
+// the others).
 __device__ __forceinline__ void scatter_body(int chunk, int nchunks, const int32_t *counts, const int32_t *local_off,
                                              const int32_t *blocksum, int32_t *parent, int R_cap, int32_t *hist_zero,
-                                             int nbins, DevState *st, long long *s_l)
+                                             int nbins, DevState *st, long long *s_l, int min_total = 1)
 {
     if (st->err) return;
     const int R_prev = st->pop;
@@ -1073,7 +1121,7 @@ __device__ __forceinline__ void scatter_body(int chunk, int nchunks, const int32
     }
     tot = block_sum_ll(tot, s_l);
     off = block_sum_ll(off, s_l);
-    if (tot > R_cap || tot <= 0) {
+    if (tot > R_cap || tot < min_total) {
         if (chunk == 0 && threadIdx.x == 0) st->err = 2;  // PA_ERR_CAPACITY
         return;
     }

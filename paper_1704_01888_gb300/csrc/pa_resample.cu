@@ -58,10 +58,11 @@ __global__ void __launch_bounds__(kBlock) k_counts(const int32_t *E, int twoN, i
 
 __global__ void __launch_bounds__(kBlock) k_scatter(const int32_t *counts, const int32_t *local_off,
                                                     const int32_t *blocksum, int32_t *parent, int R_cap,
-                                                    int32_t *hist_zero, int nbins, DevState *st)
+                                                    int32_t *hist_zero, int nbins, DevState *st, int min_total)
 {
     __shared__ long long s_l[32];
-    dev::scatter_body(blockIdx.x, gridDim.x, counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st, s_l);
+    dev::scatter_body(blockIdx.x, gridDim.x, counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st, s_l,
+                      min_total);
 }
 
 // Small populations (R_cap <= kSmallResample replicas): the three resampling
@@ -90,7 +91,8 @@ __global__ void __launch_bounds__(kBlock) k_resample_small(const int32_t *hist, 
     }
     const int nb2 = nb > (nbins + kBlock - 1) / kBlock ? nb : (nbins + kBlock - 1) / kBlock;
     for (int chunk = 0; chunk < nb2; ++chunk) {
-        dev::scatter_body(chunk, nb2, counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st, s_l);
+        dev::scatter_body(chunk, nb2, counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st, s_l,
+                          R_prev_all > 0 ? 0 : 1);
         __syncthreads();
     }
 }
@@ -175,7 +177,8 @@ cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, do
     k_counts<<<nb, kBlock, 0, s>>>(E, nbins - 1, R_target, mode, step, stream_hi, k0, k1, wtab, counts, local_off,
                                    blocksum, st, j0);
     const int nb2 = nb > (nbins + kBlock - 1) / kBlock ? nb : (nbins + kBlock - 1) / kBlock;
-    k_scatter<<<nb2, kBlock, 0, s>>>(counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st);
+    k_scatter<<<nb2, kBlock, 0, s>>>(counts, local_off, blocksum, parent, R_cap, hist_zero, nbins, st,
+                                     R_prev_all > 0 ? 0 : 1);
     bump_launch_count(3);
     return cudaGetLastError();
 }

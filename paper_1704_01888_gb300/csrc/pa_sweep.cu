@@ -24,25 +24,32 @@ namespace {
 
 using KernelFnPtr = void (*)(const SweepArgs);
 
+// Group of the local slots [first, first + nrep).  A population spread over
+// several GPUs numbers its replicas by global slot (slot0 + local slot): the
+// group carries global slot numbers, for the random keys, and array bases
+// moved down by slot0, so that indexing by global slot lands on the local
+// entries (slot0 = 0 on one GPU).
 __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity, int first, int nrep)
 {
+    const size_t s0 = a.slot0;
+    const size_t RW = (size_t)replica_words(a.q, a.L);
     dev::Group G;
-    G.in = a.buf[parity];
-    G.out = a.gather ? a.buf[parity ^ 1] : a.buf[parity];
-    G.parent = a.parent;
-    G.anc_in = a.anc[parity];
+    G.in = a.buf[parity] - s0 * RW;
+    G.out = (a.gather ? a.buf[parity ^ 1] : a.buf[parity]) - s0 * RW;
+    G.parent = a.parent ? a.parent - s0 : nullptr;
+    G.anc_in = a.anc[parity] ? a.anc[parity] - s0 : nullptr;
     G.anc_out = a.gather ? a.anc[parity ^ 1] : a.anc[parity];
+    if (G.anc_out) G.anc_out -= s0;
     G.fam = a.fam;
-    G.E = a.E;
-    G.Mt = a.Mt;
+    G.E = a.E - s0;
+    G.Mt = a.Mt - s0;
     G.hist = a.hist;
-    G.first = first;
+    G.first = (int)a.slot0 + first;
     G.nrep = nrep;
     G.q = a.q;
     G.theta = a.theta;
     G.step = a.step;
     G.stream_hi = a.stream_hi;
-    G.slot0 = a.slot0;
     G.gather = a.gather != 0;
     G.write_back = a.gather || a.theta > 0;
     return G;
