@@ -401,19 +401,25 @@ pa_status pa_profile_read(pa_ctx *ctx, double *ms_out2, int64_t *launches_out2);
  * replicas.  Random numbers are keyed by global slot and global replica
  * index, and S is an exact sum of the histogram-weighted Boltzmann factors, so
  * any number of ranks gives the population, energies, estimators and ln Z of
- * one GPU (pa_init) bit for bit.  The caller moves data between the calls
- * (the library calls no collective):
+ * one GPU (pa_init) bit for bit.  A rank's children are placed by
+ * pa_shard_plan; it sends each other rank the runs of its children bound
+ * there (a run: consecutive children of one parent), as the parent replica
+ * with a child count, so it never sends more than its own replicas plus one
+ * run per destination, and the receiving rank's next sweep gathers its new
+ * replicas from the runs.  The caller moves data between the calls (the
+ * library calls no collective):
  *   pa_shard_init                                  (each rank)
  *   sum hist, sums, fam over ranks; pa_shard_finalize(beta_0)
  *   for each step i:
  *     pa_shard_counts(dbeta_i, i, &T)              (needs the summed hist)
  *     gather T of every rank into totals[world]
- *     pa_shard_pack(totals, send_counts, recv_counts)
- *     exchange: send[sum of send_counts before d ..][send_counts[d] replicas]
- *       to rank d; receive recv_counts[g] replicas from rank g into recv,
- *       sources in rank order (replica_words 32-bit words per replica, and
- *       send_anc -> recv_anc with families)
- *     pa_shard_accept; pa_sweep(beta_i, theta, i)
+ *     pa_shard_pack(totals, send_counts)           (runs for each rank)
+ *     exchange the counts: recv_counts[g] = rank g's send_counts[this rank]
+ *     exchange the runs: the send_counts[d] runs from entry sum_{d'<d}
+ *       send_counts[d'] of send (replica_words 32-bit words each), send_cnt
+ *       (one int32 each) and, with families, send_anc go to rank d; rank g's
+ *       runs arrive in recv, recv_cnt, recv_anc, sources in rank order
+ *     pa_shard_accept(recv_counts); pa_sweep(beta_i, theta, i)
  *     sum hist, sums, fam over ranks; pa_shard_finalize(beta_i)
  * Device buffers the caller reads or writes (owned by the context; recv and
  * recv_anc change with every step: query them after pa_shard_pack). */
@@ -421,10 +427,12 @@ typedef struct {
     int32_t *hist;          /* [n_bins] energy histogram (this rank's, to be summed in place) */
     int64_t *sums;          /* [4] sum E, sum E^2, sum Mt, near ties (this rank's, to be summed in place) */
     int32_t *fam;           /* [R] family counts (this rank's, to be summed); NULL without families */
-    uint32_t *send;         /* [capacity x replica_words] children packed by pa_shard_pack */
-    int32_t *send_anc;      /* [capacity] their family ids; NULL without families */
-    uint32_t *recv;         /* [capacity x replica_words] where this rank's new replicas arrive */
-    int32_t *recv_anc;      /* [capacity]; NULL without families */
+    uint32_t *send;         /* [capacity + world runs x replica_words] run parents packed by pa_shard_pack */
+    int32_t *send_anc;      /* their family ids; NULL without families */
+    int32_t *send_cnt;      /* their child counts */
+    uint32_t *recv;         /* [capacity runs x replica_words] where the runs for this rank arrive */
+    int32_t *recv_anc;      /* NULL without families */
+    int32_t *recv_cnt;      /* child counts of the received runs */
     int64_t replica_words;  /* 32-bit words per replica in the device layout */
     int64_t capacity;       /* replicas this rank can hold */
     int64_t n_bins;         /* 2N + 1 */
@@ -460,15 +468,20 @@ pa_status pa_shard_get_buffers(pa_ctx *ctx, pa_shard_buffers *out);
  * population stays at step i-1). */
 pa_status pa_shard_counts(pa_ctx *ctx, double dbeta, int32_t step, int64_t *local_total);
 
-/* Plans the exchange (pa_shard_plan with every rank's total) and enqueues the
- * packing of this rank's children, in new-slot order, into send / send_anc.
- * send_counts / recv_counts: host int64[world] (may be NULL).
+/* Plans the exchange (pa_shard_plan with every rank's total, host int64
+ * [world]) and packs, destination by destination, the runs of this rank's
+ * children into send / send_cnt / send_anc; synchronises and writes the
+ * number of runs for each rank into send_counts (host int64[world]).
  * PA_ERR_CAPACITY if the new local range exceeds the capacity. */
-pa_status pa_shard_pack(pa_ctx *ctx, const int64_t *totals, int64_t *send_counts, int64_t *recv_counts);
+pa_status pa_shard_pack(pa_ctx *ctx, const int64_t *totals, int64_t *send_counts);
 
-/* After the exchange has filled recv (and recv_anc): they become this rank's
- * population, global slots [lo, hi) of the plan; then call pa_sweep. */
-pa_status pa_shard_accept(pa_ctx *ctx);
+/* After the exchange has filled recv, recv_cnt (and recv_anc) with
+ * recv_counts[g] runs from each rank g (host int64[world]): the runs become
+ * the parents of this rank's new replicas, global slots [lo, hi) of the plan,
+ * which the next pa_sweep gathers.  PA_ERR_INVALID for counts that cannot
+ * fill the range (a device check of the child counts flags the same, reported
+ * by the next synchronising call). */
+pa_status pa_shard_accept(pa_ctx *ctx, const int64_t *recv_counts);
 
 /* Estimators of the step (Sec. 2 step 4) from the summed sums, family counts
  * and histogram; ln Z_i = ln Z_{i-1} + ln Q_i.  Read them with pa_observables. */

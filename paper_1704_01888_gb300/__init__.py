@@ -67,7 +67,8 @@ class RunDesc(ctypes.Structure):
 class ShardBuffers(ctypes.Structure):
     _fields_ = [
         ("hist", ctypes.c_void_p), ("sums", ctypes.c_void_p), ("fam", ctypes.c_void_p), ("send", ctypes.c_void_p),
-        ("send_anc", ctypes.c_void_p), ("recv", ctypes.c_void_p), ("recv_anc", ctypes.c_void_p),
+        ("send_anc", ctypes.c_void_p), ("send_cnt", ctypes.c_void_p), ("recv", ctypes.c_void_p),
+        ("recv_anc", ctypes.c_void_p), ("recv_cnt", ctypes.c_void_p),
         ("replica_words", ctypes.c_int64), ("capacity", ctypes.c_int64), ("n_bins", ctypes.c_int64),
     ]
 
@@ -114,8 +115,8 @@ def load_library(path: str | None = None):
         "pa_shard_init": ([ctypes.POINTER(Config), i32, i32, P, ctypes.POINTER(P)], st),
         "pa_shard_get_buffers": ([P, ctypes.POINTER(ShardBuffers)], st),
         "pa_shard_counts": ([P, f64, i32, P], st),
-        "pa_shard_pack": ([P, P, P, P], st),
-        "pa_shard_accept": ([P], st),
+        "pa_shard_pack": ([P, P, P], st),
+        "pa_shard_accept": ([P, P], st),
         "pa_shard_finalize": ([P, f64], st),
         "pa_shard_range": ([P, P, P, P], st),
         "pa_run": ([P, P, i32, i32, P, P, i32, P, i32], st),

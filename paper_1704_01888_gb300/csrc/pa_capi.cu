@@ -132,8 +132,14 @@ struct pa_ctx {
     int host_parity = 0;      // buffer holding the current population (the device's parity)
     int shard_stage = 0;      // kShard* below
     bool shard_resampled = false;
-    uint32_t *send = nullptr;
-    int32_t *send_anc = nullptr;
+    uint32_t *send = nullptr;   // runs sent to other ranks: parent replicas,
+    int32_t *send_anc = nullptr; // their family ids
+    int32_t *send_cnt = nullptr; // and child counts
+    int32_t *recv_cnt = nullptr; // child counts of the runs received
+    int32_t *headpos = nullptr;  // first child of each run
+    int32_t *bounds = nullptr;   // [world + 1] destination bounds in child order
+    long long *ent_before = nullptr; // [world + 1] runs before each destination
+    int n_runs = 0;
     cudaStream_t capture_stream = nullptr;  // private stream for graph capture
 
     // event timing (pa_profile)
@@ -266,8 +272,9 @@ void release(pa_ctx *c)
 {
     release_events(c);
     release_wtables(c);
-    if (c->send) cudaFree(c->send);
-    if (c->send_anc) cudaFree(c->send_anc);
+    void *shard_bufs[] = {c->send, c->send_anc, c->send_cnt, c->recv_cnt, c->headpos, c->bounds, c->ent_before};
+    for (void *p : shard_bufs)
+        if (p) cudaFree(p);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     void *ptrs[] = {c->spins[0], c->spins[1], c->anc[0], c->anc[1], c->E, c->Mt, c->hist, c->fam,
                     c->counts, c->local_off, c->blocksum, c->parent, c->acc, c->st, c->obs,
@@ -489,12 +496,15 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out, int ra
     if (e != cudaSuccess) return fail(cuda_fail(e));
 
     const size_t spin_bytes = (size_t)c->R_cap * pa::replica_bytes(g.q, g.L);
-    const int nb = (c->R_cap + 1023) / 1024;
+    // a shard's children (parent map, run scan) can number up to the whole
+    // population's capacity, its own replicas only up to its share
+    const int R_child = (int)R_cap;
+    const int nb = (R_child + 1023) / 1024;
     if ((s = dev_alloc(&c->spins[0], spin_bytes)) || (s = dev_alloc(&c->spins[1], spin_bytes)) ||
         (s = dev_alloc(&c->E, c->R_cap)) || (s = dev_alloc(&c->Mt, c->R_cap)) ||
         (s = dev_alloc(&c->hist, c->nbins)) || (s = dev_alloc(&c->counts, c->R_cap)) ||
-        (s = dev_alloc(&c->local_off, c->R_cap)) || (s = dev_alloc(&c->blocksum, nb)) ||
-        (s = dev_alloc(&c->parent, c->R_cap)) || (s = dev_alloc(&c->acc, 4)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
+        (s = dev_alloc(&c->local_off, R_child)) || (s = dev_alloc(&c->blocksum, nb)) ||
+        (s = dev_alloc(&c->parent, R_child)) || (s = dev_alloc(&c->acc, 4)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
         return fail(s);
     if (g.track_families) {
         if ((s = dev_alloc(&c->anc[0], c->R_cap)) || (s = dev_alloc(&c->anc[1], c->R_cap)) ||
@@ -502,8 +512,11 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out, int ra
             return fail(s);
     }
     if (c->shard) {
-        if ((s = dev_alloc(&c->send, spin_bytes / sizeof(uint32_t))) ||
-            (g.track_families && (s = dev_alloc(&c->send_anc, c->R_cap))))
+        const size_t runs = (size_t)c->R_cap + world;  // own replicas, plus one split run per destination
+        if ((s = dev_alloc(&c->send, runs * pa::replica_words(g.q, g.L))) ||
+            (g.track_families && (s = dev_alloc(&c->send_anc, runs))) || (s = dev_alloc(&c->send_cnt, runs)) ||
+            (s = dev_alloc(&c->recv_cnt, runs)) || (s = dev_alloc(&c->headpos, runs)) ||
+            (s = dev_alloc(&c->bounds, (size_t)world + 1)) || (s = dev_alloc(&c->ent_before, (size_t)world + 1)))
             return fail(s);
     }
     c->obs_cap = 1024;
@@ -757,13 +770,10 @@ pa_status pa_sweep(pa_ctx *c, double beta, int32_t theta, int32_t step)
         if (c->shard_stage == kShardAccepted ? step != c->pending_step
                                              : (c->shard_stage != kShardReady || step != c->step))
             return PA_ERR_STATE;
-        const int pending = c->pending_step;
-        c->pending_step = 0;  // the exchange has placed the new replicas: no gather
+        // after pa_shard_accept the sweep gathers the new replicas from the
+        // received runs
         pa_status s = enqueue_sweep(c, beta, theta, step);
-        if (s) {
-            c->pending_step = pending;
-            return s;
-        }
+        if (s) return s;
         c->shard_stage = kShardMeasured;
         return PA_OK;
     }
@@ -975,8 +985,10 @@ pa_status pa_shard_get_buffers(pa_ctx *c, pa_shard_buffers *out)
     out->fam = c->fam;
     out->send = c->send;
     out->send_anc = c->send_anc;
+    out->send_cnt = c->send_cnt;
     out->recv = c->spins[nxt];
     out->recv_anc = c->anc[nxt];
+    out->recv_cnt = c->recv_cnt;
     out->replica_words = pa::replica_words(c->cfg.q, c->cfg.L);
     out->capacity = c->R_cap;
     out->n_bins = c->nbins;
@@ -987,8 +999,10 @@ pa_status pa_shard_finalize(pa_ctx *c, double beta)
 {
     if (!c || !std::isfinite(beta)) return PA_ERR_INVALID;
     if (!c->shard || c->failed || c->shard_stage != kShardMeasured) return PA_ERR_STATE;
-    PA_CK(pa::launch_finalize(c->st, c->acc, c->fam, c->cfg.R, next_obs_slot(c), beta, c->cfg.q, c->N, 0,
-                              c->shard_resampled ? 1 : 0, c->stream, c->R_all));
+    const int gathered = c->shard_resampled ? 1 : 0;
+    PA_CK(pa::launch_finalize(c->st, c->acc, c->fam, c->cfg.R, next_obs_slot(c), beta, c->cfg.q, c->N, gathered,
+                              gathered, c->stream, c->R_all));
+    c->host_parity ^= gathered;  // the gathering sweep wrote the other buffer
     c->shard_resampled = false;
     c->shard_stage = kShardReady;
     return PA_OK;
@@ -1002,7 +1016,7 @@ pa_status pa_shard_counts(pa_ctx *c, double dbeta, int32_t step, int64_t *local_
     const double *wtab = nullptr;
     pa_status s = get_wtable(c, dbeta, &wtab);
     if (s) return s;
-    PA_CK(pa::launch_resample(c->hist, c->nbins, c->E, dbeta, c->cfg.R, c->R_cap, c->cfg.resample_mode, step,
+    PA_CK(pa::launch_resample(c->hist, c->nbins, c->E, dbeta, c->cfg.R, c->cfg.R_cap, c->cfg.resample_mode, step,
                               (uint32_t)c->cfg.stream << 24, c->k0, c->k1, wtab, c->counts, c->local_off,
                               c->blocksum, c->parent, c->hist, c->st, c->stream, c->slot0, c->R_all));
     pa::DevState h;
@@ -1028,18 +1042,38 @@ pa_status pa_shard_counts(pa_ctx *c, double dbeta, int32_t step, int64_t *local_
     return PA_OK;
 }
 
-pa_status pa_shard_pack(pa_ctx *c, const int64_t *totals, int64_t *send_counts, int64_t *recv_counts)
+pa_status pa_shard_pack(pa_ctx *c, const int64_t *totals, int64_t *send_counts)
 {
-    if (!c || !totals) return PA_ERR_INVALID;
+    if (!c || !totals || !send_counts) return PA_ERR_INVALID;
     if (!c->shard || c->failed || c->shard_stage != kShardCounted) return PA_ERR_STATE;
     if (totals[c->rank] != c->n_pack) return PA_ERR_INVALID;
     int64_t R_new = 0, lo = 0, hi = 0;
-    pa_status s = pa_shard_plan(totals, c->world, c->rank, &R_new, &lo, &hi, send_counts, recv_counts);
+    pa_status s = pa_shard_plan(totals, c->world, c->rank, &R_new, &lo, &hi, nullptr, nullptr);
     if (s) return s;
     if (hi - lo > c->R_cap || R_new > c->cfg.R_cap) return PA_ERR_CAPACITY;
+    // destination bounds in this rank's child order: its children are the new
+    // slots [O, O + T), rank d holds [floor(d R_new / world), ...)
+    int64_t O = 0;
+    for (int g = 0; g < c->rank; ++g) O += totals[g];
+    const int T = c->n_pack, G = c->world;
+    std::vector<int32_t> A((size_t)G + 1);
+    for (int d = 0; d <= G; ++d) {
+        const int64_t b = (int64_t)d * R_new / G - O;
+        A[d] = (int32_t)(b < 0 ? 0 : b > T ? T : b);
+    }
+    PA_CK(cudaMemcpyAsync(c->bounds, A.data(), sizeof(int32_t) * A.size(), cudaMemcpyHostToDevice, c->stream));
+    PA_CK(pa::launch_shard_runs(c->parent, T, c->bounds, G, c->local_off, c->blocksum, c->headpos, c->ent_before,
+                                c->stream));
+    std::vector<long long> ent((size_t)G + 1);
+    PA_CK(cudaMemcpyAsync(ent.data(), c->ent_before, sizeof(long long) * ent.size(), cudaMemcpyDeviceToHost,
+                          c->stream));
+    PA_CK(cudaStreamSynchronize(c->stream));
+    const long long E = ent[G];
+    if (E > (long long)c->R_cap + G) return PA_ERR_CAPACITY;
     PA_CK(pa::launch_shard_pack(c->spins[c->host_parity], c->cfg.track_families ? c->anc[c->host_parity] : nullptr,
-                                c->parent, c->n_pack, pa::replica_words(c->cfg.q, c->cfg.L), c->send,
-                                c->send_anc, c->stream));
+                                c->parent, c->headpos, (int)E, T, pa::replica_words(c->cfg.q, c->cfg.L), c->send,
+                                c->send_anc, c->send_cnt, c->stream));
+    for (int d = 0; d < G; ++d) send_counts[d] = ent[d + 1] - ent[d];
     c->slot0_next = (int)lo;
     c->n_next = (int)(hi - lo);
     c->R_all_next = (int)R_new;
@@ -1047,14 +1081,22 @@ pa_status pa_shard_pack(pa_ctx *c, const int64_t *totals, int64_t *send_counts, 
     return PA_OK;
 }
 
-pa_status pa_shard_accept(pa_ctx *c)
+pa_status pa_shard_accept(pa_ctx *c, const int64_t *recv_counts)
 {
-    if (!c) return PA_ERR_INVALID;
+    if (!c || !recv_counts) return PA_ERR_INVALID;
     if (!c->shard || c->failed || c->shard_stage != kShardPacked) return PA_ERR_STATE;
-    PA_CK(pa::launch_shard_accept(c->st, c->n_next, c->stream));
-    c->host_parity ^= 1;
+    int64_t n = 0;
+    for (int g = 0; g < c->world; ++g) {
+        if (recv_counts[g] < 0) return PA_ERR_INVALID;
+        n += recv_counts[g];
+    }
+    if (n > c->n_next) return PA_ERR_INVALID;  // every received run has at least one child here
+    PA_CK(pa::launch_shard_accept(c->st, c->recv_cnt, (int)n, c->n_next, c->R_cap, c->local_off, c->blocksum,
+                                  c->parent, c->hist, c->nbins, c->stream));
+    c->host_parity ^= 1;  // the received runs are the current buffer until the sweep gathers from them
     c->slot0 = c->slot0_next;
     c->R_all = c->R_all_next;
+    c->n_runs = (int)n;
     c->shard_resampled = true;
     c->shard_stage = kShardAccepted;
     return PA_OK;

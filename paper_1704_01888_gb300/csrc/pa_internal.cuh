@@ -127,13 +127,22 @@ cudaError_t launch_resample(const int32_t *hist, int nbins, const int32_t *E, do
 // R_all: size of the whole population when the sums cover several GPUs (0 otherwise).
 cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam, int R0, DevObs *obs,
                             double beta, int q, int N, int gathered, int resampled, cudaStream_t s, int R_all = 0);
-// A population spread over several GPUs: copies the n children of the
-// pending resample (parent map, new-slot order) out of `spins` / `anc` into
-// contiguous send buffers; and, once the exchange has delivered this GPU's
-// new replicas into the other buffer, makes them the current population.
-cudaError_t launch_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent, int n, int RW,
-                             uint32_t *send, int32_t *send_anc, cudaStream_t s);
-cudaError_t launch_shard_accept(DevState *st, int n_local, cudaStream_t s);
+// A population spread over several GPUs.  The T children of the pending
+// resample (parent map, new-slot order) go to destination d for c in
+// [A[d], A[d+1]); runs of one destination's children with one parent become
+// entries (headpos[e] = the run's first child, ent_before[d] = entries before
+// destination d); the pack copies each run's parent replica, family id and
+// child count into the send buffers.  Accepting the received runs makes their
+// buffer current and scans their counts into the parent map of the next
+// (gathering) sweep; the new size must equal n_expected.
+cudaError_t launch_shard_runs(const int32_t *parent, int T, const int32_t *A, int G, int32_t *local_off,
+                             int32_t *blocksum, int32_t *headpos, long long *ent_before, cudaStream_t s);
+cudaError_t launch_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent,
+                             const int32_t *headpos, int E, int T, int RW, uint32_t *send, int32_t *send_anc,
+                             int32_t *send_cnt, cudaStream_t s);
+cudaError_t launch_shard_accept(DevState *st, const int32_t *recv_cnt, int n_runs, int n_expected, int R_cap,
+                               int32_t *local_off, int32_t *blocksum, int32_t *parent, int32_t *hist_zero,
+                               int nbins, cudaStream_t s);
 cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count,
                                 cudaStream_t s);
 

@@ -106,30 +106,111 @@ __global__ void __launch_bounds__(kBlock) k_finalize(DevState *st, unsigned long
     dev::finalize_body(st, acc, fam, R0, obs, beta, q, N, gathered, resampled, s_d, s_l, R_all);
 }
 
-// Children of the pending resample, in new-slot order, copied out of the
-// current population for the exchange between GPUs (one uint4 per thread).
-__global__ void k_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent, int n, int RW,
-                             uint32_t *send, int32_t *send_anc)
+// ---- One GPU's share of a population spread over several ----------------
+// The children of the pending resample (c = 0..T-1 in new-slot order, parent
+// map `parent`) go to destination rank d for c in [A_d, A_{d+1}).  Each rank
+// sends, per destination, the runs of its children: a run is a maximal
+// stretch of one destination's children with one parent, sent as that parent
+// replica once with its child count, so a rank never sends more than its own
+// replicas plus one per destination.
+
+// Run heads: child c starts a run if it is a destination's first child or its
+// parent differs from child c-1's.  Block-local exclusive scan of the heads
+// (local_off[c] = -1 for children that are not heads).
+__global__ void __launch_bounds__(kBlock) k_shard_heads(const int32_t *parent, int T, const int32_t *A, int G,
+                                                        int32_t *local_off, int32_t *blocksum)
 {
-    const int U = RW / 4;
-    const long long total = (long long)n * U;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i / U), o = (int)(i - (long long)c * U);
-        const int p = parent[c];
-        reinterpret_cast<uint4 *>(send + (size_t)c * RW)[o] = reinterpret_cast<const uint4 *>(spins + (size_t)p * RW)[o];
-        if (o == 0 && send_anc) send_anc[c] = anc[p];
+    __shared__ int s_i[32];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int head = 0;
+    if (c < T) {
+        int lo = 0, hi = G;  // the largest d with A_d <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A[mid] <= c) lo = mid; else hi = mid - 1;
+        }
+        head = (c == 0 || A[lo] == c || parent[c] != parent[c - 1]) ? 1 : 0;
+    }
+    int total;
+    const int before = dev::block_exclusive_scan(head, s_i, &total);
+    if (c < T) local_off[c] = head ? before : -1;
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = total;
+}
+
+// Entry index of each run: headpos[e] = its first child.
+__global__ void __launch_bounds__(kBlock) k_shard_runs(int T, const int32_t *local_off, const int32_t *blocksum,
+                                                       int32_t *headpos)
+{
+    __shared__ long long s_l[32];
+    long long off = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) off += blocksum[b];
+    off = dev::block_sum_ll(off, s_l);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < T && local_off[c] >= 0) headpos[off + local_off[c]] = c;
+}
+
+// ent_before[d] = runs before destination d's first child (d = 0..G; the
+// last is the number of runs).
+__global__ void k_shard_run_bounds(int T, const int32_t *A, int G, const int32_t *local_off, const int32_t *blocksum,
+                                   long long *ent_before)
+{
+    for (int d = threadIdx.x; d <= G; d += blockDim.x) {
+        const int pos = A[d];
+        long long e = 0;
+        const int nb = pos < T ? pos / kBlock : (T + kBlock - 1) / kBlock;
+        for (int b = 0; b < nb; ++b) e += blocksum[b];
+        if (pos < T) e += local_off[pos];  // a destination's first child is a head
+        ent_before[d] = e;
     }
 }
 
-// The received replicas (in the buffer not holding the current population)
-// become the current population.
-__global__ void k_shard_accept(DevState *st, int n_local)
+// Run e: its parent replica, family id and number of children.
+__global__ void k_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent, const int32_t *headpos,
+                             int E, int T, int RW, uint32_t *send, int32_t *send_anc, int32_t *send_cnt)
+{
+    const int U = RW / 4;
+    const long long total = (long long)E * U;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(i / U), o = (int)(i - (long long)e * U);
+        const int c = headpos[e];
+        const int p = parent[c];
+        reinterpret_cast<uint4 *>(send + (size_t)e * RW)[o] = reinterpret_cast<const uint4 *>(spins + (size_t)p * RW)[o];
+        if (o == 0) {
+            send_cnt[e] = (e + 1 < E ? headpos[e + 1] : T) - c;
+            if (send_anc) send_anc[e] = anc[p];
+        }
+    }
+}
+
+// The received runs become the parents of this rank's new population: the
+// buffer they arrived in becomes the current one (the next sweep gathers
+// from it) and the run counts are scanned into a parent map by k_scatter.
+__global__ void k_shard_accept(DevState *st, int n_runs)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0 && !st->err) {
-        st->pop = n_local;
+        st->pop = n_runs;
         st->parity ^= 1;
     }
+}
+
+__global__ void __launch_bounds__(kBlock) k_shard_run_scan(const int32_t *cnt, int n, int32_t *local_off,
+                                                           int32_t *blocksum)
+{
+    __shared__ int s_i[32];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = j < n ? cnt[j] : 0;
+    int total;
+    const int before = dev::block_exclusive_scan(r, s_i, &total);
+    if (j < n) local_off[j] = before;
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = total;
+}
+
+// The new local size must be the plan's: anything else means an exchange
+// that did not deliver what the plan placed here.
+__global__ void k_shard_check(DevState *st, int expected)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !st->err && st->pop_next != expected) st->err = 1;  // PA_ERR_INVALID
 }
 
 __global__ void k_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, long long count)
@@ -191,26 +272,49 @@ cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam,
     return cudaGetLastError();
 }
 
-cudaError_t launch_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent, int n, int RW,
-                             uint32_t *send, int32_t *send_anc, cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    k_shard_pack<<<grid_for((long long)n * (RW / 4), 256), 256, 0, s>>>(spins, anc, parent, n, RW, send, send_anc);
-    bump_launch_count(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_shard_accept(DevState *st, int n_local, cudaStream_t s)
-{
-    k_shard_accept<<<1, 32, 0, s>>>(st, n_local);
-    bump_launch_count(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count, cudaStream_t s)
 {
     k_to_canonical<<<grid_for(count * L * L, 256), 256, 0, s>>>(spins, out, q, L, count);
     bump_launch_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_runs(const int32_t *parent, int T, const int32_t *A, int G, int32_t *local_off,
+                             int32_t *blocksum, int32_t *headpos, long long *ent_before, cudaStream_t s)
+{
+    const int nb = (T + kBlock - 1) / kBlock;
+    if (nb > 0) {
+        k_shard_heads<<<nb, kBlock, 0, s>>>(parent, T, A, G, local_off, blocksum);
+        k_shard_runs<<<nb, kBlock, 0, s>>>(T, local_off, blocksum, headpos);
+        bump_launch_count(2);
+    }
+    k_shard_run_bounds<<<1, 256, 0, s>>>(T, A, G, local_off, blocksum, ent_before);
+    bump_launch_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_pack(const uint32_t *spins, const int32_t *anc, const int32_t *parent,
+                             const int32_t *headpos, int E, int T, int RW, uint32_t *send, int32_t *send_anc,
+                             int32_t *send_cnt, cudaStream_t s)
+{
+    if (E <= 0) return cudaSuccess;
+    k_shard_pack<<<grid_for((long long)E * (RW / 4), 256), 256, 0, s>>>(spins, anc, parent, headpos, E, T, RW, send,
+                                                                        send_anc, send_cnt);
+    bump_launch_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_accept(DevState *st, const int32_t *recv_cnt, int n_runs, int n_expected, int R_cap,
+                               int32_t *local_off, int32_t *blocksum, int32_t *parent, int32_t *hist_zero,
+                               int nbins, cudaStream_t s)
+{
+    k_shard_accept<<<1, 32, 0, s>>>(st, n_runs);
+    const int nb = (n_runs + kBlock - 1) / kBlock;
+    if (nb > 0) k_shard_run_scan<<<nb, kBlock, 0, s>>>(recv_cnt, n_runs, local_off, blocksum);
+    k_scatter<<<nb > 0 ? nb : 1, kBlock, 0, s>>>(recv_cnt, local_off, blocksum, parent, R_cap, hist_zero, nbins, st,
+                                                 0);
+    k_shard_check<<<1, 32, 0, s>>>(st, n_expected);
+    bump_launch_count(nb > 0 ? 4 : 3);
     return cudaGetLastError();
 }
 

@@ -33,11 +33,14 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
 {
     const size_t s0 = a.slot0;
     const size_t RW = (size_t)replica_words(a.q, a.L);
+    // arrays indexed by slot move down by slot0; a gather's sources are indexed
+    // by the parent map's values, which are local
+    const size_t s_in = a.gather ? 0 : s0;
     dev::Group G;
-    G.in = a.buf[parity] - s0 * RW;
+    G.in = a.buf[parity] - s_in * RW;
     G.out = (a.gather ? a.buf[parity ^ 1] : a.buf[parity]) - s0 * RW;
     G.parent = a.parent ? a.parent - s0 : nullptr;
-    G.anc_in = a.anc[parity] ? a.anc[parity] - s0 : nullptr;
+    G.anc_in = a.anc[parity] ? a.anc[parity] - s_in : nullptr;
     G.anc_out = a.gather ? a.anc[parity ^ 1] : a.anc[parity];
     if (G.anc_out) G.anc_out -= s0;
     G.fam = a.fam;

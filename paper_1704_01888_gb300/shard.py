@@ -9,10 +9,12 @@ contiguous range of global slots; per step it
      same exact S, ln Q_i and copy numbers of its own replicas),
   2. gathers the ranks' child totals, from which pa_shard_plan places every
      child's new global slot,
-  3. moves the children whose new slot lies on another rank with one
-     all-to-all exchange (in new-slot order),
-  4. sweeps its new replicas (random numbers keyed by global slot) and sums
-     the measurement sums, family counts and histogram over the ranks.
+  3. sends each rank the runs of its children placed there (a run: the
+     consecutive children of one parent, sent as the parent replica and a
+     child count) with one all-to-all exchange in new-slot order,
+  4. sweeps its new replicas, gathered from the received runs (random numbers
+     keyed by global slot), and sums the measurement sums, family counts and
+     histogram over the ranks.
 
 The library does the arithmetic (include/pa.h, pa_shard_*); this module only
 moves buffers between ranks through a communicator:
@@ -77,6 +79,15 @@ class TorchComm:
         self.dist.all_to_all_single(out, inp, [int(x) for x in out_splits], [int(x) for x in in_splits],
                                     group=self.group)
 
+    def all_to_all_counts(self, counts) -> list:
+        """counts[d] goes to rank d; returns what each rank sent here."""
+        import torch
+
+        t = torch.tensor([int(x) for x in counts], dtype=torch.int64, device="cuda")
+        out = torch.empty_like(t)
+        self.dist.all_to_all_single(out, t, group=self.group)
+        return [int(x) for x in out.tolist()]
+
 
 class ThreadComm:
     """`world` ranks as threads of one process on one GPU.  All ranks enqueue
@@ -117,6 +128,10 @@ class ThreadComm:
 
     def allgather_int(self, value: int) -> list:
         return [int(v) for v in self._meet(int(value))]
+
+    def all_to_all_counts(self, counts) -> list:
+        got = self._meet([int(x) for x in counts])
+        return [row[self.rank] for row in got]
 
     def all_to_all(self, out, inp, out_splits, in_splits):
         import torch
@@ -189,18 +204,18 @@ class ShardedPopulation:
         _check(self.lib.pa_shard_counts(self._ctx, dbeta, step, ctypes.byref(T)), "pa_shard_counts")
         totals = np.ascontiguousarray(self.comm.allgather_int(T.value), dtype=np.int64)
         send = np.zeros(self.comm.world, dtype=np.int64)
-        recv = np.zeros(self.comm.world, dtype=np.int64)
         _check(self.lib.pa_shard_pack(self._ctx, totals.ctypes.data_as(ctypes.c_void_p),
-                                      send.ctypes.data_as(ctypes.c_void_p), recv.ctypes.data_as(ctypes.c_void_p)),
-               "pa_shard_pack")
+                                      send.ctypes.data_as(ctypes.c_void_p)), "pa_shard_pack")
+        recv = np.ascontiguousarray(self.comm.all_to_all_counts(send), dtype=np.int64)
         b = self._buffers()
         RW = int(b.replica_words)
-        self.comm.all_to_all(_view(b.recv, int(recv.sum()) * RW, torch.int32),
-                             _view(b.send, int(send.sum()) * RW, torch.int32), recv * RW, send * RW)
+        ns, nr = int(send.sum()), int(recv.sum())
+        self.comm.all_to_all(_view(b.recv, nr * RW, torch.int32), _view(b.send, ns * RW, torch.int32), recv * RW,
+                             send * RW)
+        self.comm.all_to_all(_view(b.recv_cnt, nr, torch.int32), _view(b.send_cnt, ns, torch.int32), recv, send)
         if self.params.track_families:
-            self.comm.all_to_all(_view(b.recv_anc, int(recv.sum()), torch.int32),
-                                 _view(b.send_anc, int(send.sum()), torch.int32), recv, send)
-        _check(self.lib.pa_shard_accept(self._ctx), "pa_shard_accept")
+            self.comm.all_to_all(_view(b.recv_anc, nr, torch.int32), _view(b.send_anc, ns, torch.int32), recv, send)
+        _check(self.lib.pa_shard_accept(self._ctx, recv.ctypes.data_as(ctypes.c_void_p)), "pa_shard_accept")
         _check(self.lib.pa_sweep(self._ctx, float(beta), int(theta), step), "pa_sweep")
         self._finish(beta)
         self.step_index = step

@@ -74,8 +74,9 @@ def _free_port():
 
 def _rank_main(rank, world, port, q, L, R, seed, theta, betas, result_path):
     """One CPU rank: its slice of the population, resampled from the whole
-    population's energies, exchanged over gloo by the library's plan, swept by
-    the oracle with global slot keys."""
+    population's energies, its children sent over gloo as runs (parent
+    replica and child count) placed by the library's plan, swept by the
+    oracle with global slot keys."""
     import sys
 
     sys.path.insert(0, ROOT)
@@ -108,14 +109,35 @@ def _rank_main(rank, world, port, q, L, R, seed, theta, betas, result_path):
         totals = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
         dist.all_gather(totals, T)
         totals = [int(t.item()) for t in totals]
-        Rn, lo2, hi2, send, recv = pa.shard_plan(totals, world, rank)
+        Rn, lo2, hi2, send_children, recv_children = pa.shard_plan(totals, world, rank)
         assert Rn == R_new
-        children = spins[np.repeat(np.arange(hi - lo), r[lo:hi])]
+        # runs of this rank's children for each destination (consecutive
+        # children of one parent), sent as the parent replica and a count
+        parent_of = np.repeat(np.arange(hi - lo), r[lo:hi])
+        O = sum(totals[:rank])
+        bounds = [min(max(pa.shard_plan(totals, world, d)[1] - O, 0), len(parent_of)) for d in range(world)]
+        bounds.append(len(parent_of))
+        run_parent, run_count, send = [], [], []
+        for d in range(world):
+            seg = parent_of[bounds[d]:bounds[d + 1]]
+            heads = np.flatnonzero(np.diff(seg, prepend=-1) != 0)
+            run_parent.append(seg[heads])
+            run_count.append(np.diff(np.append(heads, seg.size)))
+            send.append(heads.size)
+            assert run_count[-1].sum() == send_children[d]
+        run_parent, run_count = np.concatenate(run_parent), np.concatenate(run_count).astype(np.int32)
+        recv = torch.zeros(world, dtype=torch.int64)
+        dist.all_to_all_single(recv, torch.tensor(send, dtype=torch.int64))
+        recv = recv.tolist()
         words = N // 4
-        out = torch.zeros(int(recv.sum()) * words, dtype=torch.int32)
-        inp = torch.from_numpy(np.ascontiguousarray(children).view(np.int32).reshape(-1).copy())
-        dist.all_to_all_single(out, inp, [int(x) * words for x in recv], [int(x) * words for x in send])
-        spins = out.numpy().view(np.uint8).reshape(-1, L, L).copy()
+        out = torch.zeros(sum(recv) * words, dtype=torch.int32)
+        inp = torch.from_numpy(np.ascontiguousarray(spins[run_parent]).view(np.int32).reshape(-1).copy())
+        dist.all_to_all_single(out, inp, [x * words for x in recv], [x * words for x in send])
+        cnt = torch.zeros(sum(recv), dtype=torch.int32)
+        dist.all_to_all_single(cnt, torch.from_numpy(run_count), recv, send)
+        runs = out.numpy().view(np.uint8).reshape(-1, L, L)
+        spins = np.repeat(runs, cnt.numpy(), axis=0).copy()
+        assert spins.shape[0] == hi2 - lo2 == recv_children.sum()
         lo, hi = lo2, hi2
         spins = np.array([oracle.sweep_replica(q, s, betas[i], theta, i, lo + k, seed) for k, s in enumerate(spins)],
                          dtype=np.uint8).reshape(-1, L, L)
@@ -132,19 +154,21 @@ def _rank_main(rank, world, port, q, L, R, seed, theta, betas, result_path):
     dist.destroy_process_group()
 
 
-def test_two_cpu_ranks_reproduce_the_single_population_run(tmp_path):
-    """world_size 2 over gloo: the gathered population, the integer sums and
-    ln Z equal the oracle's unsharded run bit for bit (ln Z exactly: both sum
-    the same ln Q values in the same order)."""
+@pytest.mark.parametrize("world,K", [(2, 6), (3, 3)])
+def test_cpu_ranks_reproduce_the_single_population_run(tmp_path, world, K):
+    """world_size 2 (and 3, with steps large enough that a few replicas take
+    most children, whose runs then span several ranks) over gloo: the gathered
+    population, the integer sums and ln Z equal the oracle's unsharded run bit
+    for bit (ln Z exactly: both sum the same ln Q values in the same order)."""
     _pa()
     import oracle
     import torch.multiprocessing as mp
 
-    q, L, R, seed, theta, K = 6, 8, 300, 5, 2, 6
+    q, L, R, seed, theta = 6, 8, 300, 5, 2
     betas = np.linspace(0.0, 1.2, K + 1)
     path = str(tmp_path / "shard.npz")
     port = _free_port()
-    mp.start_processes(_rank_main, args=(2, port, q, L, R, seed, theta, betas, path), nprocs=2, join=True,
+    mp.start_processes(_rank_main, args=(world, port, q, L, R, seed, theta, betas, path), nprocs=world, join=True,
                        start_method="spawn")
     got = np.load(path, allow_pickle=True)
     ref = oracle.run(q, L, R, seed, theta, betas)
