@@ -95,3 +95,34 @@ def widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, e_bin: int = 4, m_bins
     counts = np.bincount((Mt - lo) // width)
     centres = magnetisation(q, N, lo + width * np.arange(counts.size) + (width - 1) / 2.0)
     return fwhm(x, h), fwhm(centres, counts)
+
+
+def crossings(x: np.ndarray, f: np.ndarray, g: np.ndarray, window: int = 6):
+    """Every change of sign of d = f - g as (x_cross, score), x_cross by
+    linear interpolation and score = the smaller of max |d| over the `window`
+    points before and after it: a crossing between two clearly separated
+    branches scores high, one in the noise where the branches coincide low."""
+    x = np.asarray(x, dtype=np.float64)
+    d = np.asarray(f, dtype=np.float64) - np.asarray(g, dtype=np.float64)
+    out = []
+    for i in range(d.size - 1):
+        if (d[i] > 0.0) != (d[i + 1] > 0.0):
+            xc = float(x[i] + d[i] * (x[i + 1] - x[i]) / (d[i] - d[i + 1]))
+            score = min(np.abs(d[max(0, i - window + 1): i + 1]).max(), np.abs(d[i + 1: i + 1 + window]).max())
+            out.append((xc, float(score)))
+    return out
+
+
+def crossing(x: np.ndarray, f: np.ndarray, g: np.ndarray):
+    """The x at which f - g changes sign (the first change of sign, located
+    by linear interpolation), or None.  Used for the free-energy branches of
+    cooling and heating runs (Sec. 6: -beta F = ln Z of the two branches
+    cross at the transition)."""
+    x = np.asarray(x, dtype=np.float64)
+    d = np.asarray(f, dtype=np.float64) - np.asarray(g, dtype=np.float64)
+    for i in range(d.size - 1):
+        if d[i] == 0.0:
+            return float(x[i])
+        if (d[i] > 0.0) != (d[i + 1] > 0.0):
+            return float(x[i] + d[i] * (x[i + 1] - x[i]) / (d[i] - d[i + 1]))
+    return None

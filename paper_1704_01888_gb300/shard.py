@@ -221,10 +221,31 @@ class ShardedPopulation:
         self.step_index = step
         self.beta = float(beta)
 
-    def observables(self) -> dict:
+    def observables(self, with_hist: bool = False):
+        """The step's estimators (the whole population's, on every rank), and
+        with_hist the whole population's energy histogram."""
         obs = Obs()
-        _check(self.lib.pa_observables(self._ctx, ctypes.byref(obs), None, 0), "pa_observables")
-        return obs.as_dict()
+        hist = np.zeros(2 * self.N + 1, dtype=np.int32) if with_hist else None
+        _check(self.lib.pa_observables(self._ctx, ctypes.byref(obs),
+                                       hist.ctypes.data_as(ctypes.c_void_p) if with_hist else None,
+                                       hist.size if with_hist else 0), "pa_observables")
+        return (obs.as_dict(), hist) if with_hist else obs.as_dict()
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.pa_profile(self._ctx, int(enable)), "pa_profile")
+
+    def profile_read(self):
+        """{"sweep": (ms, launches), ...}: event-timed sweep launches on this rank."""
+        ms = np.zeros(2, dtype=np.float64)
+        n = np.zeros(2, dtype=np.int64)
+        _check(self.lib.pa_profile_read(self._ctx, ms.ctypes.data_as(ctypes.c_void_p),
+                                        n.ctypes.data_as(ctypes.c_void_p)), "pa_profile_read")
+        return {"sweep": (float(ms[0]), int(n[0])), "resample": (float(ms[1]), int(n[1]))}
+
+    def launch_shape(self):
+        v = [ctypes.c_int32() for _ in range(3)]
+        _check(self.lib.pa_get_launch(self._ctx, *[ctypes.byref(x) for x in v]), "pa_get_launch")
+        return tuple(x.value for x in v)
 
     def history(self, count: int) -> list:
         recs = (Obs * count)()

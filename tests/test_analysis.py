@@ -61,3 +61,27 @@ def test_widths_of_gaussian_populations():
     c = 2 * math.sqrt(2 * math.log(2))
     assert we == pytest.approx(c * 40.0 / N, rel=0.05)
     assert wm == pytest.approx(c * 0.08, rel=0.05)
+
+
+def test_crossing_of_two_branches():
+    from paper_1704_01888_gb300 import analysis
+
+    x = np.linspace(0.0, 2.0, 21)
+    f = 1.0 - 0.5 * x          # crosses g at x = 4/3
+    g = 0.25 * x
+    assert analysis.crossing(x, f, g) == pytest.approx(4.0 / 3.0, rel=1e-12)
+    assert analysis.crossing(x, f + 10.0, g) is None
+    assert analysis.crossing(x, g, g) == 0.0
+
+
+def test_crossings_prefer_separated_branches():
+    from paper_1704_01888_gb300 import analysis
+
+    x = np.linspace(0.0, 3.0, 301)
+    noise = 1e-4 * np.sin(37.0 * x)                  # branches that coincide below x = 1
+    f = np.where(x < 1.0, noise, 0.3 * (2.0 - x) * (x - 1.0))
+    g = np.zeros_like(x)
+    cs = analysis.crossings(x, f, g)
+    best = max(cs, key=lambda c: c[1])
+    assert best[0] == pytest.approx(2.0, abs=0.01)
+    assert len(cs) > 3
