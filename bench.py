@@ -511,15 +511,15 @@ def _batched(pa):
 
 def _hist_report(hist, N, width=4):
     """Energy histogram per site in bins of `width` units: its occupied range,
-    counts, peaks (analysis.peaks) and whether it has two."""
+    counts, modes (analysis.modes) and whether it has two."""
     from paper_1704_01888_gb300 import analysis
 
     centres, counts = analysis.rebin_energy_histogram(hist, N, width)
     nz = np.flatnonzero(counts)
     lo, hi = int(nz[0]), int(nz[-1]) + 1
-    pk = analysis.peaks(counts)
+    md = analysis.modes(counts)
     return {"bin_width": width, "e_first_bin": float(centres[lo]), "counts": [int(x) for x in counts[lo:hi]],
-            "peaks_e": [round(float(centres[k]), 5) for k in pk], "two_peaks": len(pk) >= 2,
+            "modes_e": [round(float(centres[k]), 5) for k in md], "two_peaks": len(md) >= 2,
             "fwhm_e": round(analysis.fwhm(centres[lo:hi], counts[lo:hi]), 6)}
 
 

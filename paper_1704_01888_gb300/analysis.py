@@ -67,6 +67,33 @@ def peaks(h: np.ndarray, min_separation: int = 2, rel_height: float = 0.2):
     return sorted(out)
 
 
+def modes(h: np.ndarray, smooth_frac: float = 0.03, rel_height: float = 0.1, min_dip: float = 0.25):
+    """The modes of a histogram, robust to bin-to-bin noise: the occupied
+    range is smoothed with a Gaussian of standard deviation smooth_frac of
+    its width (at least one bin); local maxima of the smoothed counts above
+    rel_height of the highest are candidates; two candidates are separate
+    modes when the smoothed counts between them dip below (1 - min_dip) of the
+    lower one (otherwise the lower is dropped).  Returns the mode indices (into
+    h) in ascending order: two or more mean coexisting phases (Sec. 4)."""
+    h = np.asarray(h, dtype=np.float64)
+    nz = np.flatnonzero(h > 0)
+    if nz.size == 0:
+        return []
+    lo, hi = int(nz[0]), int(nz[-1]) + 1
+    x = h[lo:hi]
+    sigma = max(1.0, smooth_frac * x.size)
+    r = int(np.ceil(3 * sigma))
+    k = np.exp(-0.5 * (np.arange(-r, r + 1) / sigma) ** 2)
+    sm = np.convolve(np.pad(x, r), k / k.sum(), mode="valid")
+    cand = [i for i in range(sm.size)
+            if sm[i] >= rel_height * sm.max() and (i == 0 or sm[i] > sm[i - 1]) and (i == sm.size - 1 or sm[i] >= sm[i + 1])]
+    kept = []
+    for i in sorted(cand, key=lambda c: -sm[c]):
+        if all(sm[min(i, j):max(i, j) + 1].min() <= (1.0 - min_dip) * min(sm[i], sm[j]) for j in kept):
+            kept.append(i)
+    return sorted(lo + i for i in kept)
+
+
 def magnetisation(q: int, N: int, Mt: np.ndarray) -> np.ndarray:
     """m_j = (q Mt_j / N - 1) / (q - 1), the magnetisation of Eq. 5 per replica."""
     return (q * np.asarray(Mt, dtype=np.float64) / N - 1.0) / (q - 1.0)

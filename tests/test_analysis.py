@@ -85,3 +85,18 @@ def test_crossings_prefer_separated_branches():
     best = max(cs, key=lambda c: c[1])
     assert best[0] == pytest.approx(2.0, abs=0.01)
     assert len(cs) > 3
+
+
+def test_modes_ignore_noise_and_find_two_phases():
+    from paper_1704_01888_gb300 import analysis
+
+    rng = np.random.default_rng(3)
+    x = np.arange(400)
+    one = rng.poisson(200 * np.exp(-0.5 * ((x - 200) / 30.0) ** 2))
+    assert len(analysis.modes(one)) == 1
+    two = rng.poisson(150 * np.exp(-0.5 * ((x - 120) / 20.0) ** 2) + 90 * np.exp(-0.5 * ((x - 290) / 25.0) ** 2))
+    m = analysis.modes(two)
+    assert len(m) == 2 and abs(m[0] - 120) < 8 and abs(m[1] - 290) < 10
+    # a shoulder without a dip is one mode
+    sh = 200 * np.exp(-0.5 * ((x - 200) / 30.0) ** 2) + 150 * np.exp(-0.5 * ((x - 240) / 30.0) ** 2)
+    assert len(analysis.modes(sh)) == 1
