@@ -41,8 +41,10 @@ UNIT = "attempts/ns"
 # planes.  The update is integer logic; its binding unit is the ALU pipe (it
 # executes every three-input logic operation); the 32 x 32 -> 64 bit products of
 # Philox run on the FMA-heavy pipe, which is not binding and is not counted:
-#   Philox4x32-10 words: B for the proposal, ACC_PLANES for the acceptance, a
-#     quarter call each (10 rounds x 2 three-input xors = 20 per call): 5 (B + ACC_PLANES);
+#   Philox4x32-10 words: B for the proposal, A for the acceptance, a quarter
+#     call each (10 rounds x 2 three-input xors = 20 per call): 5 (B + A);
+#     and the counter word of each acceptance call: A / 4;
+#   the fourth neighbour (the same-row word shifted by one column): B shifts;
 #   proposal s +- (1 + u) mod q: two ripple-carry adders over B and B + 1
 #     planes (3 per plane), the choice of result and its select: 7B + 4;
 #   dE class: eight B-plane equality tests, a carry-save count of the eight
@@ -50,21 +52,50 @@ UNIT = "attempts/ns"
 #   acceptance: per plane of v, the choice between the two threshold-bit
 #     selections by the class bit dE >= 3 (1; the selections themselves are
 #     multiply-adds on the FMA-heavy pipe) and the outcome and undecided
-#     updates (2): 3 ACC_PLANES;  merge of the accepted proposals: the mask of
-#     decided acceptances and B selects, B + 1.
-# ACC_PLANES = 6: a site's comparison of v with T ends at the first differing
-# bit (geometric with mean 2), and a word of 32 such sites needs the largest
-# of 32 such depths, about log2(32) + 1.3.
-ACC_PLANES = 6
+#     updates (2): 3A;  merge of the accepted proposals: the mask of decided
+#     acceptances and B selects, B + 1;
+#   the step's measurements (Eqs. 3, 5), shared by the 2 theta site-word
+#     updates of each word of a replica: four B-plane equality tests per
+#     colour-0 word for E (8B - 4 per pair of words) and one B-plane test per
+#     word and state for the largest occupation (2 q B per pair):
+#     (8B - 4 + 2qB) / (2 theta).
+# A = acceptance planes a word needs: a site's comparison of v with T ends at
+# its first differing bit, and the word draws whole Philox calls (four planes)
+# until its deepest site is decided.  Counted by the oracle on the at-scale
+# schedule (oracle/acceptance_planes.py -> profiles/acceptance_planes_q10-L64.txt):
+# 5.9 at steps 6-25, 7.5 at beta_t, 6.7 over the whole schedule; 6 where no
+# count exists.
+ACC_PLANES = 6.0
 
 
-def ops_per_word(q: int) -> int:
+def ops_per_word(q: int, A: float = ACC_PLANES, theta: int = 10) -> float:
     B = max(1, (q - 1).bit_length())
-    return 5 * (B + ACC_PLANES) + (7 * B + 4) + (8 * B + 17) + 3 * ACC_PLANES + B + 1
+    return (5 * (B + A) + A / 4 + B + (7 * B + 4) + (8 * B + 17) + 3 * A + B + 1
+            + (8 * B - 4 + 2 * q * B) / (2 * theta))
 
 
-def ops_per_attempt(q: int) -> float:
-    return ops_per_word(q) / 32.0
+def ops_per_attempt(q: int, A: float = ACC_PLANES, theta: int = 10) -> float:
+    return ops_per_word(q, A, theta) / 32.0
+
+
+def acceptance_planes(w, first: int, last: int):
+    """Mean counted acceptance planes per site word over steps first..last
+    of the workload's schedule (profiles/acceptance_planes_<case>.txt), or
+    (ACC_PLANES, None) where no count exists."""
+    path = os.path.join(ROOT, "profiles", f"acceptance_planes_q{w.q}-L{w.L}.txt")
+    try:
+        vals = []
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            i, _, a = line.split()[:3]
+            if first <= int(i) <= last:
+                vals.append(float(a))
+        if vals and w.theta == 10 and abs(w.beta_end - 1.6) < 1e-12 and w.K == 200:
+            return sum(vals) / len(vals), os.path.relpath(path, ROOT)
+    except OSError:
+        pass
+    return ACC_PLANES, None
 
 
 def replica_bytes(q: int, L: int) -> int:
@@ -375,7 +406,8 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peaks = _peaks()
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    opa = ops_per_attempt(w.q)
+    A, A_src = acceptance_planes(w, W + 1, min(W + K, w.K))
+    opa = ops_per_attempt(w.q, A, w.theta)
     achieved = opa * per_launch_attempts / sweep_avg_s / 1e12
     peak = sms * LANES_PER_SM_PER_CLK * f_max / 1e12
     rec = _sweep_record()
@@ -384,7 +416,8 @@ def run_ours(args):
                 "traffic": (rec["dram_bytes_per_replica"] * per_launch_replicas) if rec else None,
                 "traffic_unit": "bytes per launch (ncu dram read + write, scaled by replicas)",
                 "algorithmic_bytes_per_launch": 2 * replica_bytes(w.q, w.L) * per_launch_replicas,
-                "kernel": "k_sweep", "ops_per_attempt": opa, "acceptance_planes": ACC_PLANES,
+                "kernel": "k_sweep", "ops_per_attempt": opa, "acceptance_planes": A,
+                "acceptance_planes_source": A_src or "model value (no count for this workload)",
                 "kernel_ms_avg": sweep_avg_s * 1e3, "kernel_share": sweep_ms / elapsed_ms,
                 "peak_basis": f"ALU pipe: {sms} SMs x {LANES_PER_SM_PER_CLK} lanes x {f_max / 1e6:.0f} MHz "
                               f"(max SM clock), of measured clock"}

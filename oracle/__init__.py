@@ -75,6 +75,7 @@ def lib():
         L.orc_below_value.argtypes = [u32, u64]
         L.orc_below_value.restype = ctypes.c_int
         L.orc_sweep_replica.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, u32, u32, u64, u32]
+        L.orc_sweep_replica.restype = i64
         L.orc_init_random.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
         L.orc_init_ground.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, u64, u32, P]
         L.orc_copy_numbers.argtypes = [i64, P, f64, i64, ctypes.c_int, u32, u64, u32, P, P, P, P, P]
@@ -156,12 +157,13 @@ def metropolis_decide(q, cur, nb, sigma, u, v, T) -> int:
 
 
 def sweep_replica(q: int, spins: np.ndarray, beta: float, theta: int, step: int, slot: int, seed: int,
-                  stream: int = 0) -> np.ndarray:
-    """theta sweeps of one L x L replica; returns a new array."""
+                  stream: int = 0, with_calls: bool = False):
+    """theta sweeps of one L x L replica; returns a new array (and, with
+    with_calls, the number of Philox calls its site words drew)."""
     s = np.array(spins, dtype=np.uint8, copy=True, order="C")
     thr = thresholds(beta)
-    lib().orc_sweep_replica(q, s.shape[-1], _p(s), _p(thr), theta, step, slot, seed, stream)
-    return s
+    calls = lib().orc_sweep_replica(q, s.shape[-1], _p(s), _p(thr), theta, step, slot, seed, stream)
+    return (s, int(calls)) if with_calls else s
 
 
 def init_random(q: int, L: int, slot_begin: int, count: int, seed: int, stream: int = 0) -> np.ndarray:

@@ -336,18 +336,21 @@ static void orc_attempt(int q, int B, int L, uint8_t *s, int x, int y, struct or
     if (accept) s[y * L + x] = (uint8_t)prop;
 }
 
-/* theta checkerboard sweeps of one replica at the thresholds T.
+/* theta checkerboard sweeps of one replica at the thresholds T; returns the
+ * number of Philox calls drawn (a word draws its stream lazily, so this is
+ * the number its deepest site needed).
  * reading: one sweep updates the colour-0 sites ((x+y) even) and then the
  * colour-1 sites, each colour row by row and, within a row, by increasing x.
  * With L even no two sites of one colour are neighbours, so this in-place
  * order equals a simultaneous update of each colour.  (For odd L the order is
  * still a product of single-site Metropolis steps, each of which keeps the
  * Boltzmann distribution stationary.) */
-ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], int theta,
-                               uint32_t step, uint32_t slot, uint64_t seed, uint32_t stream)
+ORC_API int64_t orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], int theta,
+                                  uint32_t step, uint32_t slot, uint64_t seed, uint32_t stream)
 {
     int B = orc_state_bits(q);
     int words = orc_colour_words(L);
+    int64_t calls = 0; /* Philox calls the site words drew (each as many as its sites needed) */
     for (int k = 0; k < theta; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
             struct orc_word_stream st;
@@ -362,9 +365,11 @@ ORC_API void orc_sweep_replica(int q, int L, uint8_t *s, const uint64_t T[5], in
                     int x, y;
                     if (orc_word_site(L, colour, w, b, &x, &y)) orc_attempt(q, B, L, s, x, y, &st, b, T);
                 }
+                calls += st.have;
             }
         }
     }
+    return calls;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -65,9 +65,14 @@ def test_bench_helpers_and_global_names():
     assert bench.replica_bytes(2, 8) == 16        # 2 words padded to 4
     assert bench.replica_bytes(10, 48) == 1152    # banded: 36 words per colour
     assert bench.replica_bytes(10, 24) == 768     # padded rows: 24 words per colour
-    # q = 10 (B = 4), 6 acceptance planes: Philox 50, proposal 32, dE class 49,
-    # acceptance 18, merge 5
-    assert bench.ops_per_word(10) == 154
+    # q = 10 (B = 4), 6 acceptance planes, theta = 10: Philox 50 + 1.5 counter
+    # words, shift 4, proposal 32, dE class 49, acceptance 18, merge 5,
+    # measurements (28 + 80) / 20 = 5.4
+    assert bench.ops_per_word(10, 6.0, 10) == pytest.approx(164.9)
+    w = bench.wl.C2
+    A, src = bench.acceptance_planes(w, 6, 25)
+    assert src is not None and 5.5 < A < 6.5
+    assert bench.acceptance_planes(bench.wl.C5, 6, 25) == (bench.ACC_PLANES, None)
 
     missing = set()
 
