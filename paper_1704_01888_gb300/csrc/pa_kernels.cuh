@@ -900,27 +900,37 @@ __device__ __forceinline__ void exact_add_range(unsigned long long *acc, const i
         if (w4) atomicAdd(acc + base + 4, w4);
         w0 = w1 = w2 = w3 = w4 = 0ull;
     };
-    for (int k = k_begin; k < k_end; ++k) {
-        const int h = hist[k];
-        if (h <= 0) continue;
-        const double w = wtab[k >= kref ? k - kref : kref - k];
-        if (w == 0.0) continue;
-        uint32_t c[4];
-        const int li = exact_term((uint32_t)h, w, c);
-        if (li < base || li > base + 1) {
-            flush();
-            base = li > 0 ? li - 1 : 0;
+    // four bins at a time: their loads issue together
+    for (int k0 = k_begin; k0 < k_end; k0 += 4) {
+        int h[4];
+        double wk[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = k0 + i < k_end ? hist[k0 + i] : 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + i;
+            wk[i] = h[i] > 0 ? wtab[k >= kref ? k - kref : kref - k] : 0.0;
         }
-        if (li == base) {
-            w0 += c[0];
-            w1 += c[1];
-            w2 += c[2];
-            w3 += c[3];
-        } else {
-            w1 += c[0];
-            w2 += c[1];
-            w3 += c[2];
-            w4 += c[3];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (h[i] <= 0 || wk[i] == 0.0) continue;
+            uint32_t c[4];
+            const int li = exact_term((uint32_t)h[i], wk[i], c);
+            if (li < base || li > base + 1) {
+                flush();
+                base = li > 0 ? li - 1 : 0;
+            }
+            if (li == base) {
+                w0 += c[0];
+                w1 += c[1];
+                w2 += c[2];
+                w3 += c[3];
+            } else {
+                w1 += c[0];
+                w2 += c[1];
+                w3 += c[2];
+                w4 += c[3];
+            }
         }
     }
     flush();
@@ -976,6 +986,7 @@ __device__ __forceinline__ void weights_body(const int32_t *hist, int nbins, dou
     const int tid = threadIdx.x;
     // reference bin: lowest occupied for dbeta >= 0, highest for dbeta < 0
     long long best = dbeta >= 0.0 ? (long long)INT_MAX : -1;
+#pragma unroll 4
     for (int k = tid; k < nbins; k += blockDim.x) {
         if (hist[k] > 0) best = dbeta >= 0.0 ? min(best, (long long)k) : max(best, (long long)k);
     }
