@@ -28,6 +28,7 @@ def main(R=64, q=10, L=64, K=200, beta_end=1.6, theta=10, seed=1):
     betas = np.array([beta_end * i / K for i in range(K + 1)])
     spins = oracle.init_random(q, L, 0, R, seed)
     E = np.array([oracle.energy(s) for s in spins], dtype=np.int32)
+    print(f"# command: python oracle/acceptance_planes.py {R} > profiles/acceptance_planes_q{q}-L{L}.txt")
     print(f"# acceptance planes per site word, oracle count: q={q} L={L} R={R} (sample of the at-scale population)")
     print(f"# theta={theta}, beta 0 -> {beta_end} in {K} steps, nearest-integer resampling, seed {seed}")
     print("# step beta planes_per_word")
