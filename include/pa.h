@@ -308,9 +308,12 @@ pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream,
 
 /* Picks the sweep kernel's shared-memory budget per block (which sets the
  * replicas per block of every run) and threads per block by timing the first
- * temperature step for each candidate from the same initial populations, then
- * restarts from them.  Results are cached per batch shape for the process.
- * Only before pa_batch_run (PA_ERR_STATE after). */
+ * three temperature steps for each candidate from the same initial
+ * populations, then restarts from them.  Results are cached per GPU (name and
+ * SM count) and batch shape for the process and, when the environment
+ * variable PA_AUTOTUNE_CACHE names a file, in that file (one line per shape,
+ * appended), where later processes find them.  Only before pa_batch_run
+ * (PA_ERR_STATE after). */
 pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *threads_out);
 
 /* Sets the budget (bytes, >= the largest replica) and threads per block
@@ -352,13 +355,15 @@ void pa_batch_destroy(pa_batch *b);
  * run resumed with pa_load continues bit for bit as the uninterrupted run.
  * Synchronises.  PA_ERR_STATE with a resample pending or a failed context;
  * PA_ERR_INVALID if the file cannot be written.  Spins are stored in the
- * device layout (format version 3); files are read back by this library on
- * machines of the same byte order. */
+ * canonical layout [replica][y][x], one byte per spin (format version 4), so
+ * files do not depend on the device layout; integers and doubles are stored
+ * in the machine's byte order. */
 pa_status pa_save(pa_ctx *ctx, const char *path);
 
 /* Creates a context from a checkpoint written by pa_save (synchronises).
  * PA_ERR_INVALID for a missing, truncated or corrupted file (bad header,
- * sizes or checksum: checked before any device work); otherwise as pa_init. */
+ * version, sizes, checksum or a state outside 0..q-1: checked before any
+ * device work); otherwise as pa_init. */
 pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out);
 
 /* Releases the context and its device memory (synchronises its stream). */

@@ -12,6 +12,8 @@
 // configuration; block shapes chosen by the autotuner never change results.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -281,13 +283,54 @@ pa_status check_runs(const pa_batch *b)
 std::mutex g_tune_mutex;
 std::map<std::string, std::pair<int, int>> g_tune_cache;
 
+// The GPU (name and SM count) and the batch's shape: the key of a tuned launch.
 std::string tune_key(const pa_batch *b)
 {
     std::string k;
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+        k += std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "|";
     for (int m = 0; m < b->M; ++m)
         k += std::to_string(b->cfg[m].q) + "," + std::to_string(b->cfg[m].L) + "," + std::to_string(b->cfg[m].R) + "," +
              std::to_string(b->theta[m]) + ";";
     return k;
+}
+
+// Tuned launches kept across processes: the file named by PA_AUTOTUNE_CACHE
+// (unset: none), one line per tuned shape, "key<TAB>budget<TAB>threads".
+bool cache_file_lookup(const std::string &key, int *budget, int *threads)
+{
+    const char *path = std::getenv("PA_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    int c;
+    while (true) {
+        line.clear();
+        while ((c = std::fgetc(f)) != EOF && c != '\n') line.push_back((char)c);
+        const size_t t1 = line.find('\t'), t2 = line.rfind('\t');
+        if (t1 != std::string::npos && t2 != t1 && line.compare(0, t1, key) == 0 && t1 == key.size()) {
+            *budget = std::atoi(line.c_str() + t1 + 1);
+            *threads = std::atoi(line.c_str() + t2 + 1);
+            found = *budget > 0 && *threads > 0;  // the last line for a key wins
+        }
+        if (c == EOF) break;
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_file_store(const std::string &key, int budget, int threads)
+{
+    const char *path = std::getenv("PA_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s\t%d\t%d\n", key.c_str(), budget, threads);
+    std::fclose(f);
 }
 
 }  // namespace
@@ -552,6 +595,8 @@ pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *thre
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
+        int cb = 0, ct = 0;
+        if (it == g_tune_cache.end() && cache_file_lookup(key, &cb, &ct)) it = g_tune_cache.emplace(key, std::make_pair(cb, ct)).first;
         if (it != g_tune_cache.end()) {
             pa_status s = apply_launch(b, it->second.first, it->second.second);
             if (s) return s;
@@ -560,8 +605,11 @@ pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *thre
             return PA_OK;
         }
     }
-    // Each candidate times the first temperature step from the same initial
-    // populations (restarted between candidates); shapes never change results.
+    // Each candidate times the first kTuneSteps temperature steps from the same
+    // initial populations (restarted between candidates); shapes never change
+    // results.
+    constexpr int kTuneSteps = 3;
+    const int tune_steps = std::min(kTuneSteps, b->Kmax);
     const int budgets[] = {32768, 49152, 65536, 98304, 131072};
     const int thread_opts[] = {256, 512, 1024};
     cudaEvent_t e0, e1;
@@ -575,7 +623,8 @@ pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *thre
             pa_status s = enqueue_start(b);
             if (s) return s;
             PB_CK(cudaEventRecord(e0, b->stream));
-            if ((s = enqueue_step(b, b->stream))) return s;
+            for (int k = 0; k < tune_steps; ++k)
+                if ((s = enqueue_step(b, b->stream))) return s;
             PB_CK(cudaEventRecord(e1, b->stream));
             PB_CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -596,6 +645,7 @@ pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *thre
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = {best_budget, best_threads};
+        cache_file_store(key, best_budget, best_threads);
     }
     if (smem_budget_out) *smem_budget_out = best_budget;
     if (threads_out) *threads_out = best_threads;

@@ -539,7 +539,9 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out, int ra
 // Checkpoint file: a fixed header, the population's arrays, and an FNV-1a
 // checksum of everything before it.
 constexpr char kMagic[8] = {'P', 'A', 'G', 'B', '3', '0', '0', '\x01'};
-constexpr uint32_t kVersion = 3;  // 2: multi-spin-coded spin arrays; 3: banded rows at L = 48, 80, 96, ...
+// 4: spins in the canonical [replica][y][x] byte layout, independent of the
+// device layout (versions 2 and 3 stored the device layout)
+constexpr uint32_t kVersion = 4;
 
 struct CkptHeader {
     char magic[8];
@@ -606,12 +608,21 @@ pa_status pa_save(pa_ctx *c, const char *path)
     pa::DevState st;
     pa_status s = sync_state(c, &st);
     if (s) return s;
-    const size_t pop = (size_t)st.pop, RB = pa::replica_bytes(c->cfg.q, c->cfg.L);
+    const size_t pop = (size_t)st.pop, N = (size_t)c->N;
+    const size_t RW = (size_t)pa::replica_words(c->cfg.q, c->cfg.L);
     const bool fam = c->cfg.track_families != 0;
-    std::vector<unsigned char> payload(pop * RB + 4 * (2 * pop + (size_t)c->nbins + (fam ? pop : 0)));
+    std::vector<unsigned char> payload(pop * N + 4 * (2 * pop + (size_t)c->nbins + (fam ? pop : 0)));
     unsigned char *p = payload.data();
-    PA_CK(cudaMemcpy(p, c->spins[st.parity], pop * RB, cudaMemcpyDeviceToHost));
-    p += pop * RB;
+    // spins in the canonical layout, through the staging buffer
+    const size_t per = c->stage_bytes / N;
+    for (size_t done = 0; done < pop; done += per) {
+        const size_t n = pop - done < per ? pop - done : per;
+        PA_CK(pa::launch_to_canonical(c->spins[st.parity] + done * RW, c->stage, c->cfg.q, c->cfg.L, (int64_t)n,
+                                      c->stream));
+        PA_CK(cudaMemcpyAsync(p + done * N, c->stage, n * N, cudaMemcpyDeviceToHost, c->stream));
+        PA_CK(cudaStreamSynchronize(c->stream));
+    }
+    p += pop * N;
     PA_CK(cudaMemcpy(p, c->E, 4 * pop, cudaMemcpyDeviceToHost));
     p += 4 * pop;
     PA_CK(cudaMemcpy(p, c->Mt, 4 * pop, cudaMemcpyDeviceToHost));
@@ -666,12 +677,14 @@ pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out)
     if (check != sum) return PA_ERR_INVALID;
     if (h.cfg.q < 2 || h.cfg.q > 128 || h.cfg.L < 2 || h.cfg.L > 1024) return PA_ERR_INVALID;
     const size_t N = (size_t)h.cfg.L * h.cfg.L, pop = (size_t)h.pop;
-    const size_t RB = pa::replica_bytes(h.cfg.q, h.cfg.L);
+    const size_t RW = (size_t)pa::replica_words(h.cfg.q, h.cfg.L);
     const bool fam = h.cfg.track_families != 0;
     const size_t nbins = 2 * N + 1;
     if (h.pop < 1 || h.pop > h.cfg.R_cap || h.step < 0 ||
-        payload.size() != pop * RB + 4 * (2 * pop + nbins + (fam ? pop : 0)))
+        payload.size() != pop * N + 4 * (2 * pop + nbins + (fam ? pop : 0)))
         return PA_ERR_INVALID;
+    for (size_t k = 0; k < pop * N; ++k)
+        if (payload[k] >= (unsigned)h.cfg.q) return PA_ERR_INVALID;  // a state outside 0..q-1
     pa_ctx *c = nullptr;
     pa_status s = ctx_create(h.cfg, cuda_stream, &c);
     if (s) return s;
@@ -681,8 +694,16 @@ pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out)
         return e;
     };
     const unsigned char *p = payload.data();
-    cudaError_t e = cudaMemcpy(c->spins[0], p, pop * RB, cudaMemcpyHostToDevice);
-    p += pop * RB;
+    cudaError_t e = cudaSuccess;
+    const size_t per = c->stage_bytes / N;
+    for (size_t done = 0; done < pop && e == cudaSuccess; done += per) {
+        const size_t n = pop - done < per ? pop - done : per;
+        e = cudaMemcpy(c->stage, p + done * N, n * N, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = pa::launch_from_canonical(c->spins[0] + done * RW, c->stage, h.cfg.q, h.cfg.L, (int64_t)n, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    p += pop * N;
     if (e == cudaSuccess) e = cudaMemcpy(c->E, p, 4 * pop, cudaMemcpyHostToDevice);
     p += 4 * pop;
     if (e == cudaSuccess) e = cudaMemcpy(c->Mt, p, 4 * pop, cudaMemcpyHostToDevice);

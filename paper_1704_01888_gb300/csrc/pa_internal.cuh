@@ -145,6 +145,9 @@ cudaError_t launch_shard_accept(DevState *st, const int32_t *recv_cnt, int n_run
                                int nbins, cudaStream_t s);
 cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count,
                                 cudaStream_t s);
+// The inverse: count replicas [count][L][L] (one byte per spin) into the layout above.
+cudaError_t launch_from_canonical(uint32_t *spins, const uint8_t *canon, int q, int L, int64_t count,
+                                  cudaStream_t s);
 
 // Host: the thresholds of inverse temperature beta.
 Thresholds acceptance_thresholds(double beta);

@@ -814,6 +814,46 @@ __device__ __forceinline__ void init_item(uint32_t *spins, int32_t *anc, int q, 
     if (rem == 0 && anc) anc[slot] = (int32_t)key_slot;
 }
 
+// One site word (i indexes (slot, colour, word) as in init_item) of the
+// multi-spin-coded layout from a population in the canonical layout
+// [slot][y][x], one byte per spin (the inverse of canonical_state).
+__device__ __forceinline__ void from_canonical_item(uint32_t *spins, const uint8_t *canon, int q, int L, long long i)
+{
+    const int B = state_bits(q);
+    const int BP = plane_stride(B);
+    const int WPR = row_words(L);
+    const int nb_last = L / 2 - 32 * (WPR - 1);
+    const int IPC = colour_words(L);
+    const int IPR = 2 * IPC;
+    const long long slot = i / IPR;
+    const int rem = (int)(i - slot * IPR);
+    const int c = rem / IPC;
+    const int it = rem - c * IPC;
+    const bool packed = rows_packed(L), banded = rows_banded(L);
+    const int nb = (packed || banded) ? 32 : ((it % WPR) == WPR - 1 ? nb_last : 32);
+    const uint8_t *rep = canon + slot * (long long)L * L;
+    uint32_t planes[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (int b = 0; b < nb; ++b) {
+        int y, m;
+        if (packed) {
+            const int h = 32 * it + b;
+            y = h / (L / 2);
+            m = h - y * (L / 2);
+        } else if (banded) {
+            const int k = it / (L / 16);
+            y = k + (b >> 3) * (L / 4);
+            m = 8 * (it - k * (L / 16)) + (b & 7);
+        } else {
+            y = it / WPR;
+            m = 32 * (it - y * WPR) + b;
+        }
+        const uint32_t s = rep[y * L + 2 * m + ((y + c) & 1)];
+        for (int p = 0; p < B; ++p) planes[p] |= ((s >> p) & 1u) << b;
+    }
+    uint32_t *dst = spins + (size_t)slot * replica_words_of(B, L) + (size_t)rem * BP;
+    for (int p = 0; p < BP; ++p) dst[p] = planes[p];
+}
+
 // State of canonical site i (= r N + y L + x) of a multi-spin-coded population.
 __device__ __forceinline__ uint8_t canonical_state(const uint32_t *spins, int q, int L, long long i)
 {

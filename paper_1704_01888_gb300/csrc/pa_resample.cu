@@ -221,6 +221,14 @@ __global__ void k_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L
         out[i] = dev::canonical_state(spins, q, L, i);
 }
 
+__global__ void k_from_canonical(uint32_t *spins, const uint8_t *canon, int q, int L, long long count)
+{
+    const long long total = count * (2 * colour_words(L));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        dev::from_canonical_item(spins, canon, q, L, i);
+}
+
 int grid_for(long long work, int threads)
 {
     long long g = (work + threads - 1) / threads;
@@ -275,6 +283,14 @@ cudaError_t launch_finalize(DevState *st, unsigned long long *acc, int32_t *fam,
 cudaError_t launch_to_canonical(const uint32_t *spins, uint8_t *out, int q, int L, int64_t count, cudaStream_t s)
 {
     k_to_canonical<<<grid_for(count * L * L, 256), 256, 0, s>>>(spins, out, q, L, count);
+    bump_launch_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_canonical(uint32_t *spins, const uint8_t *canon, int q, int L, int64_t count,
+                                  cudaStream_t s)
+{
+    k_from_canonical<<<grid_for(count * 2 * colour_words(L), 256), 256, 0, s>>>(spins, canon, q, L, count);
     bump_launch_count(1);
     return cudaGetLastError();
 }

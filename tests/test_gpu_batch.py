@@ -113,3 +113,26 @@ def test_batched_configuration_first_steps_against_oracle():
             p, betas, theta = runs[m]
             lone, _ = _lone(p, betas, theta)
             assert [o["sumE"] for o in b.observables(m)] == [o["sumE"] for o in lone], m
+
+
+def test_autotune_file_cache(tmp_path, monkeypatch):
+    """The tuned launch of a batch shape is written to the file named by
+    PA_AUTOTUNE_CACHE and read back from it; tuning changes no result."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("PA_AUTOTUNE_CACHE", str(path))
+    runs = [(pa.PAParams(q=6, L=32, R=777, seed=4, stream=0), np.linspace(0.0, 1.0, 5), 2),
+            (pa.PAParams(q=10, L=16, R=555, seed=4, stream=1), np.linspace(0.0, 1.2, 7), 3)]
+    with pa.Batch(runs) as b:
+        budget, threads = b.autotune()
+        b.run()
+        tuned = [b.observables(m)[-1]["sumE"] for m in range(2)]
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].endswith(f"\t{budget}\t{threads}")
+    # a line for this shape with other values is taken by a later lookup (the
+    # process cache holds the first, so the file is read only by new processes:
+    # here through the same key in the file)
+    assert lines[0].split("\t")[0].count("|") == 1
+    with pa.Batch(runs) as b:
+        b.set_launch(32768, 256)
+        b.run()
+        assert [b.observables(m)[-1]["sumE"] for m in range(2)] == tuned

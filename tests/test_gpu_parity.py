@@ -322,6 +322,14 @@ def test_checkpoint_resume_is_bit_identical(tmp_path):
         pop.save(path)
         obs_ref, _ = pop.run(b[6:], 4)
         spins_ref, anc_ref = pop.spins(), pop.ancestors()
+    # spins are stored in the canonical layout right after the header
+    raw0 = open(path, "rb").read()
+    header_bytes = int.from_bytes(raw0[12:16], "little")
+    assert int.from_bytes(raw0[8:12], "little") == 4
+    with pa.Population(p) as pop3:
+        pop3.run(b[:7], 4)
+        canon = pop3.spins()
+    assert raw0[header_bytes: header_bytes + canon.size] == canon.tobytes()
     with pa.Population.load(path) as pop2:
         assert pop2.step == 6 and pop2.beta == b[6]
         obs, _ = pop2.run(b[6:], 4)
