@@ -227,7 +227,8 @@ class Clocks:
 
 def _sweep_sources() -> bytes:
     csrc = os.path.join(ROOT, "paper_1704_01888_gb300", "csrc")
-    return b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("pa_sweep.cu", "pa_kernels.cuh", "pa_internal.cuh"))
+    return b"".join(open(os.path.join(csrc, f), "rb").read()
+                    for f in ("pa_sweep.cu", "pa_sweep_body.cuh", "pa_internal.cuh"))
 
 
 def _sweep_record():

@@ -16,7 +16,7 @@
 // the acceptance by a most-significant-bit-first comparison of random bits
 // with the thresholds (the body is dev::sweep_group_bits).  One kernel is
 // compiled per B and row geometry.
-#include "pa_kernels.cuh"
+#include "pa_sweep_body.cuh"
 
 namespace pa {
 
