@@ -100,12 +100,12 @@ def acceptance_planes(w, first: int, last: int):
 
 def replica_bytes(q: int, L: int) -> int:
     """Device bytes of one replica: 2 colours x site words per colour x P planes
-    x 4 bytes, P = ceil(log2 q) rounded up to 1, 2, 4 or 8; a colour has
+    x 4 bytes, P = ceil(log2 q) rounded up to 1, 2 or 4 when at most 4; a colour has
     L^2 / 64 site words when L/2 divides 32 (rows packed) or when L is a
     multiple of 16 but not of 64 and L > 32 (banded segments), else
     L ceil(L/64)."""
     B = max(1, (q - 1).bit_length())
-    P = 1 if B <= 1 else 2 if B <= 2 else 4 if B <= 4 else 8
+    P = 1 if B <= 1 else 2 if B <= 2 else 4 if B <= 4 else B
     full = (L >= 8 and 64 % L == 0) or (L > 32 and L % 16 == 0 and L % 64 != 0)
     words = L * L // 64 if full else L * ((L + 63) // 64)
     return (2 * words * P + 3) // 4 * 4 * 4

@@ -123,13 +123,13 @@ typedef struct pa_ctx pa_ctx;
  * 0..255; PA_ERR_TOO_LARGE when a replica's bit planes exceed 204800 bytes
  * (a sweep block keeps whole lattices in shared memory).  Device layout of a
  * replica: a state takes B = ceil(log2 q) bits, stored as P bit planes (B
- * rounded up to 1, 2, 4 or 8); the sites of each colour ((x + y) mod 2) are
+ * rounded up to 1, 2 or 4 for B <= 4, else P = B); the sites of each colour ((x + y) mod 2) are
  * packed 32 to a 32-bit word per plane (row-major over the colour's sites
  * when L/2 divides 32; when L is a multiple of 16 but not of 64 and L > 32,
  * a word holds one 8-column segment of four rows L/4 apart; else each row is
  * padded to whole words), so a replica takes 2 W P 4 bytes, W = L^2/64 (the
- * first two cases) or L ceil(L/64) words per colour: L <= 640 for q <= 16
- * and L <= 448 for q <= 128.  PA_ERR_NOMEM or
+ * first two cases) or L ceil(L/64) words per colour: L <= 640 for q <= 16,
+ * 568 for q <= 32, 512 for q <= 64 and 456 for q <= 128.  PA_ERR_NOMEM or
  * PA_ERR_CUDA if allocation or a launch fails (nothing is leaked; *out = NULL). */
 pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 

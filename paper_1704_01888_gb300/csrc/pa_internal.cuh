@@ -4,7 +4,7 @@
 // Device layout of one replica (multi-spin coding).  A state 0..q-1 takes
 // B = ceil(log2 q) bits.  The sites of colour c = (x + y) & 1, with column index
 // m = x >> 1, are packed 32 to a "site word", stored as BP 32-bit planes (BP = B
-// rounded up to 1, 2, 4 or 8; plane p holds bit p of the states):
+// rounded up to 1, 2 or 4 for B <= 4, else B; plane p holds bit p of the states):
 //   word index (c * IPC + w) * BP + p,   IPC = site words per colour.
 // When L/2 divides 32 (L = 8, 16, 32, 64) the colour's sites in row-major order
 // h = y L/2 + m fill the words in turn (w = h >> 5, bit h & 31; IPC = L^2/64).
@@ -44,7 +44,7 @@ constexpr int kMaxLatticeBytes = 200 * 1024;
 // Bits per state, planes stored per site word, words per row of one colour,
 // words per replica (see the layout above).
 __host__ __device__ constexpr int state_bits(int q) { return q <= 2 ? 1 : q <= 4 ? 2 : q <= 8 ? 3 : q <= 16 ? 4 : q <= 32 ? 5 : q <= 64 ? 6 : 7; }
-__host__ __device__ constexpr int plane_stride(int B) { return B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8; }
+__host__ __device__ constexpr int plane_stride(int B) { return B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : B; }
 __host__ __device__ constexpr int row_words(int L) { return (L + 63) / 64; }
 // Rows packed several to a word: L/2 divides 32 (L = 8, 16, 32; at L = 64 both
 // layouts coincide).

@@ -22,17 +22,15 @@ namespace dev {
 // Bit-plane helpers
 // ===========================================================================
 
-// BP consecutive words (the planes of one site word) with one vector access.
+// BP consecutive words (the planes of one site word): one 16-byte access per
+// four planes (BP = 4: the site word's planes start on a 16-byte boundary),
+// 8-byte accesses for BP = 2 and 6, single words for BP = 1, 5 and 7 (a
+// warp's loads of one plane then fall in distinct banks: the words of
+// consecutive site words lie an odd number of words apart).
 template <int BP>
 __device__ __forceinline__ void load_planes(uint32_t (&v)[BP], const uint32_t *src)
 {
-    if constexpr (BP == 1) {
-        v[0] = src[0];
-    } else if constexpr (BP == 2) {
-        const uint2 a = *reinterpret_cast<const uint2 *>(src);
-        v[0] = a.x;
-        v[1] = a.y;
-    } else {
+    if constexpr (BP % 4 == 0) {
 #pragma unroll
         for (int h = 0; h < BP / 4; ++h) {
             const uint4 a = reinterpret_cast<const uint4 *>(src)[h];
@@ -41,20 +39,32 @@ __device__ __forceinline__ void load_planes(uint32_t (&v)[BP], const uint32_t *s
             v[4 * h + 2] = a.z;
             v[4 * h + 3] = a.w;
         }
+    } else if constexpr (BP % 2 == 0) {
+#pragma unroll
+        for (int h = 0; h < BP / 2; ++h) {
+            const uint2 a = reinterpret_cast<const uint2 *>(src)[h];
+            v[2 * h + 0] = a.x;
+            v[2 * h + 1] = a.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < BP; ++p) v[p] = src[p];
     }
 }
 
 template <int BP>
 __device__ __forceinline__ void store_planes(uint32_t *dst, const uint32_t (&v)[BP])
 {
-    if constexpr (BP == 1) {
-        dst[0] = v[0];
-    } else if constexpr (BP == 2) {
-        *reinterpret_cast<uint2 *>(dst) = make_uint2(v[0], v[1]);
-    } else {
+    if constexpr (BP % 4 == 0) {
 #pragma unroll
         for (int h = 0; h < BP / 4; ++h)
             reinterpret_cast<uint4 *>(dst)[h] = make_uint4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+    } else if constexpr (BP % 2 == 0) {
+#pragma unroll
+        for (int h = 0; h < BP / 2; ++h) reinterpret_cast<uint2 *>(dst)[h] = make_uint2(v[2 * h], v[2 * h + 1]);
+    } else {
+#pragma unroll
+        for (int p = 0; p < BP; ++p) dst[p] = v[p];
     }
 }
 

@@ -55,8 +55,9 @@ def test_status_strings_and_validation_without_gpu():
         assert lib.pa_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == pa.PA_ERR_INVALID
         assert not ctx.value
     # replicas whose bit planes exceed a block's shared memory (204800 bytes):
-    # q = 128 (8 planes) at L = 450, q = 10 (4 planes) at L = 642 and 1024
-    for q, L in ((128, 450), (10, 642), (10, 1024)):
+    # q = 128 (7 planes) at L = 458, q = 20 (5 planes) at L = 570, q = 10 (4
+    # planes) at L = 642 and 1024
+    for q, L in ((128, 458), (20, 570), (10, 642), (10, 1024)):
         cfg = pa.Config(q, L, 10, 0, 1, 0, 0, 0.0, 0, 0)
         assert lib.pa_init(ctypes.byref(cfg), None, ctypes.byref(ctx)) == pa.PA_ERR_TOO_LARGE
         assert not ctx.value

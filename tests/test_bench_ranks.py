@@ -61,7 +61,7 @@ def test_bench_helpers_and_global_names():
 
     assert bench.replica_bytes(10, 64) == 2048
     assert bench.replica_bytes(10, 16) == 128
-    assert bench.replica_bytes(20, 256) == 65536
+    assert bench.replica_bytes(20, 256) == 40960
     assert bench.replica_bytes(2, 8) == 16        # 2 words padded to 4
     assert bench.replica_bytes(10, 48) == 1152    # banded: 36 words per colour
     assert bench.replica_bytes(10, 24) == 768     # padded rows: 24 words per colour

@@ -9,11 +9,13 @@ pa_get_parents, pa_sweep) and checked against the oracle as it goes:
 * sweeps (Sec. 2 step 3): sampled slots of the new population are replayed by
   the oracle from their parents' spins of step i-1 (theta sweeps at beta_i,
   keyed by the slot) and must equal the GPU's spins and energies bit for bit;
+  at three steps of the plain case every slot is replayed;
 * measurements (Sec. 2 step 4, Eqs. 3-5): the histogram, the integer sums and
   (with families) the family ids and S_f against their definitions.
 
 The plain case at scale (q = 10, L = 64, R = 1e5, 200 steps, theta = 10)
-replays 64 slots at every step; the strong first-order case (q = 20, L = 256,
+replays 64 slots at every step and the whole population at steps 1, 100 and
+178 (beta_178 = 1.424, next to beta_t); the strong first-order case (q = 20, L = 256,
 R = 1e5, 300 steps, theta = 20) checks resampling and families at every step
 and replays slots at steps 1, 2 and around beta_t (267-269); the adaptive
 case (q = 8, L = 128, R = 2e5) checks the Newton step of each of its first 20
@@ -57,6 +59,18 @@ def _replay_one(args):
     return bool(np.array_equal(ref, child)) and orc.energy(ref) == E_child, slot
 
 
+def _replay_chunk(args):
+    q, par, beta, theta, step, slots, seed, child, E_child = args
+    import oracle as orc
+
+    bad = []
+    for k, s in enumerate(slots):
+        ref = orc.sweep_replica(q, par[k], beta, theta, step, int(s), seed)
+        if not (np.array_equal(ref, child[k]) and orc.energy(ref) == E_child[k]):
+            bad.append(int(s))
+    return bad
+
+
 class Replay:
     """Drives one run step by step and checks each step against the oracle."""
 
@@ -69,6 +83,7 @@ class Replay:
         self.jobs = []
         self.ties = 0
         self.steps = 0
+        self.full_replayed = 0
         self.pop = pa.Population(pa.PAParams(q=w.q, L=w.L, R=self.R, seed=w.seed,
                                              track_families=w.track_families))
         self.E = self.pop.energies()
@@ -77,7 +92,7 @@ class Replay:
     def close(self):
         self.pop.close()
 
-    def step(self, i, beta_prev, beta, replay_slots):
+    def step(self, i, beta_prev, beta, replay_slots, replay_all=False):
         w, pop = self.w, self.pop
         dbeta = beta - beta_prev
         lnq, R_i = pop.resample(dbeta, i, sync=True)
@@ -91,6 +106,7 @@ class Replay:
         if replay_slots:
             sample = np.unique(np.concatenate([self.rng.integers(0, R_i, self.n_slots), [0, R_i - 1]]))
             par_spins = {int(p): pop.spins(int(p), 1)[0] for p in np.unique(parents[sample])}
+        par_all = pop.spins(0, self.E.size) if replay_all else None
         pop.sweep(beta, w.theta, i)
         obs, hist = pop.observables(with_hist=True)
         E = pop.energies()
@@ -110,6 +126,14 @@ class Replay:
             s = int(s)
             self.jobs.append((w.q, par_spins[int(parents[s])], beta, w.theta, i, s, w.seed, pop.spins(s, 1)[0],
                               int(E[s])))
+        if replay_all:
+            child_all = pop.spins(0, R_i)
+            chunk = 500
+            jobs = ((w.q, par_all[parents[a:a + chunk]], beta, w.theta, i, np.arange(a, min(a + chunk, R_i)), w.seed,
+                     child_all[a:a + chunk], E[a:a + chunk]) for a in range(0, R_i, chunk))
+            bad = [s for b in self.pool.imap_unordered(_replay_chunk, jobs) for s in b]
+            assert not bad, (i, bad[:10])
+            self.full_replayed += R_i
         self.ties += int(ties.sum())
         self.steps += 1
         self.E = E
@@ -129,10 +153,11 @@ def test_plain_at_scale_every_step(pool):
     w = wl.C2
     b = w.betas()
     rp = Replay(w, pool)
+    full_steps = (1, 100, w.hist_steps[0])
     try:
         replayed = 0
         for i in range(1, w.K + 1):
-            obs, hist = rp.step(i, b[i - 1], b[i], replay_slots=True)
+            obs, hist = rp.step(i, b[i - 1], b[i], replay_slots=True, replay_all=i in full_steps)
             if i % 20 == 0:
                 replayed += rp.check_sweeps()
             if i == w.hist_steps[0]:
@@ -141,8 +166,9 @@ def test_plain_at_scale_every_step(pool):
         replayed += rp.check_sweeps()
     finally:
         rp.close()
-    assert rp.steps == w.K and replayed >= 64 * w.K
-    print(f"c2: {rp.steps} steps, {replayed} replayed slots, {rp.ties} flagged near ties")
+    assert rp.steps == w.K and replayed >= 64 * w.K and rp.full_replayed > 0.99 * len(full_steps) * w.R
+    print(f"c2: {rp.steps} steps, {replayed} sampled and {rp.full_replayed} whole-population replayed slots, "
+          f"{rp.ties} flagged near ties")
 
 
 def test_strong_first_order_every_resample_and_steps_near_beta_t(pool):
