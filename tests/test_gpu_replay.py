@@ -19,7 +19,8 @@ replays 64 slots at every step and the whole population at steps 1, 100 and
 R = 1e5, 300 steps, theta = 20) checks resampling and families at every step
 and replays slots at steps 1, 2 and around beta_t (267-269); the adaptive
 case (q = 8, L = 128, R = 2e5) checks the Newton step of each of its first 20
-steps against the oracle's on the same energies.
+steps against the oracle's on the same energies and replays the whole
+population of step 20.
 """
 import math
 import multiprocessing as mp
@@ -193,7 +194,7 @@ def test_strong_first_order_every_resample_and_steps_near_beta_t(pool):
 def test_adaptive_first_steps_at_full_size(pool):
     """q = 8, L = 128, R = 2e5, theta = 10, overlap 0.85: the Newton step of
     each of the first 20 steps equals the oracle's on the GPU's energies, and
-    each step is checked as above."""
+    each step is checked as above (every slot at step 20)."""
     w = wl.C4
     rp = Replay(w, pool, n_slots=16)
     try:
@@ -205,9 +206,11 @@ def test_adaptive_first_steps_at_full_size(pool):
             assert dbeta == dref, (i, dbeta, dref)
             a, _ = oracle.overlap(rp.E, dbeta)
             assert abs(a - 0.85) < 1e-4 or dbeta == cap
-            rp.step(i, beta, beta + dbeta, replay_slots=i in (1, 10, 20))
+            rp.step(i, beta, beta + dbeta, replay_slots=i in (1, 10, 20), replay_all=i == 20)
             beta += dbeta
         rp.check_sweeps()
     finally:
         rp.close()
-    print(f"c4: 20 adaptive steps to beta = {beta:.6f}, {rp.ties} flagged near ties")
+    assert rp.full_replayed > 0.99 * w.R
+    print(f"c4: 20 adaptive steps to beta = {beta:.6f}, {rp.full_replayed} slots replayed at step 20, "
+          f"{rp.ties} flagged near ties")
