@@ -432,7 +432,8 @@ def run_ours(args):
         e2e = _e2e(pa, w, params, betas, W, K, world, launch, Steps)
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if world == 1 and not args.no_cpu:
+        # the oracle on the host cores: one GPU only (a multi-GPU run reports the GPUs alone)
         cpu = _cpu_baseline(w)
 
     extras = {}
