@@ -438,12 +438,21 @@ def run_ours(args):
 
     extras = {}
     if world == 1 and not args.no_extras and not args.R:
-        extras["batched"] = _batched(pa)
-        cool = _observables_c2(pa)
-        extras["observables_c2"] = cool
-        extras["cooling_heating_crossing"] = _crossing(pa, cool.pop("_lnZ"))
-        extras["strong_first_order"] = _observables_c5(pa)
-        extras["adaptive"] = _adaptive(pa)
+        # measured after the timed region; one that fails is reported as such
+        # and does not take the headline line with it
+        def extra(name, fn, *a):
+            try:
+                extras[name] = fn(*a)
+            except Exception as exc:  # noqa: BLE001
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            return extras[name]
+
+        extra("batched", _batched, pa)
+        cool = extra("observables_c2", _observables_c2, pa)
+        if "_lnZ" in cool:
+            extra("cooling_heating_crossing", _crossing, pa, cool.pop("_lnZ"))
+        extra("strong_first_order", _observables_c5, pa)
+        extra("adaptive", _adaptive, pa)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
