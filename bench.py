@@ -231,10 +231,11 @@ def _sweep_sources() -> bytes:
                     for f in ("pa_sweep.cu", "pa_sweep_body.cuh", "pa_internal.cuh"))
 
 
-def _sweep_record():
+def _sweep_record(w):
     """The sweep kernel's ncu record (profiles/sweep_traffic.txt): DRAM bytes
-    per replica per launch and the issue activity, valid only while the
-    sweep kernel's sources hash to the recorded value."""
+    per replica per launch and the issue activity, valid only for the
+    workload's (q, L) it was taken on and while the sweep kernel's sources
+    hash to the recorded value."""
     rec = {}
     try:
         for line in open(os.path.join(ROOT, "profiles", "sweep_traffic.txt")):
@@ -245,6 +246,8 @@ def _sweep_record():
     except OSError:
         return None
     if rec.get("source_sha256") != hashlib.sha256(_sweep_sources()).hexdigest():
+        return None
+    if rec.get("case") != f"q{w.q}-L{w.L}":
         return None
     out = {"dram_bytes_per_replica": float(rec["dram_bytes_per_replica"])}
     if "issue_active" in rec:
@@ -411,7 +414,7 @@ def run_ours(args):
     opa = ops_per_attempt(w.q, A, w.theta)
     achieved = opa * per_launch_attempts / sweep_avg_s / 1e12
     peak = sms * LANES_PER_SM_PER_CLK * f_max / 1e12
-    rec = _sweep_record()
+    rec = _sweep_record(w)
     per_launch_replicas = per_launch_attempts / (w.N * w.theta)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": (rec["dram_bytes_per_replica"] * per_launch_replicas) if rec else None,
