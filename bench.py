@@ -684,14 +684,25 @@ def _adaptive(pa, R=200000):
     K = len(betas)
     out["adaptive"] = {"steps": K, "lnZ_per_site": obs[-1]["lnZ"] / N, "bias": obs[-1]["lnZ"] / N - ref,
                        "pa_steps_per_s": K / dt, "seconds": dt}
-    for name, Kc in (("constant", K), ("constant_2x", 2 * K)):
+    const = []
+    for name, Kc in (("constant", K), ("constant_2x", 2 * K), ("constant_3x", 3 * K)):
         bc = np.array([be * i / Kc for i in range(Kc + 1)])
         with pa.Population(pa.PAParams(q=w.q, L=w.L, R=R, seed=1)) as pop:
             (res, _), dt = timed(lambda: pop.run(bc, w.theta))
         out[name] = {"steps": Kc, "lnZ_per_site": res[-1]["lnZ"] / N, "bias": res[-1]["lnZ"] / N - ref,
                      "pa_steps_per_s": Kc / dt, "seconds": dt}
+        const.append(out[name])
     a, c = abs(out["adaptive"]["bias"]), abs(out["constant"]["bias"])
     out["adaptive_more_accurate_at_equal_steps"] = bool(a < c)
+    # constant steps at the adaptive schedule's accuracy: |bias| interpolated
+    # linearly in the step count between the constant runs that bracket it
+    for lo, hi in zip(const, const[1:]):
+        blo, bhi = abs(lo["bias"]), abs(hi["bias"])
+        if bhi <= a <= blo and blo > bhi:
+            Ke = lo["steps"] + (blo - a) / (blo - bhi) * (hi["steps"] - lo["steps"])
+            out["constant_steps_at_equal_accuracy"] = Ke
+            out["time_ratio_at_equal_accuracy"] = (Ke / hi["pa_steps_per_s"]) / out["adaptive"]["seconds"]
+            break
     return out
 
 
