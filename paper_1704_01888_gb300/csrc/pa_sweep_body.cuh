@@ -307,12 +307,16 @@ constexpr int kThresholdFull = 40;
 // (about 8 % of words at low temperature) goes to a block-wide queue, and in
 // the second pass whole warps serve only queued words, so a warp no longer
 // waits for the slowest of its ~700 sites.  Queue layout in shared memory:
-// two counters, kQueueCap entries of (site-word index, outcome bits acc,
+// two counters, QCAP entries of (site-word index, outcome bits acc,
 // undecided, class bits c0, e1, B proposal planes).  A full queue is not an error: the
-// word's own thread finishes it.
+// word's own thread finishes it.  The single-run kernel with up to four planes
+// takes 384 entries (its 48 lattices give up to ~250 queued words at low
+// temperature, so 256 entries overflowed: 1846 against 1837 attempts/ns over
+// the at-scale schedule; two blocks per SM still fit); the batched kernel
+// keeps 256, whose 96 KB lattice budget two blocks per SM would not fit with more.
 constexpr int kFirstPassCalls = 2;
 constexpr int kQueueCap = 256;
-__host__ __device__ constexpr int queue_words(int B) { return 2 + (5 + B) * kQueueCap; }
+__host__ __device__ constexpr int queue_words(int B, int cap = kQueueCap) { return 2 + (5 + B) * cap; }
 // Entry j holds, for the threshold bits t_1..t_4 of plane j (bit 31 - j of
 // T[1..4]), the coefficients of two multiply-adds: c0 * (t_1 - t_2) - t_2
 // gives the threshold bits of the dE = 1, 2 sites (c0: dE odd) and
@@ -392,7 +396,7 @@ __device__ __forceinline__ void acceptance_calls(int ch_begin, int ch_end, uint3
 // indicator bits (neighbours equal to s, neighbours different from s'), summed
 // by a carry-save tree; moves with dE > 0 compare v with T[dE] bit by bit, and
 // the warp draws further acceptance words only while some site is undecided.
-template <int B, int MODE, int Q = 0, bool HOIST = false>
+template <int B, int MODE, int Q = 0, bool HOIST = false, int QCAP = kQueueCap>
 __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32_t *sw, const uint4 *s_tab,
                                                  uint32_t *qbuf, const uint32_t *rk0, const uint32_t *rk1,
                                                  long long &sE, long long &sE2, long long &sM)
@@ -437,8 +441,8 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
     // site words still undecided after the first pass wait in qbuf for the second
     int *q_count = reinterpret_cast<int *>(qbuf);
     int *q_item = q_count + 2;
-    uint32_t(*q_mask)[kQueueCap] = reinterpret_cast<uint32_t(*)[kQueueCap]>(qbuf + 2 + kQueueCap);  // acc, und, c0, e1
-    uint32_t(*q_prop)[kQueueCap] = reinterpret_cast<uint32_t(*)[kQueueCap]>(qbuf + 2 + 5 * kQueueCap);
+    uint32_t(*q_mask)[QCAP] = reinterpret_cast<uint32_t(*)[QCAP]>(qbuf + 2 + QCAP);  // acc, und, c0, e1
+    uint32_t(*q_prop)[QCAP] = reinterpret_cast<uint32_t(*)[QCAP]>(qbuf + 2 + 5 * QCAP);
     if (tid < 2) q_count[tid] = 0;
     __syncthreads();
     int half = 0;
@@ -554,7 +558,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 bool queued = false;
                 if (und) {
                     const int e = atomicAdd(qc, 1);
-                    if (e < kQueueCap) {
+                    if (e < QCAP) {
                         q_item[e] = ii;
                         q_mask[0][e] = acc;
                         q_mask[1][e] = und;
@@ -589,7 +593,7 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
             }
             __syncthreads();
             // second pass: the queued site words, 32 to a warp
-            const int nq = min(*qc, kQueueCap);
+            const int nq = min(*qc, QCAP);
             for (int base = warp * 32; base < nq; base += nwarps * 32) {
                 const int e = base + lane;
                 const bool live = e < nq;
