@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a)
     long long sE = 0, sE2 = 0, sM = 0;
     for (int first = begin; first < end; first += a.rpb) {
         const dev::Group G = make_group(a, parity, first, min(a.rpb, end - first));
-        dev::sweep_group_bits<B, MODE, Q, MODE == 0 || MODE == 1, QCAP>(G, a.L, reinterpret_cast<uint32_t *>(smem4),
-                                                                        s_tab, s_queue, a.rk0, a.rk1, sE, sE2, sM);
+        dev::sweep_group_bits<B, MODE, Q, MODE == 0 || MODE == 1, QCAP, MODE != 0>(
+            G, a.L, reinterpret_cast<uint32_t *>(smem4), s_tab, s_queue, a.rk0, a.rk1, sE, sE2, sM);
     }
     if ((threadIdx.x & 31) == 0 && (sE | sE2 | sM)) dev::accumulate_totals(a.acc, sE, sE2, sM);
 }

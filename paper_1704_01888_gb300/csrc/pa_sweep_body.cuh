@@ -396,12 +396,14 @@ __device__ __forceinline__ void acceptance_calls(int ch_begin, int ch_end, uint3
 // indicator bits (neighbours equal to s, neighbours different from s'), summed
 // by a carry-save tree; moves with dE > 0 compare v with T[dE] bit by bit, and
 // the warp draws further acceptance words only while some site is undecided.
-template <int B, int MODE, int Q = 0, bool HOIST = false, int QCAP = kQueueCap>
+template <int B, int MODE, int Q = 0, bool HOIST = false, int QCAP = kQueueCap, bool SPLIT = false>
 __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32_t *sw, const uint4 *s_tab,
                                                  uint32_t *qbuf, const uint32_t *rk0, const uint32_t *rk1,
                                                  long long &sE, long long &sE2, long long &sM)
 {
     constexpr int BP = plane_stride(B);
+    // the measurement's per-replica counts reuse the queue (at most 16 replicas x (q + 1))
+    static_assert(16 * ((1 << B) + 1) <= queue_words(B, QCAP), "queue too small for the counts");
     const int L = MODE == 0 ? 64 : Lrt;
     const int N = L * L;
     const int WPR = MODE == 0 ? 1 : row_words(L);
@@ -623,21 +625,22 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
         }
     }
 
-    // measurements: one warp per replica, or the whole block per replica when
-    // the block holds fewer replicas than warps
-    const bool per_warp = 2 * nrep > nwarps;
-    const int n_owner = per_warp ? nwarps : 1;
-    const int owner = per_warp ? warp : 0;
-    const int stride = per_warp ? 32 : (int)blockDim.x;
-    const int me = per_warp ? lane : tid;
-    for (int r0 = 0; r0 < nrep; r0 += n_owner) {
-        const int r = r0 + owner;
-        const bool have = r < nrep;
-        const uint32_t *rep = sw + (have ? r : 0) * RW;
-        int agree = 0;
-        if (have) {
+    if (SPLIT && 2 * nrep <= nwarps) {
+        // measurements of a block holding fewer replicas than twice its warps
+        // (SPLIT: the single-run kernel, whose blocks may hold a few large
+        // lattices): every warp takes a share of each replica's words and the
+        // warps' counts are summed in shared memory (the queue's, idle now),
+        // with one barrier for the group instead of three per count
+        // (nrep <= nwarps / 2 <= 16 replicas x (q + 1) counts fit the queue)
+        int *s_cnt = reinterpret_cast<int *>(qbuf);
+        for (int i = tid; i < nrep * (q + 1); i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        for (int r = 0; r < nrep; ++r) {
+            const uint32_t *rep = sw + r * RW;
+            int *cnt_r = s_cnt + r * (q + 1);
+            int agree = 0;
             // each bond has one colour-0 end: count equal neighbours of colour-0 sites
-            for (int it = me; it < IPC; it += stride) {
+            for (int it = tid; it < IPC; it += blockDim.x) {
                 uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
                 load_planes<BP>(W, rep + it * BP);
                 const uint32_t vmask =
@@ -645,13 +648,11 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                 agree += __popc(vmask & ~differ<B, BP>(W, U)) + __popc(vmask & ~differ<B, BP>(W, D)) +
                          __popc(vmask & ~differ<B, BP>(W, H)) + __popc(vmask & ~differ<B, BP>(W, X));
             }
-        }
-        agree = per_warp ? __reduce_add_sync(0xFFFFFFFFu, agree) : block_sum_int(agree);
-        int best = 0;
-        for (int s = 0; s < q; ++s) {
-            int cnt = 0;
-            if (have) {
-                for (int it = me; it < 2 * IPC; it += stride) {
+            agree = __reduce_add_sync(0xFFFFFFFFu, agree);
+            if (lane == 0 && agree) atomicAdd(cnt_r + q, agree);
+            for (int s = 0; s < q; ++s) {
+                int cnt = 0;
+                for (int it = tid; it < 2 * IPC; it += blockDim.x) {
                     uint32_t W[BP];
                     load_planes<BP>(W, rep + it * BP);
                     const uint32_t vmask =
@@ -660,11 +661,62 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
                             : valid_mask(it - div_by(it, inv_row) * WPR, WPR, nb_last);
                     cnt += __popc(vmask & equal_state<B, BP>(W, s));
                 }
+                cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+                if (lane == 0 && cnt) atomicAdd(cnt_r + s, cnt);
             }
-            cnt = per_warp ? __reduce_add_sync(0xFFFFFFFFu, cnt) : block_sum_int(cnt);
-            best = max(best, cnt);
         }
-        if (have && me == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
+        __syncthreads();
+        // lane 0 of warp r records replica r (lane 0 of each warp carries the sums)
+        if (lane == 0 && warp < nrep) {
+            const int *cnt_r = s_cnt + warp * (q + 1);
+            int best = 0;
+            for (int s = 0; s < q; ++s) best = max(best, cnt_r[s]);
+            record_replica(G, first + warp, -cnt_r[q], best, N, sE, sE2, sM);
+        }
+    } else {
+        // measurements: one warp per replica, or the whole block per replica when
+        // the block holds fewer replicas than warps
+        const bool per_warp = 2 * nrep > nwarps;
+        const int n_owner = per_warp ? nwarps : 1;
+        const int owner = per_warp ? warp : 0;
+        const int stride = per_warp ? 32 : (int)blockDim.x;
+        const int me = per_warp ? lane : tid;
+        for (int r0 = 0; r0 < nrep; r0 += n_owner) {
+            const int r = r0 + owner;
+            const bool have = r < nrep;
+            const uint32_t *rep = sw + (have ? r : 0) * RW;
+            int agree = 0;
+            if (have) {
+                // each bond has one colour-0 end: count equal neighbours of colour-0 sites
+                for (int it = me; it < IPC; it += stride) {
+                    uint32_t W[BP], U[BP], D[BP], H[BP], X[BP];
+                    load_planes<BP>(W, rep + it * BP);
+                    const uint32_t vmask = neighbour_planes<B, MODE, BP>(rep + IPC * BP, L, IPC, WPR, nb_last,
+                                                                         inv_row, it, 0, U, D, H, X);
+                    agree += __popc(vmask & ~differ<B, BP>(W, U)) + __popc(vmask & ~differ<B, BP>(W, D)) +
+                             __popc(vmask & ~differ<B, BP>(W, H)) + __popc(vmask & ~differ<B, BP>(W, X));
+                }
+            }
+            agree = per_warp ? __reduce_add_sync(0xFFFFFFFFu, agree) : block_sum_int(agree);
+            int best = 0;
+            for (int s = 0; s < q; ++s) {
+                int cnt = 0;
+                if (have) {
+                    for (int it = me; it < 2 * IPC; it += stride) {
+                        uint32_t W[BP];
+                        load_planes<BP>(W, rep + it * BP);
+                        const uint32_t vmask =
+                            (MODE == 0 || MODE == 3 || MODE == 4)
+                                ? 0xFFFFFFFFu
+                                : valid_mask(it - div_by(it, inv_row) * WPR, WPR, nb_last);
+                        cnt += __popc(vmask & equal_state<B, BP>(W, s));
+                    }
+                }
+                cnt = per_warp ? __reduce_add_sync(0xFFFFFFFFu, cnt) : block_sum_int(cnt);
+                best = max(best, cnt);
+            }
+            if (have && me == 0) record_replica(G, first + r, -agree, best, N, sE, sE2, sM);
+        }
     }
     group_families(G);
     __syncthreads();
