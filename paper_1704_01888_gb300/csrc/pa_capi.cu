@@ -297,14 +297,17 @@ pa_status choose_launch(pa_ctx *c, int rpb_req, int threads_req)
     const long long units = pa::colour_words(L);
     int rpb = rpb_req;
     int threads = threads_req;
-    if (rpb <= 0 && threads <= 0 && units == 1024 && pa::state_bits(c->cfg.q) <= 5 &&
+    if (rpb <= 0 && threads <= 0 && (units == 1024 || units == 256) && pa::state_bits(c->cfg.q) <= 5 &&
         c->R_fill / (4 * c->sms) >= 4) {
-        // 1024 site words per colour (L = 256): blocks of 1024 threads, each
-        // keeping one site word index through all passes, with as many
-        // lattices as fit (five at q = 20: 1439 against 1339 attempts/ns with
-        // two lattices and 512 threads; six at q = 6: 1855 against 1731; even
-        // at q = 10; with seven planes the 1024-thread blocks are slower)
-        rpb = (int)((size_t)pa::kMaxLatticeBytes / RB);
+        // 1024 or 256 site words per colour (L = 256, 128): blocks of 1024
+        // threads, each keeping one site word index through all passes, with
+        // as many lattices as fit in whole passes (L = 256, q = 20: five, 1439
+        // against 1339 attempts/ns with two lattices and 512 threads; q = 6:
+        // 1855 against 1731; q = 10 even.  L = 128: q = 20 1411 against 1243,
+        // q = 8 1952 against 1919, q = 5 1857 against 1829, q = 10 even.  With
+        // six or seven planes the 1024-thread blocks are slower)
+        const int per_pass = (int)(1024 / units);
+        rpb = (int)((size_t)pa::kMaxLatticeBytes / RB) / per_pass * per_pass;
         threads = 1024;
     }
     if (rpb <= 0) {
