@@ -137,9 +137,11 @@ def _args():
     ap.add_argument("--steps", type=int, default=197)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "widths"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "widths", "table1"],
                     help="c3 runs the batch of 64 runs alone (its first --steps steps); widths runs the "
-                         "histogram-width study (20 runs, one batch)")
+                         "histogram-width study (20 runs, one batch); table1 the width study with the "
+                         "paper's Table I protocol (--runs runs per q and L)")
+    ap.add_argument("--runs", type=int, default=8, help="runs per (q, L) of the table1 workload")
     ap.add_argument("--batch-launch", default="", help="smem_budget,threads for the batched sweep kernel (c3)")
     ap.add_argument("--no-graph", action="store_true", help="c3 without graph capture")
     ap.add_argument("--no-e2e", action="store_true")
@@ -776,6 +778,56 @@ def run_width_study(args):
     return 0
 
 
+def run_table1(args):
+    """The width study with the protocol of the paper's Table I: q in {6, 8,
+    10, 20} and its L values, R = 1000, theta = 100, the paper's piecewise
+    schedule (steps of 0.001 around the transition); after every temperature
+    step the FWHM of the population's energy and magnetisation histograms;
+    omega(beta) averaged over --runs runs (random-number streams 0, 1, ...),
+    its maximum and T_max = 1 / beta there.  One JSON line, the paper's values
+    beside each row (its runs: 200 per row)."""
+    import torch
+
+    import paper_1704_01888_gb300 as pa
+    from paper_1704_01888_gb300 import analysis
+    from paper_1704_01888_gb300 import build as pabuild
+
+    torch.cuda.set_device(0)
+    pabuild.build()
+    n, theta, R = max(1, args.runs), 100, 1000
+    rows, attempts, steps = [], 0, 0
+    t0 = time.perf_counter()
+    for q, L in sorted(wl.TABLE_I):
+        b = wl.table1_betas(q)
+        we = np.zeros((n, b.size))
+        wm = np.zeros((n, b.size))
+        for r in range(n):
+            with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=1, stream=r)) as pop:
+                for i in range(1, b.size):
+                    pop.resample(b[i] - b[i - 1], i)
+                    pop.sweep(b[i], theta, i)
+                    E = pop.energies()
+                    we[r, i], wm[r, i] = analysis.ranged_widths(q, L, E, pop.occupations())
+                    attempts += E.size * L * L * theta
+            steps += b.size - 1
+        me, mm = we.mean(axis=0), wm.mean(axis=0)
+        ie, im = int(np.argmax(me[1:])) + 1, int(np.argmax(mm[1:])) + 1
+        pe, te, pm, tm = wl.TABLE_I[(q, L)]
+        rows.append({"q": q, "L": L, "omega_e_max": round(float(me[ie]), 4), "T_e": round(1.0 / b[ie], 4),
+                     "omega_m_max": round(float(mm[im]), 4), "T_m": round(1.0 / b[im], 4),
+                     "omega_e_max_sd_runs": round(float(we.max(axis=1).std()), 4),
+                     "paper": {"omega_e_max": pe, "T_e": te, "omega_m_max": pm, "T_m": tm}})
+    dt = time.perf_counter() - t0
+    print(json.dumps({"metric": "histogram widths (FWHM) at their maxima over the schedule; PA steps/s",
+                      "value": steps / dt, "unit": "PA steps/s", "n_gpus": 1, "attempts_per_ns": attempts / dt / 1e9,
+                      "seconds": dt,
+                      "config": {"workload": f"Table I protocol: q 6, 8, 10, 20 x L 16-256, R={R}, theta={theta}, "
+                                             f"{n} runs per row, one population at a time, host reads E and Mt "
+                                             "after every step"},
+                      "widths": rows}))
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -784,6 +836,8 @@ def main():
         return run_batch_only(args)
     if args.workload == "widths":
         return run_width_study(args)
+    if args.workload == "table1":
+        return run_table1(args)
     return run_ours(args)
 
 

@@ -124,6 +124,27 @@ def widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, e_bin: int = 4, m_bins
     return fwhm(x, h), fwhm(centres, counts)
 
 
+def ranged_widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, bins: int = 40):
+    """(omega_e, omega_m): FWHM of the energy-per-site and magnetisation
+    histograms of one population, each in about `bins` bins of a whole
+    number of its integer units (E, Mt) spanning the population's range, so
+    that the resolution follows the distribution's width at every L."""
+    N = L * L
+
+    def binned(v):
+        v = np.asarray(v, dtype=np.int64)
+        lo, hi = int(v.min()), int(v.max())
+        width = max(1, -(-(hi - lo + 1) // bins))
+        counts = np.bincount((v - lo) // width)
+        return lo + width * np.arange(counts.size) + (width - 1) / 2.0, counts
+
+    if np.asarray(E).size == 0:
+        return 0.0, 0.0
+    ue, he = binned(E)
+    um, hm = binned(Mt)
+    return fwhm(ue / N, he), fwhm(magnetisation(q, N, um), hm)
+
+
 def crossings(x: np.ndarray, f: np.ndarray, g: np.ndarray, window: int = 6):
     """Every change of sign of d = f - g as (x_cross, score), x_cross by
     linear interpolation and score = the smaller of max |d| over the `window`

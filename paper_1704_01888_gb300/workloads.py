@@ -117,3 +117,37 @@ def width_study_runs(seed: int = 1, qs=(6, 8, 10, 20), Ls=(16, 32, 64, 128, 256)
                                  seed=seed, stream=m))
             m += 1
     return runs
+
+
+# Inverse-temperature schedules of the paper's width study (Table I caption):
+# steps of 1/N_beta = 0.001 in a window [b, c] around the transition, 0.01
+# next to it and 0.05 below a and above d (this schedule stops at d); in
+# thousandths of beta: (a, b, c, d).
+TABLE_I_WINDOWS = {6: (995, 1135, 1305, 1545), 8: (1110, 1250, 1420, 1660), 10: (1165, 1305, 1475, 1715),
+                   20: (1595, 1735, 1905, 2145)}
+
+# The paper's Table I (R = 1000, theta = 100, averages over 200 runs): for
+# (q, L), (omega_max(e), T_max(e), omega_max(m), T_max(m)).
+TABLE_I = {
+    (6, 16): (0.71, 0.82, 0.51, 0.82), (6, 32): (0.39, 0.81, 0.41, 0.81), (6, 64): (0.23, 0.80, 0.40, 0.80),
+    (6, 128): (0.07, 0.80, 0.16, 0.80), (6, 256): (0.03, 0.80, 0.055, 0.79),
+    (8, 16): (0.64, 0.75, 0.46, 0.75), (8, 32): (0.34, 0.74, 0.36, 0.74), (8, 64): (0.22, 0.74, 0.31, 0.74),
+    (8, 96): (0.11, 0.74, 0.12, 0.74), (8, 128): (0.074, 0.74, 0.09, 0.73), (8, 192): (0.045, 0.73, 0.052, 0.73),
+    (8, 256): (0.032, 0.73, 0.037, 0.73),
+    (10, 16): (0.74, 0.71, 0.50, 0.71), (10, 32): (0.38, 0.70, 0.43, 0.70), (10, 64): (0.20, 0.69, 0.27, 0.69),
+    (10, 128): (0.074, 0.69, 0.088, 0.68), (10, 256): (0.032, 0.69, 0.026, 0.68),
+    (20, 16): (0.84, 0.57, 0.64, 0.57), (20, 32): (0.57, 0.57, 0.48, 0.57), (20, 64): (0.18, 0.57, 0.17, 0.56),
+    (20, 128): (0.07, 0.57, 0.06, 0.52), (20, 256): (0.029, 0.57, 0.018, 0.52),
+}
+
+
+def table1_betas(q: int) -> np.ndarray:
+    """beta_0 = 0, ..., d / 1000 for q's window (a, b, c, d): steps of 0.05
+    up to a, 0.01 up to b, 0.001 up to c, 0.01 up to d (each part ending
+    exactly on its bound)."""
+    a, b, c, d = TABLE_I_WINDOWS[q]
+    k = [0]
+    for bound, step in ((a, 50), (b, 10), (c, 1), (d, 10)):
+        while k[-1] < bound:
+            k.append(min(k[-1] + step, bound))
+    return np.array(k, dtype=np.float64) / 1000.0

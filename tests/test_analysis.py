@@ -63,6 +63,37 @@ def test_widths_of_gaussian_populations():
     assert wm == pytest.approx(c * 0.08, rel=0.05)
 
 
+def test_ranged_widths_resolve_narrow_and_wide_populations():
+    """The bins follow the population's range: the FWHM of Gaussian E and m
+    is recovered at a small and at a large lattice alike."""
+    rng = np.random.default_rng(11)
+    c = 2 * math.sqrt(2 * math.log(2))
+    q = 10
+    for L, sd_E, sd_m, R in ((16, 6.0, 0.05, 200000), (256, 900.0, 0.004, 200000)):
+        N = L * L
+        E = np.clip(np.round(rng.normal(-1.0 * N, sd_E, R)), -2 * N, 0).astype(np.int32)
+        Mt = np.round((rng.normal(0.3, sd_m, R) * (q - 1) + 1) * N / q).astype(np.int32)
+        we, wm = analysis.ranged_widths(q, L, E, Mt, bins=60)
+        assert we == pytest.approx(c * sd_E / N, rel=0.08)
+        assert wm == pytest.approx(c * sd_m, rel=0.08)
+    # a population of identical replicas has zero width
+    assert analysis.ranged_widths(q, 16, np.full(5, -300), np.full(5, 40)) == (0.0, 0.0)
+
+
+def test_table1_schedule_follows_the_caption():
+    from paper_1704_01888_gb300 import workloads as wl
+
+    for q, (a, b, c, d) in wl.TABLE_I_WINDOWS.items():
+        beta = wl.table1_betas(q)
+        k = np.round(beta * 1000).astype(int)
+        steps = np.diff(k)
+        assert k[0] == 0 and k[-1] == d and np.all(steps > 0)
+        assert np.all(steps[k[1:] <= a] <= 50) and np.all(steps[(k[:-1] >= a) & (k[1:] <= b)] == 10)
+        assert np.all(steps[(k[:-1] >= b) & (k[1:] <= c)] == 1) and np.all(steps[k[:-1] >= c] == 10)
+        assert np.count_nonzero(steps == 1) == c - b
+    assert len(wl.TABLE_I) == 22 and {q for q, _ in wl.TABLE_I} == {6, 8, 10, 20}
+
+
 def test_crossing_of_two_branches():
     from paper_1704_01888_gb300 import analysis
 
