@@ -799,24 +799,28 @@ def run_table1(args):
     t0 = time.perf_counter()
     for q, L in sorted(wl.TABLE_I):
         b = wl.table1_betas(q)
-        we = np.zeros((n, b.size))
-        wm = np.zeros((n, b.size))
+        # [run, step, (e, m), (outermost crossings, main peak)]
+        w = np.zeros((n, b.size, 2, 2))
         for r in range(n):
             with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=1, stream=r)) as pop:
                 for i in range(1, b.size):
                     pop.resample(b[i] - b[i - 1], i)
                     pop.sweep(b[i], theta, i)
-                    E = pop.energies()
-                    we[r, i], wm[r, i] = analysis.ranged_widths(q, L, E, pop.occupations())
+                    E, Mt = pop.energies(), pop.occupations()
+                    w[r, i, :, 0] = analysis.ranged_widths(q, L, E, Mt)
+                    w[r, i, :, 1] = analysis.ranged_widths(q, L, E, Mt, main_peak=True)
                     attempts += E.size * L * L * theta
             steps += b.size - 1
-        me, mm = we.mean(axis=0), wm.mean(axis=0)
-        ie, im = int(np.argmax(me[1:])) + 1, int(np.argmax(mm[1:])) + 1
+        mean = w.mean(axis=0)
+        row = {"q": q, "L": L}
+        for k, (name, sfx) in enumerate((("outermost", ""), ("main_peak", "_main_peak"))):
+            ie, im = int(np.argmax(mean[1:, 0, k])) + 1, int(np.argmax(mean[1:, 1, k])) + 1
+            row.update({"omega_e_max" + sfx: round(float(mean[ie, 0, k]), 4), "T_e" + sfx: round(1.0 / b[ie], 4),
+                        "omega_m_max" + sfx: round(float(mean[im, 1, k]), 4), "T_m" + sfx: round(1.0 / b[im], 4)})
+        row["omega_e_max_sd_runs"] = round(float(w[:, :, 0, 0].max(axis=1).std()), 4)
         pe, te, pm, tm = wl.TABLE_I[(q, L)]
-        rows.append({"q": q, "L": L, "omega_e_max": round(float(me[ie]), 4), "T_e": round(1.0 / b[ie], 4),
-                     "omega_m_max": round(float(mm[im]), 4), "T_m": round(1.0 / b[im], 4),
-                     "omega_e_max_sd_runs": round(float(we.max(axis=1).std()), 4),
-                     "paper": {"omega_e_max": pe, "T_e": te, "omega_m_max": pm, "T_m": tm}})
+        row["paper"] = {"omega_e_max": pe, "T_e": te, "omega_m_max": pm, "T_m": tm}
+        rows.append(row)
     dt = time.perf_counter() - t0
     print(json.dumps({"metric": "histogram widths (FWHM) at their maxima over the schedule; PA steps/s",
                       "value": steps / dt, "unit": "PA steps/s", "n_gpus": 1, "attempts_per_ns": attempts / dt / 1e9,

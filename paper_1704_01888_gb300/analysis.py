@@ -31,16 +31,26 @@ def rebin_energy_histogram(hist: np.ndarray, N: int, width: int = 1):
     return centres, counts
 
 
-def fwhm(x: np.ndarray, h: np.ndarray) -> float:
+def fwhm(x: np.ndarray, h: np.ndarray, main_peak: bool = False) -> float:
     """Full width at half maximum of a histogram h over equally spaced bin
-    centres x (outermost half-maximum crossings, linear interpolation)."""
+    centres x, by linear interpolation between bins: between the outermost
+    half-maximum crossings, or (main_peak) the crossings nearest to the
+    maximum on either side, i.e. the width of the peak that holds the
+    maximum when the histogram has several."""
     x = np.asarray(x, dtype=np.float64)
     h = np.asarray(h, dtype=np.float64)
     if h.size == 0 or h.max() <= 0:
         return 0.0
     half = h.max() / 2.0
-    above = np.nonzero(h >= half)[0]
-    lo, hi = int(above[0]), int(above[-1])
+    if main_peak:
+        top = int(np.argmax(h))
+        below_l = np.nonzero(h[:top] < half)[0]
+        below_r = np.nonzero(h[top:] < half)[0]
+        lo = int(below_l[-1]) + 1 if below_l.size else 0
+        hi = top + int(below_r[0]) - 1 if below_r.size else h.size - 1
+    else:
+        above = np.nonzero(h >= half)[0]
+        lo, hi = int(above[0]), int(above[-1])
     if lo > 0:
         x_left = x[lo - 1] + (half - h[lo - 1]) * (x[lo] - x[lo - 1]) / (h[lo] - h[lo - 1])
     else:
@@ -124,11 +134,12 @@ def widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, e_bin: int = 4, m_bins
     return fwhm(x, h), fwhm(centres, counts)
 
 
-def ranged_widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, bins: int = 40):
+def ranged_widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, bins: int = 40, main_peak: bool = False):
     """(omega_e, omega_m): FWHM of the energy-per-site and magnetisation
     histograms of one population, each in about `bins` bins of a whole
     number of its integer units (E, Mt) spanning the population's range, so
-    that the resolution follows the distribution's width at every L."""
+    that the resolution follows the distribution's width at every L
+    (main_peak as for fwhm)."""
     N = L * L
 
     def binned(v):
@@ -142,7 +153,7 @@ def ranged_widths(q: int, L: int, E: np.ndarray, Mt: np.ndarray, bins: int = 40)
         return 0.0, 0.0
     ue, he = binned(E)
     um, hm = binned(Mt)
-    return fwhm(ue / N, he), fwhm(magnetisation(q, N, um), hm)
+    return fwhm(ue / N, he, main_peak), fwhm(magnetisation(q, N, um), hm, main_peak)
 
 
 def crossings(x: np.ndarray, f: np.ndarray, g: np.ndarray, window: int = 6):

@@ -20,6 +20,10 @@ def test_fwhm_outermost_crossings_and_edges():
     # outermost crossings of the line at 2: between x=1,2 (at 1 + 1/3) and x=6,7 (at 6 + 2/3)
     assert analysis.fwhm(x, h) == pytest.approx((6 + 2 / 3) - (1 + 1 / 3))
     assert analysis.peaks(h) == [2, 6]
+    # the peak holding the maximum alone: crossings at 1 + 1/3 and 3 + 0 (h[3] = 2 is at half)
+    h2 = np.array([0, 1, 4, 2, 1, 2, 3, 1, 0, 0], dtype=float)
+    assert analysis.fwhm(x, h2, main_peak=True) == pytest.approx(3.0 - (1 + 1 / 3))
+    assert analysis.fwhm(x, h2) == pytest.approx((6 + 1 / 2) - (1 + 1 / 3))
     assert analysis.fwhm(x, np.zeros(10)) == 0.0
     assert analysis.fwhm(x, np.eye(10)[0]) == pytest.approx(0.5)  # a peak on the edge
 
