@@ -137,11 +137,12 @@ def _args():
     ap.add_argument("--steps", type=int, default=197)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5", "widths", "table1"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c1", "c2", "c3", "c5", "widths", "table1", "table2", "table3"],
                     help="c3 runs the batch of 64 runs alone (its first --steps steps); widths runs the "
-                         "histogram-width study (20 runs, one batch); table1 the width study with the "
-                         "paper's Table I protocol (--runs runs per q and L)")
-    ap.add_argument("--runs", type=int, default=8, help="runs per (q, L) of the table1 workload")
+                         "histogram-width study (20 runs, one batch); table1-3 the width studies of the "
+                         "paper's Tables I-III (--runs runs per row)")
+    ap.add_argument("--runs", type=int, default=8, help="runs per row of the table1-3 workloads")
     ap.add_argument("--batch-launch", default="", help="smem_budget,threads for the batched sweep kernel (c3)")
     ap.add_argument("--no-graph", action="store_true", help="c3 without graph capture")
     ap.add_argument("--no-e2e", action="store_true")
@@ -778,14 +779,41 @@ def run_width_study(args):
     return 0
 
 
-def run_table1(args):
-    """The width study with the protocol of the paper's Table I: q in {6, 8,
-    10, 20} and its L values, R = 1000, theta = 100, the paper's piecewise
-    schedule (steps of 0.001 around the transition); after every temperature
-    step the FWHM of the population's energy and magnetisation histograms;
-    omega(beta) averaged over --runs runs (random-number streams 0, 1, ...),
-    its maximum and T_max = 1 / beta there.  One JSON line, the paper's values
-    beside each row (its runs: 200 per row)."""
+def _width_row(pa, analysis, q, L, theta, n_beta, n, R=1000):
+    """One row of the paper's width tables: n runs (streams 0..n-1) of q, L,
+    R replicas, theta sweeps, the Table I schedule with fine steps 1/n_beta;
+    after every step the FWHM of the energy and magnetisation histograms
+    (outermost crossings and main peak), averaged over the runs and maximised
+    over the schedule; T_max = 1 / beta there."""
+    b = wl.table1_betas(q, n_beta)
+    # [run, step, (e, m), (outermost crossings, main peak)]
+    w = np.zeros((n, b.size, 2, 2))
+    attempts = 0
+    for r in range(n):
+        with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=1, stream=r)) as pop:
+            for i in range(1, b.size):
+                pop.resample(b[i] - b[i - 1], i)
+                pop.sweep(b[i], theta, i)
+                E, Mt = pop.energies(), pop.occupations()
+                w[r, i, :, 0] = analysis.ranged_widths(q, L, E, Mt)
+                w[r, i, :, 1] = analysis.ranged_widths(q, L, E, Mt, main_peak=True)
+                attempts += E.size * L * L * theta
+    mean = w.mean(axis=0)
+    row = {"q": q, "L": L, "theta": theta, "N_beta": n_beta}
+    for k, sfx in enumerate(("", "_main_peak")):
+        ie, im = int(np.argmax(mean[1:, 0, k])) + 1, int(np.argmax(mean[1:, 1, k])) + 1
+        row.update({"omega_e_max" + sfx: round(float(mean[ie, 0, k]), 4), "T_e" + sfx: round(1.0 / b[ie], 4),
+                    "omega_m_max" + sfx: round(float(mean[im, 1, k]), 4), "T_m" + sfx: round(1.0 / b[im], 4)})
+    row["omega_e_max_sd_runs"] = round(float(w[:, :, 0, 0].max(axis=1).std()), 4)
+    return row, attempts, n * (b.size - 1)
+
+
+def run_width_tables(args):
+    """The width studies of the paper's Tables I-III (Sec. 4): table1, q in
+    {6, 8, 10, 20} and the table's L values at theta = 100, N_beta = 1000;
+    table2, q = 8, L = 64 against theta; table3, q = 8, L = 64 against
+    N_beta.  R = 1000, the table caption's piecewise schedule, --runs runs per
+    row (the paper: 200).  One JSON line, the paper's values beside each row."""
     import torch
 
     import paper_1704_01888_gb300 as pa
@@ -794,40 +822,27 @@ def run_table1(args):
 
     torch.cuda.set_device(0)
     pabuild.build()
-    n, theta, R = max(1, args.runs), 100, 1000
+    n = max(1, args.runs)
+    if args.workload == "table1":
+        specs = [((q, L, 100, 1000), wl.TABLE_I[(q, L)]) for q, L in sorted(wl.TABLE_I)]
+    elif args.workload == "table2":
+        specs = [((8, 64, th, 1000), wl.TABLE_II[th]) for th in sorted(wl.TABLE_II)]
+    else:
+        specs = [((8, 64, 100, nb), wl.TABLE_III[nb]) for nb in sorted(wl.TABLE_III)]
     rows, attempts, steps = [], 0, 0
     t0 = time.perf_counter()
-    for q, L in sorted(wl.TABLE_I):
-        b = wl.table1_betas(q)
-        # [run, step, (e, m), (outermost crossings, main peak)]
-        w = np.zeros((n, b.size, 2, 2))
-        for r in range(n):
-            with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=1, stream=r)) as pop:
-                for i in range(1, b.size):
-                    pop.resample(b[i] - b[i - 1], i)
-                    pop.sweep(b[i], theta, i)
-                    E, Mt = pop.energies(), pop.occupations()
-                    w[r, i, :, 0] = analysis.ranged_widths(q, L, E, Mt)
-                    w[r, i, :, 1] = analysis.ranged_widths(q, L, E, Mt, main_peak=True)
-                    attempts += E.size * L * L * theta
-            steps += b.size - 1
-        mean = w.mean(axis=0)
-        row = {"q": q, "L": L}
-        for k, (name, sfx) in enumerate((("outermost", ""), ("main_peak", "_main_peak"))):
-            ie, im = int(np.argmax(mean[1:, 0, k])) + 1, int(np.argmax(mean[1:, 1, k])) + 1
-            row.update({"omega_e_max" + sfx: round(float(mean[ie, 0, k]), 4), "T_e" + sfx: round(1.0 / b[ie], 4),
-                        "omega_m_max" + sfx: round(float(mean[im, 1, k]), 4), "T_m" + sfx: round(1.0 / b[im], 4)})
-        row["omega_e_max_sd_runs"] = round(float(w[:, :, 0, 0].max(axis=1).std()), 4)
-        pe, te, pm, tm = wl.TABLE_I[(q, L)]
+    for (q, L, theta, n_beta), (pe, te, pm, tm) in specs:
+        row, att, st = _width_row(pa, analysis, q, L, theta, n_beta, n)
         row["paper"] = {"omega_e_max": pe, "T_e": te, "omega_m_max": pm, "T_m": tm}
         rows.append(row)
+        attempts += att
+        steps += st
     dt = time.perf_counter() - t0
     print(json.dumps({"metric": "histogram widths (FWHM) at their maxima over the schedule; PA steps/s",
                       "value": steps / dt, "unit": "PA steps/s", "n_gpus": 1, "attempts_per_ns": attempts / dt / 1e9,
                       "seconds": dt,
-                      "config": {"workload": f"Table I protocol: q 6, 8, 10, 20 x L 16-256, R={R}, theta={theta}, "
-                                             f"{n} runs per row, one population at a time, host reads E and Mt "
-                                             "after every step"},
+                      "config": {"workload": f"{args.workload} of the paper (Sec. 4), R=1000, {n} runs per row, one "
+                                             "population at a time, host reads E and Mt after every step"},
                       "widths": rows}))
     return 0
 
@@ -840,8 +855,8 @@ def main():
         return run_batch_only(args)
     if args.workload == "widths":
         return run_width_study(args)
-    if args.workload == "table1":
-        return run_table1(args)
+    if args.workload in ("table1", "table2", "table3"):
+        return run_width_tables(args)
     return run_ours(args)
 
 

@@ -141,13 +141,23 @@ TABLE_I = {
 }
 
 
-def table1_betas(q: int) -> np.ndarray:
+def table1_betas(q: int, n_beta: int = 1000) -> np.ndarray:
     """beta_0 = 0, ..., d / 1000 for q's window (a, b, c, d): steps of 0.05
-    up to a, 0.01 up to b, 0.001 up to c, 0.01 up to d (each part ending
-    exactly on its bound)."""
-    a, b, c, d = TABLE_I_WINDOWS[q]
+    up to a, 0.01 up to b, 1 / n_beta up to c, 0.01 up to d (each part ending
+    exactly on its bound; n_beta divides 10000)."""
+    a, b, c, d = (10 * x for x in TABLE_I_WINDOWS[q])
     k = [0]
-    for bound, step in ((a, 50), (b, 10), (c, 1), (d, 10)):
+    for bound, step in ((a, 500), (b, 100), (c, 10000 // n_beta), (d, 100)):
         while k[-1] < bound:
             k.append(min(k[-1] + step, bound))
-    return np.array(k, dtype=np.float64) / 1000.0
+    return np.array(k, dtype=np.float64) / 10000.0
+
+
+# The paper's Tables II and III (q = 8, L = 64, R = 1000, the schedule of
+# Table I): (omega_max(e), T_max(e), omega_max(m), T_max(m)) against theta
+# (N_beta = 1000), and against N_beta (theta = 100).
+TABLE_II = {10: (0.10, 0.73, 0.14, 0.72), 25: (0.13, 0.74, 0.20, 0.73), 50: (0.17, 0.74, 0.23, 0.74),
+            100: (0.22, 0.74, 0.31, 0.74), 200: (0.28, 0.74, 0.39, 0.74), 500: (0.29, 0.74, 0.36, 0.74),
+            1000: (0.34, 0.74, 0.42, 0.74)}
+TABLE_III = {100: (0.11, 0.73, 0.15, 0.72), 200: (0.13, 0.74, 0.21, 0.72), 500: (0.17, 0.74, 0.27, 0.73),
+             1000: (0.23, 0.74, 0.34, 0.74), 2000: (0.27, 0.74, 0.38, 0.74)}

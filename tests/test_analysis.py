@@ -88,14 +88,17 @@ def test_table1_schedule_follows_the_caption():
     from paper_1704_01888_gb300 import workloads as wl
 
     for q, (a, b, c, d) in wl.TABLE_I_WINDOWS.items():
-        beta = wl.table1_betas(q)
-        k = np.round(beta * 1000).astype(int)
-        steps = np.diff(k)
-        assert k[0] == 0 and k[-1] == d and np.all(steps > 0)
-        assert np.all(steps[k[1:] <= a] <= 50) and np.all(steps[(k[:-1] >= a) & (k[1:] <= b)] == 10)
-        assert np.all(steps[(k[:-1] >= b) & (k[1:] <= c)] == 1) and np.all(steps[k[:-1] >= c] == 10)
-        assert np.count_nonzero(steps == 1) == c - b
+        for n_beta in (1000, 2000, 200):
+            beta = wl.table1_betas(q, n_beta)
+            k = np.round(beta * 10000).astype(int)
+            steps = np.diff(k)
+            a4, b4, c4, d4, f = 10 * a, 10 * b, 10 * c, 10 * d, 10000 // n_beta
+            assert k[0] == 0 and k[-1] == d4 and np.all(steps > 0)
+            assert np.all(steps[k[1:] <= a4] <= 500) and np.all(steps[(k[:-1] >= a4) & (k[1:] <= b4)] == 100)
+            assert np.all(steps[(k[:-1] >= b4) & (k[1:] <= c4)] == f) and np.all(steps[k[:-1] >= c4] == 100)
+            assert np.count_nonzero((k[:-1] >= b4) & (k[1:] <= c4)) == (c4 - b4) // f
     assert len(wl.TABLE_I) == 22 and {q for q, _ in wl.TABLE_I} == {6, 8, 10, 20}
+    assert sorted(wl.TABLE_II) == [10, 25, 50, 100, 200, 500, 1000] and sorted(wl.TABLE_III) == [100, 200, 500, 1000, 2000]
 
 
 def test_crossing_of_two_branches():
