@@ -377,7 +377,13 @@ const char *pa_last_cuda_error(void);
 
 /* Launch-shape control for the sweep kernel: replicas per block and threads
  * per block (0 = automatic).  Any choice gives bit-identical results; this
- * exists for autotuning and for tests that check exactly that. */
+ * exists for autotuning and for tests that check exactly that.  Automatic:
+ * 96 KB of lattices and up to 512 threads per block (two blocks per SM), or,
+ * for L = 128 and 256 with states of at most five bits and at least 16
+ * replicas per SM, one block of 1024 threads per SM holding as many whole
+ * passes of lattices as fit 200 KB.  Errors: PA_ERR_INVALID for a shape that
+ * does not fit (threads not a multiple of 32 or above 1024, lattices above
+ * 200 KB); PA_ERR_TOO_LARGE if one lattice alone exceeds it. */
 pa_status pa_set_launch(pa_ctx *ctx, int32_t replicas_per_block, int32_t threads_per_block);
 
 /* The sweep kernel's current launch shape: replicas per block, threads per
