@@ -118,6 +118,28 @@ def test_step_api_graph_and_launch_shapes_agree():
         assert [x["sumE"] for x in g["obs"]] == [x["sumE"] for x in ref["obs"]], kw
 
 
+@pytest.mark.parametrize("q,L,R,other", [(8, 128, 3000, (8, 512)), (20, 256, 2500, (2, 512)), (3, 256, 2500, (1, 256))])
+def test_large_lattice_launch_shapes_agree(q, L, R, other):
+    """At L = 128 and 256 the automatic shape is one 1024-thread block per SM
+    holding whole passes of lattices (measurements split over its warps when
+    it holds few); it gives the bits of 512- and 256-thread blocks, and the
+    first steps match the oracle."""
+    betas = np.array([0.0, 0.3, 0.9, 1.3, 1.6, 1.9])[: 4 if L == 256 else 6]
+    B = max(1, (q - 1).bit_length())
+    words = L * ((L + 63) // 64)  # site words per colour (L a multiple of 64)
+    lattice = 2 * words * (B if B > 4 else 4 if B > 2 else B) * 4
+    with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=3)) as pop:
+        rpb, threads, _ = pop.launch_shape()
+    assert threads == 1024 and rpb * lattice <= 204800 < (rpb + 1024 // words) * lattice
+    assert (rpb * words) % 1024 == 0  # whole passes of the block's threads
+    ref = _gpu_run(q, L, R, 3, 3, betas)
+    g = _gpu_run(q, L, R, 3, 3, betas, launch=other)
+    assert np.array_equal(g["spins"], ref["spins"]) and np.array_equal(g["Mt"], ref["Mt"])
+    assert [x["lnZ"] for x in g["obs"]] == [x["lnZ"] for x in ref["obs"]]
+    if L == 128:
+        _compare(_gpu_run(q, L, R, 3, 3, betas[:3]), _oracle_run(q, L, R, 3, 3, betas[:3]))
+
+
 # ---------------------------------------------------------------------------
 # Edge cases: every row geometry of the multi-spin-coded kernel (L = 64; rows
 # of whole words; rows packed several to a word at L = 8, 16, 32; four bands
