@@ -5,12 +5,12 @@ same-colour sites share each Philox word; the proposal takes B words, the
 acceptance words follow and are drawn only while a site of the word is
 undecided), so the number of Philox calls the oracle's sweep draws for a word
 is the number that word's deepest site needs, in whole calls of four words.
-This script runs the plain at-scale schedule (q = 10, L = 64, beta 0 -> 1.6 in
-200 steps, theta = 10) on a sample of the population with the oracle and
-prints, per step, the mean acceptance planes per site word:
-4 x (calls per word) - B.  It uses only the oracle.
+This script runs a constant-step schedule (by default the plain at-scale one:
+q = 10, L = 64, beta 0 -> 1.6 in 200 steps, theta = 10) on a sample of the
+population with the oracle and prints, per step, the mean acceptance planes per
+site word: 4 x (calls per word) - B.  It uses only the oracle.
 
-    python oracle/acceptance_planes.py [R_sample] [> profiles/acceptance_planes_q10-L64.txt]
+    python oracle/acceptance_planes.py [R_sample [q L K beta_end theta]] > profiles/acceptance_planes_q<q>-L<L>.txt
 """
 import os
 import sys
@@ -28,8 +28,9 @@ def main(R=64, q=10, L=64, K=200, beta_end=1.6, theta=10, seed=1):
     betas = np.array([beta_end * i / K for i in range(K + 1)])
     spins = oracle.init_random(q, L, 0, R, seed)
     E = np.array([oracle.energy(s) for s in spins], dtype=np.int32)
-    print(f"# command: python oracle/acceptance_planes.py {R} > profiles/acceptance_planes_q{q}-L{L}.txt")
-    print(f"# acceptance planes per site word, oracle count: q={q} L={L} R={R} (sample of the at-scale population)")
+    args = f"{R}" if (q, L, K, beta_end, theta) == (10, 64, 200, 1.6, 10) else f"{R} {q} {L} {K} {beta_end} {theta}"
+    print(f"# command: python oracle/acceptance_planes.py {args} > profiles/acceptance_planes_q{q}-L{L}.txt")
+    print(f"# acceptance planes per site word, oracle count: q={q} L={L} R={R} (a sample of the population)")
     print(f"# theta={theta}, beta 0 -> {beta_end} in {K} steps, nearest-integer resampling, seed {seed}")
     print("# step beta planes_per_word")
     for i in range(1, K + 1):
@@ -47,4 +48,10 @@ def main(R=64, q=10, L=64, K=200, beta_end=1.6, theta=10, seed=1):
 
 
 if __name__ == "__main__":
-    main(*(int(a) for a in sys.argv[1:2]))
+    a = sys.argv[1:]
+    kw = {}
+    if a:
+        kw["R"] = int(a[0])
+    if len(a) >= 6:
+        kw.update(q=int(a[1]), L=int(a[2]), K=int(a[3]), beta_end=float(a[4]), theta=int(a[5]))
+    main(**kw)
