@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -84,14 +85,20 @@ def acceptance_planes(w, first: int, last: int):
     (ACC_PLANES, None) where no count exists."""
     path = os.path.join(ROOT, "profiles", f"acceptance_planes_q{w.q}-L{w.L}.txt")
     try:
-        vals = []
+        vals, schedule = [], None
         for line in open(path):
-            if line.startswith("#") or not line.strip():
+            if line.startswith("#"):
+                m = re.search(r"theta=(\d+), beta 0 -> ([\d.]+) in (\d+) steps", line)
+                if m:
+                    schedule = (int(m.group(1)), float(m.group(2)), int(m.group(3)))
+                continue
+            if not line.strip():
                 continue
             i, _, a = line.split()[:3]
             if first <= int(i) <= last:
                 vals.append(float(a))
-        if vals and w.theta == 10 and abs(w.beta_end - 1.6) < 1e-12 and w.K == 200:
+        # the count holds for the schedule it was taken on
+        if vals and schedule and schedule[0] == w.theta and abs(schedule[1] - w.beta_end) < 1e-9 and schedule[2] == w.K:
             return sum(vals) / len(vals), os.path.relpath(path, ROOT)
     except OSError:
         pass
