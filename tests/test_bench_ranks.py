@@ -72,7 +72,12 @@ def test_bench_helpers_and_global_names():
     w = bench.wl.C2
     A, src = bench.acceptance_planes(w, 6, 25)
     assert src is not None and 5.5 < A < 6.5
-    assert bench.acceptance_planes(bench.wl.C5, 6, 25) == (bench.ACC_PLANES, None)
+    A5, src5 = bench.acceptance_planes(bench.wl.C5, 6, 25)
+    assert src5 is not None and 4.5 < A5 < 6.0
+    # no count for the small case; a count holds only for the schedule it was taken on
+    assert bench.acceptance_planes(bench.wl.C1, 6, 25) == (bench.ACC_PLANES, None)
+    other = bench.wl.scaled(bench.wl.C2, K=100, name="c2-K100")
+    assert bench.acceptance_planes(other, 6, 25) == (bench.ACC_PLANES, None)
 
     missing = set()
 
