@@ -145,10 +145,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c5", "widths", "table1", "table2", "table3"],
+                    choices=["c1", "c2", "c3", "c5", "widths", "table1", "table2", "table3", "hysteresis"],
                     help="c3 runs the batch of 64 runs alone (its first --steps steps); widths runs the "
                          "histogram-width study (20 runs, one batch); table1-3 the width studies of the "
-                         "paper's Tables I-III (--runs runs per row)")
+                         "paper's Tables I-III (--runs runs per row); hysteresis the cooling and heating "
+                         "branches of its Figs. 2-3")
     ap.add_argument("--runs", type=int, default=8, help="runs per row of the table1-3 workloads")
     ap.add_argument("--batch-launch", default="", help="smem_budget,threads for the batched sweep kernel (c3)")
     ap.add_argument("--no-graph", action="store_true", help="c3 without graph capture")
@@ -854,6 +855,66 @@ def run_width_tables(args):
     return 0
 
 
+def run_hysteresis(args):
+    """The protocol of the paper's Figs. 2 and 3 (Secs. 5-6): q = 3, 6, 10,
+    L = 32, R = 10000, theta = 10, steps of 0.01 between beta = 0 and 3;
+    cooling from random states at beta = 0 (ln Z_0 = N ln q) and heating from
+    ground states at beta = 3 (ln Z = ln q + 2 N beta, Eqs. 7-8).  Per q: the
+    area between the cooling and heating energy curves (hysteresis), the
+    same with resampling off (q = 10), and the beta where the ln Z branches
+    cross against beta_t = ln(1 + sqrt q).  One JSON line."""
+    import torch
+
+    import paper_1704_01888_gb300 as pa
+    from paper_1704_01888_gb300 import analysis
+    from paper_1704_01888_gb300 import build as pabuild
+
+    torch.cuda.set_device(0)
+    pabuild.build()
+    L, R, theta, n = 32, 10000, 10, 300
+    N = L * L
+    up = np.array([k / 100.0 for k in range(n + 1)])
+    down = up[::-1].copy()
+    t0 = time.perf_counter()
+
+    def branches(q, mode):
+        with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=1, resample_mode=mode)) as pop:
+            c0 = pop.observables()
+            cool, _ = pop.run(up, theta, use_graph=True)
+        with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=2, resample_mode=mode, init_mode=pa.INIT_GROUND,
+                                       beta0=3.0)) as pop:
+            h0 = pop.observables()
+            heat, _ = pop.run(down, theta, use_graph=True)
+        cool, heat = [c0] + cool, ([h0] + heat)[::-1]  # both on up's grid
+        e_c = np.array([o["meanE"] for o in cool]) / N
+        e_h = np.array([o["meanE"] for o in heat]) / N
+        f_c = np.array([o["lnZ"] for o in cool]) / N
+        f_h = np.array([o["lnZ"] for o in heat]) / N
+        return e_c, e_h, f_c, f_h
+
+    rows = []
+    for q in (3, 6, 10):
+        e_c, e_h, f_c, f_h = branches(q, pa.RESAMPLE_NEAREST_INT)
+        cs = analysis.crossings(up, f_c, f_h)
+        x = max(cs, key=lambda c: c[1]) if cs else None
+        row = {"q": q, "beta_t": wl.beta_t(q), "hysteresis_area": float(np.abs(e_c - e_h).sum() * 0.01),
+               "max_energy_gap": float(np.abs(e_c - e_h).max()),
+               "max_lnZ_gap_per_site": float(np.abs(f_c - f_h).max()),
+               "beta_cross": x[0] if x else None, "cross_score": x[1] if x else None}
+        if q == 10:
+            e_c0, e_h0, _, _ = branches(q, pa.RESAMPLE_OFF)
+            row["hysteresis_area_resampling_off"] = float(np.abs(e_c0 - e_h0).sum() * 0.01)
+            row["max_energy_gap_resampling_off"] = float(np.abs(e_c0 - e_h0).max())
+        rows.append(row)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"metric": "hysteresis and free-energy branches (Figs. 2-3 protocol)", "value": dt,
+                      "unit": "s", "n_gpus": 1, "higher_is_better": False,
+                      "config": {"workload": f"q 3, 6, 10, L={L}, R={R}, theta={theta}, beta 0 <-> 3 in steps of 0.01, "
+                                             "cooling from beta 0, heating from ground states at beta 3"},
+                      "branches": rows}))
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -864,6 +925,8 @@ def main():
         return run_width_study(args)
     if args.workload in ("table1", "table2", "table3"):
         return run_width_tables(args)
+    if args.workload == "hysteresis":
+        return run_hysteresis(args)
     return run_ours(args)
 
 
