@@ -856,13 +856,15 @@ def run_width_tables(args):
 
 
 def run_hysteresis(args):
-    """The protocol of the paper's Figs. 2 and 3 (Secs. 5-6): q = 3, 6, 10,
+    """The protocol of the paper's Figs. 1-3 (Secs. 4-6): q = 3, 6, 10,
     L = 32, R = 10000, theta = 10, steps of 0.01 between beta = 0 and 3;
     cooling from random states at beta = 0 (ln Z_0 = N ln q) and heating from
     ground states at beta = 3 (ln Z = ln q + 2 N beta, Eqs. 7-8).  Per q: the
     area between the cooling and heating energy curves (hysteresis), the
     same with resampling off (q = 10), and the beta where the ln Z branches
-    cross against beta_t = ln(1 + sqrt q).  One JSON line."""
+    cross against beta_t = ln(1 + sqrt q); for q = 6 the cooling run's energy
+    histograms at beta = 0.8, 1.24 and 1.4 (FWHM, number of modes).  One JSON
+    line."""
     import torch
 
     import paper_1704_01888_gb300 as pa
@@ -877,10 +879,18 @@ def run_hysteresis(args):
     down = up[::-1].copy()
     t0 = time.perf_counter()
 
+    fig1 = {}
+
     def branches(q, mode):
         with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=1, resample_mode=mode)) as pop:
             c0 = pop.observables()
-            cool, _ = pop.run(up, theta, use_graph=True)
+            # Fig. 1 (left): the q = 6 cooling run's energy histograms at beta 0.8, 1.24 (beta_t), 1.4
+            steps = (80, 124, 140) if q == 6 and mode == pa.RESAMPLE_NEAREST_INT else ()
+            cool, hists = pop.run(up, theta, hist_steps=steps, use_graph=True)
+            for k, st in enumerate(steps):
+                x, h = analysis.rebin_energy_histogram(hists[k], N, 4)
+                fig1[f"{up[st]:.2f}"] = {"fwhm": analysis.fwhm(x, h), "modes": len(analysis.modes(h)),
+                                         "mean_e": float(cool[st - 1]["meanE"]) / N}
         with pa.Population(pa.PAParams(q=q, L=L, R=R, seed=2, resample_mode=mode, init_mode=pa.INIT_GROUND,
                                        beta0=3.0)) as pop:
             h0 = pop.observables()
@@ -905,6 +915,8 @@ def run_hysteresis(args):
             e_c0, e_h0, _, _ = branches(q, pa.RESAMPLE_OFF)
             row["hysteresis_area_resampling_off"] = float(np.abs(e_c0 - e_h0).sum() * 0.01)
             row["max_energy_gap_resampling_off"] = float(np.abs(e_c0 - e_h0).max())
+        if q == 6:
+            row["energy_histograms"] = fig1
         rows.append(row)
     dt = time.perf_counter() - t0
     print(json.dumps({"metric": "hysteresis and free-energy branches (Figs. 2-3 protocol)", "value": dt,
