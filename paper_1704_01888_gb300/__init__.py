@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import time
 from dataclasses import dataclass
 
 import numpy as np
@@ -394,31 +395,49 @@ class Population:
         return d.value
 
     def run_adaptive(self, beta_end: float, theta: int, target: float = 0.85, dbeta_max: float = 0.05,
-                     iters: int = 12, max_steps: int = 10000):
-        """PA to beta_end with adaptive steps.  Returns (obs list, betas)."""
+                     iters: int = 12, max_steps: int = 10000, log=None):
+        """PA to beta_end with adaptive steps.  Returns (obs list, betas).
+        log: a path or text file that receives one JSON line per step
+        (paper_1704_01888_gb300.log)."""
         obs = (Obs * max_steps)()
         betas = np.zeros(max_steps, dtype=np.float64)
         K = ctypes.c_int32()
+        beta0 = self.beta
+        t0 = time.perf_counter()
         _check(self.lib.pa_run_adaptive(self._ctx, float(beta_end), float(target), float(dbeta_max), int(iters),
                                         int(theta), int(max_steps), ctypes.cast(obs, ctypes.c_void_p), _ptr(betas),
                                         ctypes.byref(K)), "pa_run_adaptive")
+        dt = time.perf_counter() - t0
         self.step += K.value
         if K.value:
             self.beta = float(betas[K.value - 1])
-        return [o.as_dict() for o in obs[: K.value]], betas[: K.value].copy()
+        out = [o.as_dict() for o in obs[: K.value]]
+        if log is not None and out:
+            from . import log as _log
 
-    def run(self, betas, theta: int, hist_steps=(), use_graph: bool = False):
-        """Runs betas[1..K] (betas[0] = current beta).  Returns (obs list, hists)."""
+            _log.write_jsonl(log, _log.step_records(out, self.N, beta0, dt / len(out), overlap_target=target))
+        return out, betas[: K.value].copy()
+
+    def run(self, betas, theta: int, hist_steps=(), use_graph: bool = False, log=None):
+        """Runs betas[1..K] (betas[0] = current beta).  Returns (obs list,
+        hists).  log: a path or text file that receives one JSON line per
+        step (paper_1704_01888_gb300.log)."""
         betas = np.ascontiguousarray(betas, dtype=np.float64)
         K = betas.size - 1
         obs = (Obs * K)()
         hs = np.ascontiguousarray(hist_steps, dtype=np.int32)
         hist = np.zeros((hs.size, 2 * self.N + 1), dtype=np.int32)
+        t0 = time.perf_counter()
         _check(self.lib.pa_run(self._ctx, _ptr(betas), K, int(theta), ctypes.cast(obs, ctypes.c_void_p),
                                _ptr(hs) if hs.size else None, hs.size, _ptr(hist) if hs.size else None,
                                int(use_graph)), "pa_run")
+        dt = time.perf_counter() - t0
         self.step += K
         self.beta = float(betas[-1])
+        if log is not None and K > 0:
+            from . import log as _log
+
+            _log.write_jsonl(log, _log.step_records([o.as_dict() for o in obs], self.N, float(betas[0]), dt / K))
         return [o.as_dict() for o in obs], hist
 
 

@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([nvcc, "-shared", "-o", tmp] + objs + ARCH, check=True)
+    subprocess.run([nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-ldl"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -23,6 +23,7 @@
 
 #include "../../include/pa.h"
 #include "pa_batch.cuh"
+#include "pa_trace.h"
 
 namespace pa {
 
@@ -339,6 +340,7 @@ extern "C" {
 
 pa_status pa_batch_create(const pa_run_desc *runs, int32_t M, void *cuda_stream, pa_batch **out)
 {
+    pa::TraceRange trace("pa_batch_create");
     if (!out) return PA_ERR_INVALID;
     *out = nullptr;
     if (!runs || M < 1 || M > pa::kMaxRuns) return PA_ERR_INVALID;
@@ -526,6 +528,7 @@ pa_status pa_batch_get_launch(pa_batch *b, int32_t *smem_budget, int32_t *thread
 
 pa_status pa_batch_run(pa_batch *b, int32_t use_graph)
 {
+    pa::TraceRange trace("pa_batch_run");
     if (!b) return PA_ERR_INVALID;
     if (b->ran) return PA_ERR_STATE;
     b->ran = true;
@@ -589,6 +592,7 @@ pa_status pa_batch_get_spins(pa_batch *b, int32_t m, int64_t slot_begin, int64_t
 
 pa_status pa_batch_autotune(pa_batch *b, int32_t *smem_budget_out, int32_t *threads_out)
 {
+    pa::TraceRange trace("pa_batch_autotune");
     if (!b) return PA_ERR_INVALID;
     if (b->ran) return PA_ERR_STATE;
     const std::string key = tune_key(b);

@@ -21,6 +21,7 @@
 
 #include "../../include/pa.h"
 #include "pa_internal.cuh"
+#include "pa_trace.h"
 
 namespace pa {
 
@@ -581,6 +582,7 @@ extern "C" {
 
 pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
 {
+    pa::TraceRange trace("pa_init");
     if (!out) return PA_ERR_INVALID;
     *out = nullptr;
     if (!cfg) return PA_ERR_INVALID;
@@ -615,6 +617,7 @@ pa_status pa_init(const pa_config *cfg, void *cuda_stream, pa_ctx **out)
 
 pa_status pa_save(pa_ctx *c, const char *path)
 {
+    pa::TraceRange trace("pa_save");
     if (!c || !path) return PA_ERR_INVALID;
     if (c->shard) return PA_ERR_STATE;
     if (c->failed || c->pending_step != 0) return PA_ERR_STATE;
@@ -668,6 +671,7 @@ pa_status pa_save(pa_ctx *c, const char *path)
 
 pa_status pa_load(const char *path, void *cuda_stream, pa_ctx **out)
 {
+    pa::TraceRange trace("pa_load");
     if (!out) return PA_ERR_INVALID;
     *out = nullptr;
     if (!path) return PA_ERR_INVALID;
@@ -765,6 +769,7 @@ pa_status pa_get_launch(pa_ctx *c, int32_t *rpb, int32_t *threads, int32_t *bloc
 
 pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, int32_t *R_out)
 {
+    pa::TraceRange trace("pa_resample");
     if (!c) return PA_ERR_INVALID;
     if (c->shard) return PA_ERR_STATE;
     if (c->failed || c->pending_step != 0 || step <= c->step) return PA_ERR_STATE;
@@ -795,6 +800,7 @@ pa_status pa_resample(pa_ctx *c, double dbeta, int32_t step, double *lnQ_out, in
 
 pa_status pa_sweep(pa_ctx *c, double beta, int32_t theta, int32_t step)
 {
+    pa::TraceRange trace("pa_sweep");
     if (!c) return PA_ERR_INVALID;
     if (theta < 0 || theta > pa::kMaxTheta || !(beta >= 0.0) || !std::isfinite(beta)) return PA_ERR_INVALID;
     if (c->failed) return PA_ERR_STATE;
@@ -869,6 +875,7 @@ pa_status pa_population_size(pa_ctx *c, int32_t *R_out)
 
 pa_status pa_observables(pa_ctx *c, pa_obs *out, int32_t *hist_out, int32_t hist_len)
 {
+    pa::TraceRange trace("pa_observables");
     if (!c || !out) return PA_ERR_INVALID;
     if (hist_out && hist_len < c->nbins) return PA_ERR_INVALID;
     // one round trip: the device state, the latest record and the histogram
@@ -972,6 +979,7 @@ pa_status pa_shard_plan(const int64_t *totals, int32_t world, int32_t rank, int6
 
 pa_status pa_shard_init(const pa_config *cfg, int32_t rank, int32_t world, void *cuda_stream, pa_ctx **out)
 {
+    pa::TraceRange trace("pa_shard_init");
     if (!out) return PA_ERR_INVALID;
     *out = nullptr;
     if (!cfg || world < 2) return PA_ERR_INVALID;
@@ -1031,6 +1039,7 @@ pa_status pa_shard_get_buffers(pa_ctx *c, pa_shard_buffers *out)
 
 pa_status pa_shard_finalize(pa_ctx *c, double beta)
 {
+    pa::TraceRange trace("pa_shard_finalize");
     if (!c || !std::isfinite(beta)) return PA_ERR_INVALID;
     if (!c->shard || c->failed || c->shard_stage != kShardMeasured) return PA_ERR_STATE;
     const int gathered = c->shard_resampled ? 1 : 0;
@@ -1044,6 +1053,7 @@ pa_status pa_shard_finalize(pa_ctx *c, double beta)
 
 pa_status pa_shard_counts(pa_ctx *c, double dbeta, int32_t step, int64_t *local_total)
 {
+    pa::TraceRange trace("pa_shard_counts");
     if (!c || !local_total) return PA_ERR_INVALID;
     if (!c->shard || c->failed || c->shard_stage != kShardReady || step <= c->step) return PA_ERR_STATE;
     if (!std::isfinite(dbeta) || !(c->beta + dbeta >= 0.0)) return PA_ERR_INVALID;
@@ -1078,6 +1088,7 @@ pa_status pa_shard_counts(pa_ctx *c, double dbeta, int32_t step, int64_t *local_
 
 pa_status pa_shard_pack(pa_ctx *c, const int64_t *totals, int64_t *send_counts)
 {
+    pa::TraceRange trace("pa_shard_pack");
     if (!c || !totals || !send_counts) return PA_ERR_INVALID;
     if (!c->shard || c->failed || c->shard_stage != kShardCounted) return PA_ERR_STATE;
     if (totals[c->rank] != c->n_pack) return PA_ERR_INVALID;
@@ -1117,6 +1128,7 @@ pa_status pa_shard_pack(pa_ctx *c, const int64_t *totals, int64_t *send_counts)
 
 pa_status pa_shard_accept(pa_ctx *c, const int64_t *recv_counts)
 {
+    pa::TraceRange trace("pa_shard_accept");
     if (!c || !recv_counts) return PA_ERR_INVALID;
     if (!c->shard || c->failed || c->shard_stage != kShardPacked) return PA_ERR_STATE;
     int64_t n = 0;
@@ -1152,6 +1164,7 @@ pa_status pa_shard_range(pa_ctx *c, int64_t *slot0, int64_t *count, int64_t *R_a
 pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_obs *obs_out,
                  const int32_t *hist_steps, int32_t n_hist, int32_t *hist_out, int32_t use_graph)
 {
+    pa::TraceRange trace("pa_run");
     if (!c || !betas || K < 1 || theta < 0 || theta > pa::kMaxTheta || n_hist < 0 || (n_hist > 0 && (!hist_steps || !hist_out)))
         return PA_ERR_INVALID;
     if (c->shard) return PA_ERR_STATE;
@@ -1288,6 +1301,7 @@ pa_status pa_run(pa_ctx *c, const double *betas, int32_t K, int32_t theta, pa_ob
 
 pa_status pa_next_dbeta(pa_ctx *c, double target, double dbeta_cap, int32_t iters, double *dbeta_out)
 {
+    pa::TraceRange trace("pa_next_dbeta");
     if (!c || !dbeta_out || !(target > 0.0 && target < 1.0) || !(dbeta_cap > 0.0) || !std::isfinite(dbeta_cap) ||
         iters < 0 || iters > 200)
         return PA_ERR_INVALID;
@@ -1305,6 +1319,7 @@ pa_status pa_next_dbeta(pa_ctx *c, double target, double dbeta_cap, int32_t iter
 pa_status pa_run_adaptive(pa_ctx *c, double beta_end, double target, double dbeta_max, int32_t iters, int32_t theta,
                           int32_t max_steps, pa_obs *obs_out, double *betas_out, int32_t *K_out)
 {
+    pa::TraceRange trace("pa_run_adaptive");
     if (!c || !K_out || theta < 0 || theta > pa::kMaxTheta || max_steps < 1 || !(beta_end >= 0.0) || !std::isfinite(beta_end) ||
         !(dbeta_max > 0.0))
         return PA_ERR_INVALID;

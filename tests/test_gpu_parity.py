@@ -118,6 +118,22 @@ def test_step_api_graph_and_launch_shapes_agree():
         assert [x["sumE"] for x in g["obs"]] == [x["sumE"] for x in ref["obs"]], kw
 
 
+def test_run_writes_one_log_line_per_step(tmp_path):
+    """pa_run through Population.run(log=...): one JSON line per temperature
+    step carrying that step's observables."""
+    import json
+
+    w = wl.C1
+    b = w.betas()[:11]
+    path = tmp_path / "steps.jsonl"
+    with pa.Population(pa.PAParams(q=w.q, L=w.L, R=w.R, seed=w.seed)) as pop:
+        obs, _ = pop.run(b, w.theta, log=str(path))
+    recs = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(recs) == 10
+    assert [r["lnZ"] for r in recs] == [o["lnZ"] for o in obs] and [r["R"] for r in recs] == [o["R"] for o in obs]
+    assert recs[0]["dbeta"] == pytest.approx(b[1]) and recs[-1]["e"] == pytest.approx(obs[-1]["meanE"] / w.N)
+
+
 @pytest.mark.parametrize("q,L,R,other", [(8, 128, 3000, (8, 512)), (20, 256, 2500, (2, 512)), (3, 256, 2500, (1, 256))])
 def test_large_lattice_launch_shapes_agree(q, L, R, other):
     """At L = 128 and 256 the automatic shape is one 1024-thread block per SM
