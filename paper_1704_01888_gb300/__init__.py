@@ -91,11 +91,12 @@ _lib = None
 
 
 def load_library(path: str | None = None):
-    """Loads libpa_gb300.so (raises if it has not been built)."""
+    """Loads libpa_gb300.so, or the library the PA_LIBRARY environment
+    variable names (e.g. the checked build); raises if it has not been built."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or os.environ.get("PA_LIBRARY") or LIB_PATH
     if not os.path.exists(p):
         raise RuntimeError(f"CUDA library {p} is missing: run paper_1704_01888_gb300.build.build() first")
     lib = ctypes.CDLL(p)

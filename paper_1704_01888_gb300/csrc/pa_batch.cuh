@@ -158,6 +158,10 @@ __global__ void __launch_bounds__(1024) k_batch_sweep(const BatchArgs b)
         G.stream_hi = r.stream_hi;
         G.gather = b.gather != 0;
         G.write_back = b.gather || sp.theta > 0;
+#if PA_CHECKED
+        G.src_limit = r.st->pop;
+        G.err = &r.st->err;
+#endif
         dev::build_threshold_table(s_tab, sp.thr);
         long long sE = 0, sE2 = 0, sM = 0;
         uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);

@@ -24,6 +24,16 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Checked builds (-DPA_CHECKED=1; build.build(checked=True) makes
+// libpa_gb300_checked.so): the kernels test the indices they take from device
+// data -- a gather's parent slot, a replica's energy bin -- before using them;
+// a failed test sets the run's error flag to PA_ERR_INVALID (1) and skips the
+// access, so the host call reports it and no access leaves its array.  Off by
+// default: the tests cost instructions on the hot path.
+#ifndef PA_CHECKED
+#define PA_CHECKED 0
+#endif
+
 namespace pa {
 
 // Top two bits of the second Philox counter word separate the uses of the

@@ -55,6 +55,10 @@ __device__ __forceinline__ dev::Group make_group(const SweepArgs &a, int parity,
     G.stream_hi = a.stream_hi;
     G.gather = a.gather != 0;
     G.write_back = a.gather || a.theta > 0;
+#if PA_CHECKED
+    G.src_limit = a.st->pop;  // the old population (received runs on a shard) until k_finalize
+    G.err = &a.st->err;
+#endif
     return G;
 }
 

@@ -268,6 +268,10 @@ struct Group {
     int q, theta, step;
     uint32_t stream_hi;      // stream number << 24, or'ed into the slot counter word
     bool gather, write_back;
+#if PA_CHECKED
+    int src_limit;           // a gather's parent slots lie in [0, src_limit)
+    int32_t *err;            // the run's error flag
+#endif
 };
 
 __device__ __forceinline__ void record_replica(const Group &G, int slot, int E, int Mt, int N, long long &sE,
@@ -275,6 +279,12 @@ __device__ __forceinline__ void record_replica(const Group &G, int slot, int E, 
 {
     G.E[slot] = E;
     G.Mt[slot] = Mt;
+#if PA_CHECKED
+    if (E < -2 * N || E > 0) {
+        atomicExch(G.err, 1);  // PA_ERR_INVALID
+        return;
+    }
+#endif
     atomicAdd(G.hist + (E + 2 * N), 1);
     sE += E;
     sE2 += (long long)E * (long long)E;
@@ -424,7 +434,15 @@ __device__ __forceinline__ void sweep_group_bits(const Group &G, int Lrt, uint32
         const int r = i / UPR;
         const int o = i - r * UPR;
         const int slot = first + r;
+#if PA_CHECKED
+        int src = G.gather ? G.parent[slot] : slot;
+        if (G.gather && (src < 0 || src >= G.src_limit)) {
+            atomicExch(G.err, 1);  // PA_ERR_INVALID
+            src = 0;
+        }
+#else
         const int src = G.gather ? G.parent[slot] : slot;
+#endif
         smem4[r * UPR + o] = reinterpret_cast<const uint4 *>(G.in + (size_t)src * RW)[o];
     }
     __syncthreads();
