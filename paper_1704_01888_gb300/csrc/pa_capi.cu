@@ -113,6 +113,7 @@ struct pa_ctx {
     size_t stage_bytes = 0;
     uint8_t *host_stage = nullptr;  // pinned: device state, one record, the histogram
     double *aux = nullptr;  // small device outputs (Newton step)
+    int32_t *work = nullptr;  // the sweep kernel's group counter
 
     int step = 0;          // last completed temperature step
     int pending_step = 0;  // step of an enqueued resample awaiting its sweep
@@ -279,7 +280,7 @@ void release(pa_ctx *c)
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     void *ptrs[] = {c->spins[0], c->spins[1], c->anc[0], c->anc[1], c->E, c->Mt, c->hist, c->fam,
                     c->counts, c->local_off, c->blocksum, c->parent, c->acc, c->st, c->obs,
-                    c->stage, c->aux};
+                    c->stage, c->aux, c->work};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->host_stage) cudaFreeHost(c->host_stage);
@@ -380,6 +381,10 @@ pa::SweepArgs sweep_args(pa_ctx *c, double beta, int theta, int step, int gather
     a.gather = gather;
     a.stream_hi = (uint32_t)c->cfg.stream << 24;
     a.slot0 = (uint32_t)c->slot0;
+    // few groups per block: hand them out from a counter, so that the blocks
+    // end together; with many, equal shares (their ends even out)
+    const long long R_est = c->R_fill > 0 ? c->R_fill : c->cfg.R;
+    a.work = R_est < 16LL * c->rpb * c->grid ? c->work : nullptr;
     return a;
 }
 
@@ -518,7 +523,8 @@ pa_status ctx_create(const pa_config &g, void *cuda_stream, pa_ctx **out, int ra
         (s = dev_alloc(&c->E, c->R_cap)) || (s = dev_alloc(&c->Mt, c->R_cap)) ||
         (s = dev_alloc(&c->hist, c->nbins)) || (s = dev_alloc(&c->counts, c->R_cap)) ||
         (s = dev_alloc(&c->local_off, R_child)) || (s = dev_alloc(&c->blocksum, nb)) ||
-        (s = dev_alloc(&c->parent, R_child)) || (s = dev_alloc(&c->acc, 4)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)))
+        (s = dev_alloc(&c->parent, R_child)) || (s = dev_alloc(&c->acc, 4)) || (s = dev_alloc(&c->st, 1)) || (s = dev_alloc(&c->aux, 4)) ||
+        (s = dev_alloc(&c->work, 1)))
         return fail(s);
     if (g.track_families) {
         if ((s = dev_alloc(&c->anc[0], c->R_cap)) || (s = dev_alloc(&c->anc[1], c->R_cap)) ||

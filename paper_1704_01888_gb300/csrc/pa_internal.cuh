@@ -115,6 +115,8 @@ struct SweepArgs {
     int32_t gather;            // 1: read parents from buf[parity], write buf[parity^1]
     uint32_t stream_hi;        // stream number << 24 (top byte of the slot counter word)
     uint32_t slot0;            // global slot of local slot 0 (0 unless the population spans GPUs)
+    int32_t *work;             // next replica group to hand out (zeroed before each launch), or
+                               // null: each block takes an equal share
 };
 
 // Launchers (pa_sweep.cu)
